@@ -1,0 +1,331 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the GB300 windowed GenASM aligner.
+
+One step aligns a whole batch: every pair of the workload goes through the
+windowing loop (GenASM-DC with ET, DENT/SENE storage, GenASM-TB, slide).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload long_reads]
+                  [--impl ours|reference] [--pairs P] [--no-e2e] [--no-cpu-baseline]
+
+Prints one JSON line (rank 0). ``value`` is alignments/s of the device-resident
+batch (CUDA events around each launch on the launching stream, max over
+ranks); ``e2e`` is the same metric through the C ABI with pinned host buffers
+(host-to-device copies of the packed inputs and device-to-host copies of all
+outputs inside the timed region). ``--impl reference`` times the CPU oracle on
+the host cores instead. With N > 1 (torchrun), each rank aligns its own batch
+of the same size (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2208_09985_gb300 import synth  # noqa: E402
+
+WORKLOADS = {
+    "long_reads": dict(
+        make=lambda n, seed: synth.long_reads(n, seed=seed), n=100_000, seed=2, W=64, O=24, cap=4096,
+        desc="100,000 pairs: 10 kbp patterns vs 10.5 kbp texts, 10% edits (50/25/25, 20% homopolymer "
+             "indels of 1-5 bases), W=64 O=24 k=64"),
+    "short_reads": dict(
+        make=lambda n, seed: synth.short_reads(n, seed=seed), n=1_000_000, seed=1, W=64, O=24, cap=None,
+        desc="1,000,000 pairs: patterns U{100..250} bp, texts +5% padding, 5% edits, W=64 O=24 k=64"),
+    "uneven_reads": dict(
+        make=lambda n, seed: synth.uneven_reads(n, seed=seed), n=200_000, seed=3, W=64, O=24, cap=None,
+        desc="200,000 pairs: log-normal lengths (median 8 kbp, 1-100 kbp), per-pair error U[1%,15%], W=64 O=24"),
+    "tiny_windows": dict(
+        make=lambda n, seed: synth.tiny_windows(n, seed=seed), n=1000, seed=0, W=64, O=24, cap=None,
+        desc="1,000 pairs: 110 bp texts, 100 bp patterns, 2% edits, W=64 O=24"),
+}
+
+METRIC = "alignments/s and Gbases/s on 1 GB300 (10 kbp, 10% err), learned+persistent vs plain"
+INT_LOGIC_OPS_PER_CLK_PER_SM = 64  # LOP3/SHF pipe, measured on GB300
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="long_reads")
+    ap.add_argument("--pairs", type=int, default=0, help="override the workload's pair count")
+    ap.add_argument("--flags", type=int, default=0, help="extra SCROOGE_* flags (ablations)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="time budget of the CPU baseline")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while alive."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        rows = [r.split(",") for r in out.strip().splitlines() if r.count(",") >= 8]
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows]
+        mx = [float(r[2]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].strip().lower() == "active"})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": reasons, "samples": len(rows)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def kernel_traffic(words: int):
+    """DRAM bytes per launch of the alignment kernel from the committed ncu summary,
+    or None when the kernel source changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "align_kernel_traffic.json")
+    try:
+        rec = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    src = open(os.path.join(ROOT, "paper_2208_09985_gb300", "csrc", "align_kernel.cuh"), "rb").read()
+    if rec.get("source_sha256") != hashlib.sha256(src).hexdigest():
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+def cpu_baseline(batch, W, O, budget_s: float):
+    """The oracle as it stands on all host cores, over a time-bounded prefix of the batch."""
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    chunk = 1024
+    done, t0 = 0, time.perf_counter()
+    while done < batch.n_pairs and time.perf_counter() - t0 < budget_s:
+        hi = min(batch.n_pairs, done + chunk)
+        oracle.align_batch(batch.subset(np.arange(done, hi)), W, O, threads=cores)
+        done = hi
+    dt = time.perf_counter() - t0
+    bases = int(np.diff(batch.pattern_off)[:done].sum())
+    return {"value": done / dt, "unit": "alignments/s", "cores": cores, "kind": "oracle",
+            "gbases_per_s": bases / dt / 1e9,
+            "sample": f"first {done} pairs of the workload (time-bounded at {budget_s:g} s), {cores} threads"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    wl = WORKLOADS[args.workload]
+    n_total = args.pairs or wl["n"]
+    per_step = min(n_total, 2048 if args.workload in ("long_reads", "uneven_reads") else 65536)
+    batch = wl["make"](per_step, wl["seed"])
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        oracle.align_batch(batch, wl["W"], wl["O"], threads=cores)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.align_batch(batch, wl["W"], wl["O"], threads=cores)
+        times.append(time.perf_counter() - t0)
+    ms = 1e3 * sum(times) / len(times)
+    value = per_step / (ms / 1e3)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "alignments/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32 bit-vectors", "data": "synthetic",
+        "config": {"workload": args.workload, "desc": wl["desc"], "pairs_per_step": per_step,
+                   "W": wl["W"], "O": wl["O"], "k": wl["W"]},
+        "gbases_per_s": float(np.diff(batch.pattern_off).sum()) / (ms / 1e3) / 1e9,
+        "cpu_baseline": {"value": value, "unit": "alignments/s", "cores": cores, "kind": "oracle",
+                         "sample": f"first {per_step} pairs of the workload per step, {cores} threads"},
+        "e2e": {"value": value, "unit": "alignments/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import paper_2208_09985_gb300 as sc
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    wl = WORKLOADS[args.workload]
+    n_pairs = args.pairs or wl["n"]
+    W, O, k = wl["W"], wl["O"], wl["W"]
+    batch = wl["make"](n_pairs, wl["seed"] + 1000 * rank)
+    pb = sc.PackedBatch(batch)
+    stream = torch.cuda.current_stream()
+    ctx = sc.scrooge_create(local, stream)
+    db = sc.DeviceBatch(pb, cigar_capacity=wl["cap"])
+    flags = args.flags
+    words = 1 if W <= 32 else (2 if W <= 64 else 4)
+
+    # untimed run with per-pair statistics: algorithmic DP cells of the method
+    cells = torch.zeros(n_pairs, dtype=torch.int64, device="cuda")
+    rows = torch.zeros(n_pairs, dtype=torch.int64, device="cuda")
+    sc.scrooge_set_stats(ctx, None, rows, cells, None)
+    sc.align_device(ctx, db, W, O, k, flags | sc.SCROOGE_SYNC)
+    sc.scrooge_set_stats(ctx)
+    total_cells = int(cells.sum().item())
+    total_rows = int(rows.sum().item())
+    ec = db.edit_counts.cpu().numpy()
+    cl = db.cigar_lens.cpu().numpy()
+    if (ec < 0).any() or (cl < 0).any():
+        raise SystemExit("bench: some pairs failed or overflowed their CIGAR capacity")
+
+    for _ in range(args.warmup):
+        sc.align_device(ctx, db, W, O, k, flags)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(local)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    for a, b in evs:
+        a.record(stream)
+        sc.align_device(ctx, db, W, O, k, flags)
+        b.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    ms = sum(step_ms) / len(step_ms)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * n_pairs / (ms / 1e3)
+    bases = int(np.diff(batch.pattern_off).sum())
+
+    # end to end through the C ABI with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+        h_in = [pin(x) for x in (pb.texts, pb.text_off, pb.text_len, pb.patterns, pb.pat_off, pb.pat_len)]
+        coff = pin(pb.cigar_offsets(wl["cap"]))
+        h_ec = torch.zeros(n_pairs, dtype=torch.int32).pin_memory().numpy()
+        h_tc = torch.zeros(n_pairs, dtype=torch.int32).pin_memory().numpy()
+        h_cl = torch.zeros(n_pairs, dtype=torch.int32).pin_memory().numpy()
+        h_cig = torch.zeros(int(coff[-1]), dtype=torch.int32).pin_memory().numpy().view(np.uint32)
+        e2e_ctx = sc.scrooge_create(local, stream)
+
+        def call():
+            sc.scrooge_align_batch(e2e_ctx, h_in[0], h_in[1], h_in[2], h_in[3], h_in[4], h_in[5], n_pairs, W, O,
+                                   k, flags, h_ec, h_tc, h_cig, coff, h_cl)
+        call()
+        e2e_steps = max(2, min(args.steps, 5))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            call()
+        torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - t0) / e2e_steps
+        if world > 1:
+            t = torch.tensor([e2e_s], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        h2d = sum(int(x.nbytes) for x in h_in) + int(coff.nbytes)
+        d2h = int(h_ec.nbytes + h_tc.nbytes + h_cl.nbytes + h_cig.nbytes)
+        if not (np.array_equal(h_ec, ec) and np.array_equal(h_cl, cl)):
+            raise SystemExit("bench: end-to-end results differ from the device-resident run")
+        e2e = {"value": world * n_pairs / e2e_s, "unit": "alignments/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "gbases_per_s": world * bases / e2e_s / 1e9}
+        sc.scrooge_destroy(e2e_ctx)
+
+    if rank != 0:
+        sc.scrooge_destroy(ctx)
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+
+    # roofline of the alignment kernel: LOP3/SHF integer pipe
+    props = torch.cuda.get_device_properties(local)
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz") or (clk or {}).get("sm_max_mhz") or 2070.0)
+    peak_ops = props.multi_processor_count * INT_LOGIC_OPS_PER_CLK_PER_SM * sm_max * 1e6
+    ops_per_cell = 3 * words - 1
+    achieved = total_cells * ops_per_cell / (ms / 1e3)
+    traffic = kernel_traffic(words)
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(batch, W, O, args.cpu_seconds)
+    line = {
+        "metric": METRIC, "value": value, "unit": "alignments/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32 bit-vectors", "data": "synthetic",
+        "config": {"workload": args.workload, "desc": wl["desc"], "pairs_per_gpu": n_pairs, "W": W, "O": O, "k": k,
+                   "path": "plain per-pair launch (static pair order)", "flags": flags,
+                   "kernel_config": list(sc.scrooge_get_kernel_config(ctx, words)),
+                   "l2": "inputs larger than L2 (packed inputs %.0f MB)" % (pb.texts.nbytes / 1e6 + pb.patterns.nbytes / 1e6),
+                   "parallelism": f"dp{world}" if world > 1 else "single GPU"},
+        "gbases_per_s": world * bases / (ms / 1e3) / 1e9,
+        "mean_edits_per_pair": float(ec.mean()),
+        "dp_cells_per_step": total_cells, "dp_rows_per_step": total_rows,
+        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
+                     "frac": achieved / peak_ops, "traffic": traffic,
+                     "basis": f"{ops_per_cell} LOP3/SHF ops per DP cell computed up to each window's edit "
+                              f"distance; peak = {props.multi_processor_count} SMs x "
+                              f"{INT_LOGIC_OPS_PER_CLK_PER_SM} ops/clk x {sm_max:.0f} MHz"},
+        "clocks": clk,
+        "gpu_launches": args.steps,
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+        "step_ms": [round(x, 4) for x in step_ms],
+    }
+    print(json.dumps(line), flush=True)
+    sc.scrooge_destroy(ctx)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,161 @@
+/*
+ * scrooge.h -- C ABI of a GB300 (sm_103a) library for Scrooge's windowed
+ * GenASM pairwise alignment (Lindegger et al., "Scrooge: A Fast and Memory-
+ * Frugal Genomic Sequence Aligner for CPUs, GPUs, and ASICs", arXiv 2208.09985).
+ *
+ * The library aligns many (text = reference, pattern = read) pairs. For each
+ * pair it runs the windowing heuristic of Section 2.2.3: a W-character window
+ * of both strings is aligned by GenASM-DC (Algorithm 1, Section 2.2.1) with
+ * early termination at the first edit count d that reaches the window start
+ * (ET, Section 2.4.3), the DP entries that the traceback can reach are kept
+ * (SENE, Section 2.4.1; DENT, Section 2.4.2), and GenASM-TB (Section 2.2.2)
+ * walks them to emit CIGAR operations for the first W-O characters; the next
+ * window starts where the traceback stopped. The problem solved in each
+ * window is edit distance with the whole pattern and a free end in the text
+ * (Theorem 1 with the initial column R[n][d] = 1..1 << d).
+ *
+ * Conventions fixed where the paper is silent (identical to the CPU oracle):
+ * the traceback prefers M, then S (substitution), then I, then D when several
+ * edges hold a 0; it stops as soon as W-O text characters, or W-O pattern
+ * characters, or the whole pattern window are consumed; text and pattern
+ * cursors advance by the characters consumed.
+ *
+ * Thread safety: a context may be used by one host thread at a time.
+ * All entry points return 0 (SCROOGE_OK) or a negative SCROOGE_E_* code;
+ * scrooge_last_error() then describes the failure.
+ */
+#ifndef SCROOGE_H
+#define SCROOGE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct scrooge_ctx scrooge_ctx; /* opaque, owned by the library */
+
+/* ------------------------------------------------------------ status codes */
+#define SCROOGE_OK 0
+#define SCROOGE_E_INVAL (-1)    /* bad argument (sizes, alignment, W/O/k, null pointer) */
+#define SCROOGE_E_NOMEM (-2)    /* device or host allocation failed */
+#define SCROOGE_E_CUDA (-3)     /* a CUDA call failed; see scrooge_last_error */
+#define SCROOGE_E_TIMEOUT (-4)  /* a bounded device wait gave up */
+#define SCROOGE_E_NOMODEL (-5)  /* SCROOGE_LEARNED without a loaded or trained model */
+#define SCROOGE_E_INTERNAL (-6) /* a kernel reported an impossible state */
+
+/* ------------------------------------------------------------------- flags */
+/* All pointers passed to scrooge_align_batch are device pointers and the
+ * call is asynchronous on the context stream. Without it, all pointers are
+ * host pointers: inputs are copied to the device, outputs back, and the call
+ * returns when the results are in host memory. */
+#define SCROOGE_DEVICE_PTRS (1u << 0)
+/* With SCROOGE_DEVICE_PTRS: synchronise the stream before returning. */
+#define SCROOGE_SYNC (1u << 1)
+/* Ablation switches (Section 3.3); results are identical with any of them. */
+#define SCROOGE_NO_SENE (1u << 2) /* store GenASM's three edge vectors instead of entries */
+#define SCROOGE_NO_DENT (1u << 3) /* store every column and every bit of each entry */
+#define SCROOGE_NO_ET (1u << 4)   /* compute all k+1 rows of every window */
+/* Scheduling (results are identical): */
+#define SCROOGE_PERSISTENT (1u << 5) /* persistent kernel pulling pairs from a device queue */
+#define SCROOGE_LEARNED (1u << 6)    /* order pairs by the MLP's predicted load (implies PERSISTENT) */
+#define SCROOGE_GRAPH (1u << 7)      /* capture the learned/persistent pipeline in a CUDA graph */
+
+/* CIGAR run encoding: (length << 4) | op, op in SAM codes. */
+#define SCROOGE_OP_I 1  /* base only in the pattern (read): insertion */
+#define SCROOGE_OP_D 2  /* base only in the text (reference): deletion */
+#define SCROOGE_OP_EQ 7 /* '=' match */
+#define SCROOGE_OP_X 8  /* 'X' substitution */
+
+/* Create a context on CUDA device `cuda_device`, issuing work on
+ * `cuda_stream` (a cudaStream_t; NULL = the legacy default stream).
+ * *out receives the context; free it with scrooge_destroy. */
+int scrooge_create(scrooge_ctx **out, int cuda_device, void *cuda_stream);
+
+/* Free a context and all device memory it owns (NULL is accepted). */
+int scrooge_destroy(scrooge_ctx *ctx);
+
+/* Description of the last failure on this context ("" if none). The string
+ * is owned by the context and valid until the next call on it. */
+const char *scrooge_last_error(const scrooge_ctx *ctx);
+
+/* Replace the stream used by later calls. */
+int scrooge_set_stream(scrooge_ctx *ctx, void *cuda_stream);
+
+/* ---------------------------------------------------------- input packing
+ * Sequences are read in a 2-bit packed form (Section 2.5: the GPU version
+ * transfers two bits per base): every 32 bases form one block of two 32-bit
+ * words, the low-bit plane then the high-bit plane of the codes A=0, C=1,
+ * G=2, T=3; base t of a block sits at bit 31-t of both words. A packed
+ * sequence starts at a base offset that is a multiple of 64 (16 bytes) and
+ * its unused tail bits are 0. */
+
+/* 32-bit words that scrooge_pack_2bit uses for a sequence of n bases
+ * (rounded up to a 64-base boundary). */
+int64_t scrooge_packed_words(int64_t n_bases);
+
+/* Host-side packer. seqs[offsets[s] .. offsets[s+1]) is sequence s, as codes
+ * 0..3 (ascii = 0) or letters ACGT/acgt (ascii = 1; anything else is
+ * SCROOGE_E_INVAL). Writes the packed words of all n_seqs sequences
+ * back to back into `packed` (capacity `packed_words`), their base offsets
+ * into packed_offsets[n_seqs] and their lengths into lengths[n_seqs].
+ * All pointers are host pointers owned by the caller. */
+int scrooge_pack_2bit(const uint8_t *seqs, const int64_t *offsets, int32_t n_seqs, int ascii,
+                      uint32_t *packed, int64_t packed_words, int64_t *packed_offsets, int32_t *lengths);
+
+/* ------------------------------------------------------------- alignment
+ * Align pair p = (text p, pattern p) for p in [0, n_pairs).
+ *
+ *   texts, patterns      packed sequences (see above)
+ *   *_offsets[n_pairs]   base offset of each sequence (multiple of 64)
+ *   *_lengths[n_pairs]   its length in bases (>= 0)
+ *   W                    window size, 1..128 (Section 2.2.3)
+ *   O                    window overlap, 0..W-1
+ *   k                    largest edit count tried per window, 0..W; a window
+ *                        with no d <= k fails the pair (k = W never fails)
+ *   flags                SCROOGE_* flags above
+ * Outputs (caller-owned):
+ *   edit_counts[n_pairs]    X + I + D operations of the pair's CIGAR, or -1
+ *                           if some window failed (empty CIGAR)
+ *   text_consumed[n_pairs]  text bases covered by the CIGAR (the text end is free)
+ *   cigar                   run-length CIGAR runs (SCROOGE_OP_*); pair p may
+ *                           write cigar[cigar_offsets[p] .. cigar_offsets[p+1])
+ *   cigar_offsets[n_pairs+1] capacity layout (input); m + n + 1 runs always suffice
+ *   cigar_lens[n_pairs]     runs written, or -1 if the capacity was too small
+ * Returns SCROOGE_E_INVAL before any work on bad arguments. */
+int scrooge_align_batch(scrooge_ctx *ctx, const uint32_t *texts, const int64_t *text_offsets,
+                        const int32_t *text_lengths, const uint32_t *patterns, const int64_t *pattern_offsets,
+                        const int32_t *pattern_lengths, int32_t n_pairs, int32_t W, int32_t O, int32_t k,
+                        uint32_t flags, int32_t *edit_counts, int32_t *text_consumed, uint32_t *cigar,
+                        const int64_t *cigar_offsets, int32_t *cigar_lens);
+
+/* ------------------------------------------------------- kernel settings
+ * Implementation parameters of the alignment kernel for windows of up to
+ * 32 * words bases (words = 1, 2 or 4). They never change results.
+ *   lanes_per_pair   threads that share one pair's window (words=1: 1,2,4;
+ *                    words=2: 2,4,8; words=4: 8,16)
+ *   smem_rows        DP rows of each pair kept in shared memory (>= 1); rows
+ *                    beyond go to a device scratch area
+ *   warps_per_block  1..8
+ * scrooge_get_kernel_config reports the current values. */
+int scrooge_set_kernel_config(scrooge_ctx *ctx, int32_t words, int32_t lanes_per_pair, int32_t smem_rows,
+                              int32_t warps_per_block);
+int scrooge_get_kernel_config(const scrooge_ctx *ctx, int32_t words, int32_t *lanes_per_pair,
+                              int32_t *smem_rows, int32_t *warps_per_block);
+
+/* Per-pair statistics of the next scrooge_align_batch calls, written to
+ * caller-owned DEVICE arrays of n_pairs entries (any may be NULL; all NULL
+ * switches statistics off): windows aligned, DP rows computed up to each
+ * window's edit distance (sum of d_opt + 1), DP cells in those rows (sum of
+ * (d_opt + 1) * text window length), and SM clock cycles the pair took. */
+int scrooge_set_stats(scrooge_ctx *ctx, int32_t *windows, int64_t *rows, int64_t *cells, int64_t *cycles);
+
+/* Testing hook: make the next `count` device allocations of this context
+ * fail with SCROOGE_E_NOMEM (0 switches it off). */
+int scrooge_debug_fail_next_allocs(scrooge_ctx *ctx, int32_t count);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SCROOGE_H */

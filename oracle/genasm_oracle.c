@@ -315,8 +315,9 @@ int orc_align_pair(const uint8_t *text, int64_t n, const uint8_t *pattern, int64
     int64_t tc = 0, nwin = 0;
     int st = align_pair(&w, text, n, pattern, m, W, O, k, &c, &tc, &nwin, dopt_log, dopt_cap);
     work_free(&w);
-    *edit_count = st == 0 ? (int32_t)c.edits : -1;
-    *text_consumed = st == 0 ? tc : 0;
+    /* a CIGAR overflow still aligned the pair: only the run count reports it */
+    *edit_count = (st == 0 || st == -2) ? (int32_t)c.edits : -1;
+    *text_consumed = (st == 0 || st == -2) ? tc : 0;
     *cigar_len = st == 0 ? c.len : (st == -2 ? -1 : 0);
     if (n_windows) *n_windows = nwin;
     return st;
@@ -364,8 +365,8 @@ static void *batch_worker(void *arg) {
             b->err = -1;
             pthread_mutex_unlock(&b->lock);
         }
-        b->edit_counts[p] = st == 0 ? (int32_t)c.edits : -1;
-        b->text_consumed[p] = st == 0 ? (int32_t)tc : 0;
+        b->edit_counts[p] = (st == 0 || st == -2) ? (int32_t)c.edits : -1;
+        b->text_consumed[p] = (st == 0 || st == -2) ? (int32_t)tc : 0;
         b->cigar_lens[p] = st == 0 ? (int32_t)c.len : (st == -2 ? -1 : 0);
     }
     work_free(&w);

@@ -1,0 +1,256 @@
+"""Python binding of ``libscrooge.so``, the GB300 windowed GenASM aligner.
+
+The functions below carry the names of the C ABI in ``include/scrooge.h`` and
+only marshal arguments: every step of the alignment runs in the CUDA library.
+There is no fallback: if the library is not built, calls raise.
+
+Arrays may be numpy arrays (host memory) or torch tensors. With
+``SCROOGE_DEVICE_PTRS`` in ``flags`` every array of ``scrooge_align_batch``
+must be a CUDA tensor; otherwise every array must be in host memory.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(_HERE)
+LIB_PATH = os.path.join(_HERE, "_build", "libscrooge.so")
+HEADER = os.path.join(ROOT, "include", "scrooge.h")
+
+SCROOGE_OK = 0
+SCROOGE_E_INVAL = -1
+SCROOGE_E_NOMEM = -2
+SCROOGE_E_CUDA = -3
+SCROOGE_E_TIMEOUT = -4
+SCROOGE_E_NOMODEL = -5
+SCROOGE_E_INTERNAL = -6
+
+SCROOGE_DEVICE_PTRS = 1 << 0
+SCROOGE_SYNC = 1 << 1
+SCROOGE_NO_SENE = 1 << 2
+SCROOGE_NO_DENT = 1 << 3
+SCROOGE_NO_ET = 1 << 4
+SCROOGE_PERSISTENT = 1 << 5
+SCROOGE_LEARNED = 1 << 6
+SCROOGE_GRAPH = 1 << 7
+
+SCROOGE_OP_I, SCROOGE_OP_D, SCROOGE_OP_EQ, SCROOGE_OP_X = 1, 2, 7, 8
+
+_lib = None
+_lock = threading.Lock()
+
+
+class ScroogeError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"scrooge error {code}: {msg}")
+        self.code = code
+
+
+def load():
+    """The loaded CUDA library. Raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"CUDA library missing at {LIB_PATH}: build it with "
+                                   "`python -c 'import __graft_entry__ as g; g.build()'`")
+            lib = ctypes.CDLL(LIB_PATH)
+            P, i32, i64, u32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32
+            sig = {
+                "scrooge_create": ([ctypes.POINTER(P), ctypes.c_int, P], ctypes.c_int),
+                "scrooge_destroy": ([P], ctypes.c_int),
+                "scrooge_last_error": ([P], ctypes.c_char_p),
+                "scrooge_set_stream": ([P, P], ctypes.c_int),
+                "scrooge_packed_words": ([i64], i64),
+                "scrooge_pack_2bit": ([P, P, i32, ctypes.c_int, P, i64, P, P], ctypes.c_int),
+                "scrooge_align_batch": ([P, P, P, P, P, P, P, i32, i32, i32, i32, u32, P, P, P, P, P],
+                                        ctypes.c_int),
+                "scrooge_set_kernel_config": ([P, i32, i32, i32, i32], ctypes.c_int),
+                "scrooge_get_kernel_config": ([P, i32, P, P, P], ctypes.c_int),
+                "scrooge_set_stats": ([P, P, P, P, P], ctypes.c_int),
+                "scrooge_debug_fail_next_allocs": ([P, i32], ctypes.c_int),
+            }
+            for name, (args, res) in sig.items():
+                f = getattr(lib, name)
+                f.argtypes = args
+                f.restype = res
+            _lib = lib
+    return _lib
+
+
+def header_functions() -> list[str]:
+    """Names of every function declared in include/scrooge.h."""
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(scrooge_\w+)\s*\(", src)))
+
+
+def _ptr(a):
+    """Raw address of a numpy array or torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return a.data_ptr()
+    if isinstance(a, int):
+        return a
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _check(ctx, rc: int):
+    if rc != SCROOGE_OK:
+        msg = load().scrooge_last_error(ctx).decode() if ctx else ""
+        raise ScroogeError(rc, msg)
+    return rc
+
+
+def scrooge_create(device: int = 0, stream=None):
+    """New context on ``device``; ``stream`` is a torch.cuda.Stream, a raw handle or None."""
+    h = ctypes.c_void_p()
+    s = getattr(stream, "cuda_stream", stream)
+    rc = load().scrooge_create(ctypes.byref(h), int(device), s)
+    if rc != SCROOGE_OK:
+        raise ScroogeError(rc, "scrooge_create failed (no usable CUDA device?)")
+    return h
+
+
+def scrooge_destroy(ctx):
+    return load().scrooge_destroy(ctx)
+
+
+def scrooge_last_error(ctx) -> str:
+    return load().scrooge_last_error(ctx).decode()
+
+
+def scrooge_set_stream(ctx, stream):
+    return _check(ctx, load().scrooge_set_stream(ctx, getattr(stream, "cuda_stream", stream)))
+
+
+def scrooge_packed_words(n_bases: int) -> int:
+    return int(load().scrooge_packed_words(int(n_bases)))
+
+
+def scrooge_pack_2bit(seqs: np.ndarray, offsets: np.ndarray, ascii: bool = False):
+    """Pack concatenated sequences; returns (packed uint32, base offsets int64, lengths int32)."""
+    seqs = np.ascontiguousarray(seqs, dtype=np.uint8)
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    n = offsets.shape[0] - 1
+    lens = np.diff(offsets)
+    total = int(sum((int(x) + 63) // 64 * 4 for x in lens)) if n < 4096 else \
+        int((((lens + 63) // 64) * 4).sum())
+    packed = np.zeros(max(total, 1), dtype=np.uint32)
+    poff = np.zeros(max(n, 1), dtype=np.int64)
+    plen = np.zeros(max(n, 1), dtype=np.int32)
+    rc = load().scrooge_pack_2bit(_ptr(seqs), _ptr(offsets), n, 1 if ascii else 0, _ptr(packed),
+                                  packed.shape[0], _ptr(poff), _ptr(plen))
+    if rc != SCROOGE_OK:
+        raise ScroogeError(rc, "scrooge_pack_2bit: bad sequence or offsets")
+    return packed, poff[:n], plen[:n]
+
+
+def scrooge_align_batch(ctx, texts, text_offsets, text_lengths, patterns, pattern_offsets, pattern_lengths,
+                        n_pairs: int, W: int, O: int, k: int, flags: int, edit_counts, text_consumed, cigar,
+                        cigar_offsets, cigar_lens):
+    """Direct call of the C entry point; raises ScroogeError on a non-zero return."""
+    rc = load().scrooge_align_batch(ctx, _ptr(texts), _ptr(text_offsets), _ptr(text_lengths), _ptr(patterns),
+                                    _ptr(pattern_offsets), _ptr(pattern_lengths), int(n_pairs), int(W), int(O),
+                                    int(k), int(flags), _ptr(edit_counts), _ptr(text_consumed), _ptr(cigar),
+                                    _ptr(cigar_offsets), _ptr(cigar_lens))
+    return _check(ctx, rc)
+
+
+def scrooge_set_kernel_config(ctx, words: int, lanes_per_pair: int, smem_rows: int, warps_per_block: int):
+    return _check(ctx, load().scrooge_set_kernel_config(ctx, words, lanes_per_pair, smem_rows, warps_per_block))
+
+
+def scrooge_get_kernel_config(ctx, words: int):
+    a, b, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(ctx, load().scrooge_get_kernel_config(ctx, words, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return a.value, b.value, c.value
+
+
+def scrooge_set_stats(ctx, windows=None, rows=None, cells=None, cycles=None):
+    return _check(ctx, load().scrooge_set_stats(ctx, _ptr(windows), _ptr(rows), _ptr(cells), _ptr(cycles)))
+
+
+def scrooge_debug_fail_next_allocs(ctx, count: int):
+    return _check(ctx, load().scrooge_debug_fail_next_allocs(ctx, int(count)))
+
+
+# --------------------------------------------------------------- helpers
+
+
+class PackedBatch:
+    """A synth.PairBatch packed for the library (host numpy arrays)."""
+
+    def __init__(self, batch):
+        self.n_pairs = batch.n_pairs
+        self.texts, self.text_off, self.text_len = scrooge_pack_2bit(batch.texts, batch.text_off)
+        self.patterns, self.pat_off, self.pat_len = scrooge_pack_2bit(batch.patterns, batch.pattern_off)
+
+    def cigar_offsets(self, capacity=None) -> np.ndarray:
+        """Capacity layout: m + n + 1 runs per pair unless ``capacity`` (scalar or per pair) is given."""
+        if capacity is None:
+            cap = self.text_len.astype(np.int64) + self.pat_len.astype(np.int64) + 1
+        else:
+            cap = np.broadcast_to(np.asarray(capacity, dtype=np.int64), (self.n_pairs,))
+        off = np.zeros(self.n_pairs + 1, dtype=np.int64)
+        np.cumsum(cap, out=off[1:])
+        return off
+
+
+def align_host(ctx, pb: PackedBatch, W: int = 64, O: int = 24, k: int | None = None, flags: int = 0,
+               cigar_capacity=None) -> dict:
+    """Align a PackedBatch from host memory; returns host numpy results."""
+    k = W if k is None else k
+    n = pb.n_pairs
+    coff = pb.cigar_offsets(cigar_capacity)
+    ec = np.zeros(n, np.int32)
+    tc = np.zeros(n, np.int32)
+    cl = np.zeros(n, np.int32)
+    cig = np.zeros(max(int(coff[-1]), 1), np.uint32)
+    scrooge_align_batch(ctx, pb.texts, pb.text_off, pb.text_len, pb.patterns, pb.pat_off, pb.pat_len, n, W, O, k,
+                        flags & ~SCROOGE_DEVICE_PTRS, ec, tc, cig, coff, cl)
+    return {"edit_counts": ec, "text_consumed": tc, "cigar": cig, "cigar_off": coff, "cigar_lens": cl}
+
+
+class DeviceBatch:
+    """A PackedBatch resident on a CUDA device (torch tensors), with output buffers."""
+
+    def __init__(self, pb: PackedBatch, device="cuda", cigar_capacity=None):
+        import torch
+        t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(device)
+        self.n_pairs = pb.n_pairs
+        self.texts, self.text_off, self.text_len = t(pb.texts), t(pb.text_off), t(pb.text_len)
+        self.patterns, self.pat_off, self.pat_len = t(pb.patterns), t(pb.pat_off), t(pb.pat_len)
+        coff = pb.cigar_offsets(cigar_capacity)
+        self.cigar_off = t(coff)
+        self.edit_counts = torch.zeros(self.n_pairs, dtype=torch.int32, device=device)
+        self.text_consumed = torch.zeros_like(self.edit_counts)
+        self.cigar_lens = torch.zeros_like(self.edit_counts)
+        self.cigar = torch.zeros(max(int(coff[-1]), 1), dtype=torch.int32, device=device)
+
+
+def align_device(ctx, db: DeviceBatch, W: int = 64, O: int = 24, k: int | None = None, flags: int = 0):
+    """Align a DeviceBatch in place (asynchronous unless SCROOGE_SYNC is in flags)."""
+    k = W if k is None else k
+    return scrooge_align_batch(ctx, db.texts, db.text_off, db.text_len, db.patterns, db.pat_off, db.pat_len,
+                               db.n_pairs, W, O, k, flags | SCROOGE_DEVICE_PTRS, db.edit_counts, db.text_consumed,
+                               db.cigar, db.cigar_off, db.cigar_lens)
+
+
+def device_results(db: DeviceBatch) -> dict:
+    """Copy a DeviceBatch's outputs to host numpy arrays."""
+    return {"edit_counts": db.edit_counts.cpu().numpy(), "text_consumed": db.text_consumed.cpu().numpy(),
+            "cigar": db.cigar.cpu().numpy().view(np.uint32), "cigar_off": db.cigar_off.cpu().numpy(),
+            "cigar_lens": db.cigar_lens.cpu().numpy()}

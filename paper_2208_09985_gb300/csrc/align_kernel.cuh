@@ -1,0 +1,415 @@
+// Windowed GenASM alignment kernel for sm_103a (Scrooge, arXiv 2208.09985).
+//
+// Work decomposition. A warp holds 32/G pairs; the G lanes of a pair split the
+// W columns (text positions) of a window into G contiguous chunks of C = W/G
+// columns. Lane l owns columns [(G-1-l)*C, (G-l)*C): lane 0 the highest, lane
+// G-1 column 0. Algorithm 1 (Section 2.2.1) computes a row d from column n-1
+// down to column 0, because entry R[i][d] needs R[i+1][d]; the lanes form a
+// pipeline over rows: in step s lane l computes row d = s - l of its chunk,
+// taking R[top+1][d] from lane l-1 (computed one step earlier) by a warp
+// shuffle. Every lane keeps, for each of its columns, the part of the
+// recurrence that comes from the previous row in registers,
+//     X[i] = (R[i][d-1] << 1) & R[i+1][d-1] & (R[i+1][d-1] << 1),
+// so a cell costs one shift of the new entry and two 3-input logic ops per
+// 32-bit word:  R[i][d] = X[i] & ((R[i+1][d] << 1) | PM[text[i]]).
+// Rows are built one after the other, so early termination (ET, Section
+// 2.4.3) stops a window as soon as lane G-1 sees a 0 in the first bit of
+// R[0][d]: at most G-1 extra rows are touched by the other lanes.
+//
+// Storage. With SENE (Section 2.4.1) only entries are stored; with DENT
+// (Section 2.4.2) only columns 0..W-O and bits 0..W-O. Rows below `rcap` go
+// to shared memory, interleaved over the pairs of the warp; deeper rows go to
+// a per-pair device scratch area. Without SENE the three GenASM edge vectors
+// I, D, M of every cell are stored instead (ablation).
+//
+// Traceback (GenASM-TB, Section 2.2.2) runs on lane G-1 of each pair. Along
+// the path every visited entry holds a 0 (Theorem 1), so when text[i] equals
+// pattern[j] the match edge is always open: a whole run of matches is taken at
+// once by comparing 32 packed bases with one XOR and a count of leading zeros.
+// Only at a mismatch (or at the end of the text) are stored bits read, and
+// substitution, insertion, deletion are tried in that order. The traceback
+// stops after W-O text or pattern characters or at the end of the pattern
+// window (Section 2.2.3), and the window slides by what it consumed.
+//
+// Bit order: bit j of a vector (j = 0 is the paper's most significant "first
+// bit") is bit 31 - (j % 32) of word j / 32. "<< 1" moves bit j+1 into bit j.
+// Bits j >= m of every entry are 0, which is exactly the shifted-in 0 of
+// Algorithm 1 for a shorter pattern window.
+#pragma once
+
+#include <stdint.h>
+
+#include "scrooge_internal.h"
+
+namespace scrooge {
+namespace kern {
+
+constexpr uint32_t kFull = 0xffffffffu;
+constexpr int kOpI = 1, kOpD = 2, kOpEq = 7, kOpX = 8;
+
+// First `bits` bits set (MSB-first); bits <= 0 -> 0, bits >= 32 -> all.
+__device__ __forceinline__ uint32_t prefix_mask(int bits) {
+    return bits <= 0 ? 0u : (bits >= 32 ? kFull : (kFull << (32 - bits)));
+}
+
+__device__ __forceinline__ uint2 load_block(const uint2 *seq, int64_t b, int64_t nblk) {
+    return (b >= 0 && b < nblk) ? __ldg(seq + b) : make_uint2(0u, 0u);
+}
+
+// Bit planes of the 32 bases starting at base `pos` (bases past the end read 0).
+__device__ __forceinline__ void load32(const uint2 *seq, int64_t nblk, int64_t pos, uint32_t &p0, uint32_t &p1) {
+    const int64_t b = pos >> 5;
+    const int r = (int)(pos & 31);
+    const uint2 a = load_block(seq, b, nblk);
+    const uint2 c = load_block(seq, b + 1, nblk);
+    p0 = __funnelshift_l(c.x, a.x, r);
+    p1 = __funnelshift_l(c.y, a.y, r);
+}
+
+template <int NW>
+__device__ __forceinline__ void shl1(const uint32_t (&x)[NW], uint32_t (&y)[NW]) {
+#pragma unroll
+    for (int w = 0; w + 1 < NW; ++w) y[w] = __funnelshift_l(x[w + 1], x[w], 1);
+    y[NW - 1] = x[NW - 1] + x[NW - 1];
+}
+
+// 32 bases of a staged window (NW+1 words per plane) starting at `pos`.
+__device__ __forceinline__ uint32_t stage_ext(const uint32_t *plane, int pos) {
+    const int w = pos >> 5;
+    return __funnelshift_l(plane[w + 1], plane[w], pos & 31);
+}
+
+struct CigarOut {
+    uint32_t *dst;
+    int64_t cap;
+    int32_t n;
+    uint32_t cur;  // pending run (len << 4 | op), 0 = none
+    int32_t edits;
+
+    __device__ __forceinline__ void emit(int op, int len) {
+        if (op != kOpEq) edits += len;
+        if (cur != 0u && (int)(cur & 15u) == op) {
+            cur += (uint32_t)len << 4;
+            return;
+        }
+        flush();
+        cur = ((uint32_t)len << 4) | (uint32_t)op;
+    }
+    __device__ __forceinline__ void flush() {
+        if (cur != 0u) {
+            if (n < cap) dst[n] = cur;
+            ++n;
+        }
+        cur = 0u;
+    }
+};
+
+template <int NW, int G, bool SENE>
+__global__ void __launch_bounds__(256) align_kernel(const AlignParams p) {
+    constexpr int WMAX = 32 * NW;
+    constexpr int C = WMAX / G;
+    constexpr int PPW = 32 / G;
+    constexpr int NV = SENE ? 1 : 3;  // stored vectors per cell
+    static_assert(C * G == WMAX && C <= 32 && 32 % G == 0, "unsupported shape");
+
+    extern __shared__ __align__(16) uint32_t smem[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int g = lane / G;
+    const int l = lane - g * G;
+    const int tbl = g * G + G - 1;  // traceback lane of this pair (owns column 0)
+    const int W = p.W, L = p.W - p.O, k = p.k;
+    const int ncol = p.ncol, sw = p.sw, rcap = p.rcap;
+    const int colbase = (G - 1 - l) * C;
+
+    uint32_t *tab = smem + (int64_t)wib * p.smem_words_per_warp;
+    uint32_t *stage = tab + p.table_words_per_warp + g * (4 * (NW + 1));
+    const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    uint32_t *spill = p.spill + (gw * PPW + g) * p.spill_words_per_pair;
+
+    // word `w` of stored vector `v` of cell (row, col) of this pair
+    auto cell_ptr = [&](int row, int col, int v) -> uint32_t * {
+        if (row < rcap) return tab + ((((int64_t)row * ncol + col) * NV + v) * sw) * PPW + g;
+        return spill + (((int64_t)(row - rcap) * ncol + col) * NV + v) * sw;
+    };
+    auto cell_stride = [&](int row) -> int { return row < rcap ? PPW : 1; };
+
+    for (int64_t base = gw * PPW; base < p.n_pairs; base += nwarps * PPW) {
+        const int64_t slot = base + g;
+        const bool live = slot < p.n_pairs;
+        const int pair = live ? (p.order ? p.order[slot] : (int)slot) : 0;
+        int n = 0, m = 0;
+        const uint2 *tseq = nullptr, *pseq = nullptr;
+        if (live) {
+            n = p.text_len[pair];
+            m = p.pat_len[pair];
+            tseq = reinterpret_cast<const uint2 *>(p.texts + (p.text_off[pair] >> 4));
+            pseq = reinterpret_cast<const uint2 *>(p.patterns + (p.pat_off[pair] >> 4));
+        }
+        const int64_t tblk = (n + 31) >> 5, pblk = (m + 31) >> 5;
+        int ti = 0, pj = 0;
+        CigarOut out;
+        out.dst = nullptr;
+        out.cap = 0;
+        out.n = 0;
+        out.cur = 0u;
+        out.edits = 0;
+        int64_t st_rows = 0, st_cells = 0;
+        int32_t st_windows = 0;
+        long long t_start = 0;
+        bool failed = false;
+        if (live && l == G - 1) {
+            const int64_t c0 = p.cigar_off[pair];
+            out.dst = p.cigar + c0;
+            out.cap = p.cigar_off[pair + 1] - c0;
+            t_start = clock64();
+        }
+        bool active = live && m > 0;
+
+        while (__any_sync(kFull, active)) {
+            const int nw = active ? min(W, n - ti) : 0;
+            const int mw = active ? min(W, m - pj) : 0;
+
+            // ---- window set-up: pattern planes, per-column masks PM[text[i]]
+            uint32_t XA[C][NW];  // X (SENE) or the insertion edge I of the next row
+            uint32_t XB[SENE ? 1 : C][NW];  // without SENE: R[i+1][d-1] of the next row
+            uint32_t PMC[C][NW];
+            {
+                uint32_t P0[NW], P1[NW], mm[NW];
+#pragma unroll
+                for (int w = 0; w < NW; ++w) {
+                    load32(pseq, active ? pblk : 0, pj + 32 * w, P0[w], P1[w]);
+                    mm[w] = prefix_mask(mw - 32 * w);
+                }
+                uint32_t T0, T1;
+                load32(tseq, active ? tblk : 0, ti + colbase, T0, T1);
+#pragma unroll
+                for (int c = 0; c < C; ++c) {
+                    const uint32_t m0 = 0u - ((T0 >> (31 - c)) & 1u);
+                    const uint32_t m1 = 0u - ((T1 >> (31 - c)) & 1u);
+                    const bool real = colbase + c < nw;
+#pragma unroll
+                    for (int w = 0; w < NW; ++w) {
+                        PMC[c][w] = real ? ((P0[w] ^ m0) | (P1[w] ^ m1)) : kFull;
+                        XA[c][w] = mm[w];
+                        if (!SENE) XB[c][w] = kFull;
+                    }
+                }
+                if (active && l == G - 1) {
+#pragma unroll
+                    for (int w = 0; w <= NW; ++w) {
+                        uint32_t a, b;
+                        load32(tseq, tblk, ti + 32 * w, a, b);
+                        stage[w] = a;
+                        stage[(NW + 1) + w] = b;
+                        load32(pseq, pblk, pj + 32 * w, a, b);
+                        stage[2 * (NW + 1) + w] = a;
+                        stage[3 * (NW + 1) + w] = b;
+                    }
+                }
+            }
+
+            // ---- GenASM-DC, rows in a pipeline over the lanes of each pair
+            bool dc_done = !active;
+            int d_opt = -1;
+            uint32_t bottom[NW];
+#pragma unroll
+            for (int w = 0; w < NW; ++w) bottom[w] = 0u;
+            for (int s = 0;; ++s) {
+                const int d = s - l;
+                uint32_t pR[NW], pS[NW];
+#pragma unroll
+                for (int w = 0; w < NW; ++w) {
+                    const uint32_t v = __shfl_up_sync(kFull, bottom[w], 1);
+                    // lane 0 starts from the right column R[n][d] = 1..1 << d
+                    pR[w] = (l == 0) ? prefix_mask(mw - d - 32 * w) : v;
+                }
+                int found = 0;
+                if (!dc_done && d >= 0 && d <= k) {
+                    shl1<NW>(pR, pS);
+#pragma unroll
+                    for (int c = C - 1; c >= 0; --c) {
+                        uint32_t R[NW], S[NW];
+                        if (SENE) {
+#pragma unroll
+                            for (int w = 0; w < NW; ++w) R[w] = XA[c][w] & (pS[w] | PMC[c][w]);
+                        } else {
+                            // row 0 has no I/D/S edges: XA = mask, XB = all ones
+                            uint32_t Dd[NW], Sd[NW];
+#pragma unroll
+                            for (int w = 0; w < NW; ++w) Dd[w] = XB[c][w];
+                            shl1<NW>(Dd, Sd);
+#pragma unroll
+                            for (int w = 0; w < NW; ++w) {
+                                const uint32_t sdm = (d == 0) ? kFull : Sd[w];
+                                R[w] = XA[c][w] & Dd[w] & sdm & (pS[w] | PMC[c][w]);
+                            }
+                        }
+                        shl1<NW>(R, S);
+                        const int i = colbase + c;
+                        if (i < ncol) {
+                            if (SENE) {
+                                uint32_t *e = cell_ptr(d, i, 0);
+                                const int st = cell_stride(d);
+#pragma unroll
+                                for (int w = 0; w < NW; ++w)
+                                    if (w < sw) e[w * st] = R[w];
+                            } else if (d > 0) {
+                                // GenASM's stored edges: I, D (S = D << 1) and M
+                                const int st = cell_stride(d);
+                                uint32_t *eI = cell_ptr(d, i, 0), *eD = cell_ptr(d, i, 1), *eM = cell_ptr(d, i, 2);
+#pragma unroll
+                                for (int w = 0; w < NW; ++w)
+                                    if (w < sw) {
+                                        eI[w * st] = XA[c][w];
+                                        eD[w * st] = XB[c][w];
+                                        eM[w * st] = pS[w] | PMC[c][w];
+                                    }
+                            }
+                        }
+                        if (SENE) {
+#pragma unroll
+                            for (int w = 0; w < NW; ++w) XA[c][w] = S[w] & pR[w] & pS[w];
+                        } else {
+#pragma unroll
+                            for (int w = 0; w < NW; ++w) {
+                                XA[c][w] = S[w];   // I of cell (i, d+1)
+                                XB[c][w] = pR[w];  // D of cell (i, d+1)
+                            }
+                        }
+#pragma unroll
+                        for (int w = 0; w < NW; ++w) {
+                            pR[w] = R[w];
+                            pS[w] = S[w];
+                        }
+                    }
+#pragma unroll
+                    for (int w = 0; w < NW; ++w) bottom[w] = pR[w];
+                    found = (l == G - 1) && ((pR[0] >> 31) == 0u);
+                }
+                const int f = __shfl_sync(kFull, found, tbl);
+                const int dl = s - (G - 1);  // row finished by the traceback lane
+                if (!dc_done) {
+                    if (f && d_opt < 0) d_opt = dl;
+                    if ((p.et && f) || dl >= k) dc_done = true;
+                }
+                if (__all_sync(kFull, dc_done)) break;
+            }
+
+            // ---- GenASM-TB on the traceback lane
+            if (active && l == G - 1) {
+                st_windows += 1;
+                if (d_opt < 0) {
+                    failed = true;
+                } else {
+                    st_rows += d_opt + 1;
+                    st_cells += (int64_t)(d_opt + 1) * nw;
+                    const uint32_t *T0s = stage, *T1s = stage + (NW + 1);
+                    const uint32_t *P0s = stage + 2 * (NW + 1), *P1s = stage + 3 * (NW + 1);
+                    // bit `bit` of entry R[col][row] (SENE) -- the right column is implicit
+                    auto entry_bit = [&](int col, int row, int bit) -> uint32_t {
+                        if (bit >= mw) return 0u;
+                        if (col >= nw) return bit < mw - row ? 1u : 0u;
+                        const uint32_t v = cell_ptr(row, col, 0)[(bit >> 5) * cell_stride(row)];
+                        return (v >> (31 - (bit & 31))) & 1u;
+                    };
+                    // bit of edge vector v (0 = I, 1 = D) of cell (col, row), row >= 1
+                    auto edge_bit = [&](int col, int row, int v, int bit) -> uint32_t {
+                        if (bit >= mw) return 0u;
+                        if (col >= nw) {  // right column: I = R[n][d-1] << 1
+                            const int b = bit + 1;
+                            return (b < mw && b < mw - (row - 1)) ? 1u : 0u;
+                        }
+                        const uint32_t w = cell_ptr(row, col, v)[(bit >> 5) * cell_stride(row)];
+                        return (w >> (31 - (bit & 31))) & 1u;
+                    };
+                    int i = 0, j = 0, d = d_opt;
+                    while (j < mw && i < L && j < L) {
+                        const int lim = min(min(nw - i, mw - j), min(L - i, L - j));
+                        if (lim > 0) {
+                            int run = 0;
+                            for (;;) {
+                                const uint32_t x = (stage_ext(T0s, i + run) ^ stage_ext(P0s, j + run)) |
+                                                   (stage_ext(T1s, i + run) ^ stage_ext(P1s, j + run));
+                                const int z = __clz(x);
+                                run += z;
+                                if (z < 32 || run >= lim) break;
+                            }
+                            run = min(run, lim);
+                            if (run > 0) {
+                                out.emit(kOpEq, run);
+                                i += run;
+                                j += run;
+                                if (!(j < mw && i < L && j < L)) break;
+                            }
+                        }
+                        if (d <= 0) {  // no edge can leave row 0 here (Theorem 1)
+                            atomicOr(p.status, 1);
+                            failed = true;
+                            break;
+                        }
+                        const bool tx = i < nw;
+                        uint32_t bS, bI, bD;
+                        if (SENE) {
+                            bS = tx ? entry_bit(i + 1, d - 1, j + 1) : 1u;
+                            bI = entry_bit(i, d - 1, j + 1);
+                            bD = tx ? entry_bit(i + 1, d - 1, j) : 1u;
+                        } else {
+                            bS = tx ? edge_bit(i, d, 1, j + 1) : 1u;
+                            bI = edge_bit(i, d, 0, j);
+                            bD = tx ? edge_bit(i, d, 1, j) : 1u;
+                        }
+                        if (tx && bS == 0u) {
+                            out.emit(kOpX, 1);
+                            ++i;
+                            ++j;
+                            --d;
+                        } else if (bI == 0u) {
+                            out.emit(kOpI, 1);
+                            ++j;
+                            --d;
+                        } else if (tx && bD == 0u) {
+                            out.emit(kOpD, 1);
+                            ++i;
+                            --d;
+                        } else {
+                            atomicOr(p.status, 1);
+                            failed = true;
+                            break;
+                        }
+                    }
+                    ti += i;
+                    pj += j;
+                }
+                if (failed || pj >= m) {
+                    active = false;
+                    out.flush();
+                    p.edit_counts[pair] = failed ? -1 : out.edits;
+                    p.text_consumed[pair] = failed ? 0 : ti;
+                    p.cigar_lens[pair] = failed ? 0 : (out.n > out.cap ? -1 : out.n);
+                    if (p.st_windows) p.st_windows[pair] = st_windows;
+                    if (p.st_rows) p.st_rows[pair] = st_rows;
+                    if (p.st_cells) p.st_cells[pair] = st_cells;
+                    if (p.st_cycles) p.st_cycles[pair] = clock64() - t_start;
+                }
+            }
+            ti = __shfl_sync(kFull, ti, tbl);
+            pj = __shfl_sync(kFull, pj, tbl);
+            active = __shfl_sync(kFull, (int)active, tbl) != 0;
+            __syncwarp();
+        }
+        if (live && m == 0 && l == G - 1) {
+            p.edit_counts[pair] = 0;
+            p.text_consumed[pair] = 0;
+            p.cigar_lens[pair] = 0;
+            if (p.st_windows) p.st_windows[pair] = 0;
+            if (p.st_rows) p.st_rows[pair] = 0;
+            if (p.st_cells) p.st_cells[pair] = 0;
+            if (p.st_cycles) p.st_cycles[pair] = 0;
+        }
+    }
+}
+
+}  // namespace kern
+}  // namespace scrooge

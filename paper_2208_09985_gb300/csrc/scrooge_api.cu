@@ -1,0 +1,436 @@
+// C ABI of the library: contexts, argument checks, packing and launches.
+// The operations are described in include/scrooge.h.
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/scrooge.h"
+#include "scrooge_internal.h"
+
+namespace scrooge {
+cudaError_t launch_align_w32(const AlignParams &, int, bool, int, int, size_t, cudaStream_t);
+cudaError_t launch_align_w64(const AlignParams &, int, bool, int, int, size_t, cudaStream_t);
+cudaError_t launch_align_w128(const AlignParams &, int, bool, int, int, size_t, cudaStream_t);
+cudaError_t occupancy_w32(int, bool, int, size_t, int *);
+cudaError_t occupancy_w64(int, bool, int, size_t, int *);
+cudaError_t occupancy_w128(int, bool, int, size_t, int *);
+
+bool align_supported(int words, int lanes) {
+    switch (words) {
+        case 1: return lanes == 1 || lanes == 2 || lanes == 4;
+        case 2: return lanes == 2 || lanes == 4 || lanes == 8;
+        case 4: return lanes == 8 || lanes == 16;
+        default: return false;
+    }
+}
+}  // namespace scrooge
+
+using namespace scrooge;
+
+namespace {
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+struct KernelConfig {
+    int lanes, rows, wpb;
+};
+
+}  // namespace
+
+struct scrooge_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int sm_count = 0;
+    size_t smem_optin = 0;
+    std::string err;
+    KernelConfig kcfg[3] = {{2, 16, 2}, {4, 12, 2}, {8, 12, 2}};  // words 1, 2, 4
+    int fail_allocs = 0;  // testing hook: fail the next N device allocations
+    DevBuf spill, status;
+    DevBuf in_text, in_pat, in_toff, in_tlen, in_poff, in_plen, in_coff;
+    DevBuf out_ec, out_tc, out_cig, out_cl;
+    int32_t *st_windows = nullptr;
+    int64_t *st_rows = nullptr, *st_cells = nullptr, *st_cycles = nullptr;
+};
+
+namespace {
+
+int fail(scrooge_ctx *c, int code, const char *fmt, ...) {
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        c->err = buf;
+    }
+    return code;
+}
+
+int cuda_fail(scrooge_ctx *c, cudaError_t e, const char *what) {
+    return fail(c, SCROOGE_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+int kcfg_index(int words) { return words == 1 ? 0 : (words == 2 ? 1 : (words == 4 ? 2 : -1)); }
+
+// Grow a device buffer to at least `bytes` (contents are not kept).
+int ensure(scrooge_ctx *c, DevBuf &b, size_t bytes, const char *what) {
+    if (bytes == 0) bytes = 16;
+    if (b.bytes >= bytes) return SCROOGE_OK;
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+    if (c->fail_allocs > 0) {
+        c->fail_allocs -= 1;
+        return fail(c, SCROOGE_E_NOMEM, "device allocation of %zu bytes for %s failed (injected)", bytes, what);
+    }
+    size_t sz = bytes + bytes / 8;  // some headroom for growing batches
+    cudaError_t e = cudaMalloc(&b.p, sz);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, SCROOGE_E_NOMEM, "device allocation of %zu bytes for %s failed: %s", sz, what,
+                    cudaGetErrorString(e));
+    }
+    b.bytes = sz;
+    return SCROOGE_OK;
+}
+
+void release(DevBuf &b) {
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+int words_for(int W) { return W <= 32 ? 1 : (W <= 64 ? 2 : 4); }
+
+}  // namespace
+
+extern "C" {
+
+int scrooge_create(scrooge_ctx **out, int cuda_device, void *cuda_stream) {
+    if (!out) return SCROOGE_E_INVAL;
+    *out = nullptr;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return SCROOGE_E_CUDA;
+    }
+    if (cuda_device < 0 || cuda_device >= ndev) return SCROOGE_E_INVAL;
+    scrooge_ctx *c = new (std::nothrow) scrooge_ctx();
+    if (!c) return SCROOGE_E_NOMEM;
+    c->device = cuda_device;
+    c->stream = (cudaStream_t)cuda_stream;
+    if ((e = cudaSetDevice(cuda_device)) != cudaSuccess) {
+        delete c;
+        return SCROOGE_E_CUDA;
+    }
+    cudaDeviceProp prop;
+    if ((e = cudaGetDeviceProperties(&prop, cuda_device)) != cudaSuccess) {
+        delete c;
+        return SCROOGE_E_CUDA;
+    }
+    c->sm_count = prop.multiProcessorCount;
+    c->smem_optin = prop.sharedMemPerBlockOptin;
+    *out = c;
+    return SCROOGE_OK;
+}
+
+int scrooge_destroy(scrooge_ctx *c) {
+    if (!c) return SCROOGE_OK;
+    cudaSetDevice(c->device);
+    DevBuf *all[] = {&c->spill, &c->status, &c->in_text, &c->in_pat, &c->in_toff, &c->in_tlen, &c->in_poff,
+                     &c->in_plen, &c->in_coff, &c->out_ec, &c->out_tc, &c->out_cig, &c->out_cl};
+    for (DevBuf *b : all) release(*b);
+    delete c;
+    return SCROOGE_OK;
+}
+
+const char *scrooge_last_error(const scrooge_ctx *c) { return c ? c->err.c_str() : "no context"; }
+
+int scrooge_set_stream(scrooge_ctx *c, void *cuda_stream) {
+    if (!c) return SCROOGE_E_INVAL;
+    c->stream = (cudaStream_t)cuda_stream;
+    return SCROOGE_OK;
+}
+
+int scrooge_debug_fail_next_allocs(scrooge_ctx *c, int32_t count) {
+    if (!c || count < 0) return SCROOGE_E_INVAL;
+    c->fail_allocs = count;
+    return SCROOGE_OK;
+}
+
+int64_t scrooge_packed_words(int64_t n_bases) {
+    if (n_bases < 0) return -1;
+    return ((n_bases + 63) / 64) * 4;
+}
+
+int scrooge_pack_2bit(const uint8_t *seqs, const int64_t *offsets, int32_t n_seqs, int ascii, uint32_t *packed,
+                      int64_t packed_words, int64_t *packed_offsets, int32_t *lengths) {
+    if (n_seqs < 0 || (n_seqs > 0 && (!seqs || !offsets || !packed || !packed_offsets || !lengths)))
+        return SCROOGE_E_INVAL;
+    std::vector<int64_t> wstart((size_t)n_seqs + 1, 0);
+    for (int32_t s = 0; s < n_seqs; ++s) {
+        const int64_t len = offsets[s + 1] - offsets[s];
+        if (len < 0 || len > INT32_MAX) return SCROOGE_E_INVAL;
+        wstart[s + 1] = wstart[s] + scrooge_packed_words(len);
+    }
+    if (wstart[n_seqs] > packed_words) return SCROOGE_E_INVAL;
+    uint8_t code_of[256];
+    memset(code_of, 255, sizeof code_of);
+    if (ascii) {
+        const char *a = "ACGT", *b = "acgt";
+        for (int x = 0; x < 4; ++x) code_of[(uint8_t)a[x]] = code_of[(uint8_t)b[x]] = (uint8_t)x;
+    } else {
+        for (int x = 0; x < 4; ++x) code_of[x] = (uint8_t)x;
+    }
+    int bad = 0;
+    auto work = [&](int32_t lo, int32_t hi, int *badflag) {
+        for (int32_t s = lo; s < hi; ++s) {
+            const uint8_t *q = seqs + offsets[s];
+            const int64_t len = offsets[s + 1] - offsets[s];
+            uint32_t *dst = packed + wstart[s];
+            const int64_t nw = wstart[s + 1] - wstart[s];
+            for (int64_t blk = 0; blk < nw / 2; ++blk) {
+                uint32_t p0 = 0, p1 = 0;
+                for (int t = 0; t < 32; ++t) {
+                    const int64_t pos = blk * 32 + t;
+                    if (pos >= len) break;
+                    const uint8_t c = code_of[q[pos]];
+                    if (c > 3) {
+                        *badflag = 1;
+                        return;
+                    }
+                    p0 |= (uint32_t)(c & 1u) << (31 - t);
+                    p1 |= (uint32_t)((c >> 1) & 1u) << (31 - t);
+                }
+                dst[2 * blk] = p0;
+                dst[2 * blk + 1] = p1;
+            }
+            packed_offsets[s] = wstart[s] * 16;
+            lengths[s] = (int32_t)len;
+        }
+    };
+    const int64_t total = offsets[n_seqs] - offsets[0];
+    unsigned nth = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    if (total < (1 << 22) || n_seqs < 64) nth = 1;
+    std::vector<std::thread> th;
+    std::vector<int> bads(nth, 0);
+    const int32_t per = (n_seqs + (int32_t)nth - 1) / (int32_t)nth;
+    for (unsigned t = 0; t < nth; ++t) {
+        const int32_t lo = (int32_t)t * per, hi = std::min(n_seqs, lo + per);
+        if (lo >= hi) break;
+        if (nth == 1) work(lo, hi, &bads[t]);
+        else th.emplace_back(work, lo, hi, &bads[t]);
+    }
+    for (auto &x : th) x.join();
+    for (int b : bads) bad |= b;
+    return bad ? SCROOGE_E_INVAL : SCROOGE_OK;
+}
+
+int scrooge_set_kernel_config(scrooge_ctx *c, int32_t words, int32_t lanes, int32_t rows, int32_t wpb) {
+    if (!c) return SCROOGE_E_INVAL;
+    const int ix = kcfg_index(words);
+    if (ix < 0 || !align_supported(words, lanes) || rows < 1 || rows > 129 || wpb < 1 || wpb > 8)
+        return fail(c, SCROOGE_E_INVAL, "unsupported kernel config words=%d lanes=%d rows=%d warps=%d", words,
+                    lanes, rows, wpb);
+    c->kcfg[ix] = {lanes, rows, wpb};
+    return SCROOGE_OK;
+}
+
+int scrooge_get_kernel_config(const scrooge_ctx *c, int32_t words, int32_t *lanes, int32_t *rows, int32_t *wpb) {
+    if (!c) return SCROOGE_E_INVAL;
+    const int ix = kcfg_index(words);
+    if (ix < 0) return SCROOGE_E_INVAL;
+    if (lanes) *lanes = c->kcfg[ix].lanes;
+    if (rows) *rows = c->kcfg[ix].rows;
+    if (wpb) *wpb = c->kcfg[ix].wpb;
+    return SCROOGE_OK;
+}
+
+int scrooge_set_stats(scrooge_ctx *c, int32_t *windows, int64_t *rows, int64_t *cells, int64_t *cycles) {
+    if (!c) return SCROOGE_E_INVAL;
+    c->st_windows = windows;
+    c->st_rows = rows;
+    c->st_cells = cells;
+    c->st_cycles = cycles;
+    return SCROOGE_OK;
+}
+
+int scrooge_align_batch(scrooge_ctx *c, const uint32_t *texts, const int64_t *text_offsets,
+                        const int32_t *text_lengths, const uint32_t *patterns, const int64_t *pattern_offsets,
+                        const int32_t *pattern_lengths, int32_t n_pairs, int32_t W, int32_t O, int32_t k,
+                        uint32_t flags, int32_t *edit_counts, int32_t *text_consumed, uint32_t *cigar,
+                        const int64_t *cigar_offsets, int32_t *cigar_lens) {
+    if (!c) return SCROOGE_E_INVAL;
+    c->err.clear();
+    if (n_pairs < 0) return fail(c, SCROOGE_E_INVAL, "n_pairs < 0");
+    if (W < 1 || W > 128) return fail(c, SCROOGE_E_INVAL, "W=%d outside 1..128", W);
+    if (O < 0 || O >= W) return fail(c, SCROOGE_E_INVAL, "O=%d outside 0..W-1", O);
+    if (k < 0 || k > W) return fail(c, SCROOGE_E_INVAL, "k=%d outside 0..W", k);
+    if (flags & (SCROOGE_PERSISTENT | SCROOGE_LEARNED | SCROOGE_GRAPH))
+        return fail(c, SCROOGE_E_INVAL, "scheduling flags are not available in this build");
+    if (n_pairs == 0) return SCROOGE_OK;
+    if (!texts || !text_offsets || !text_lengths || !patterns || !pattern_offsets || !pattern_lengths ||
+        !edit_counts || !text_consumed || !cigar_offsets || !cigar_lens)
+        return fail(c, SCROOGE_E_INVAL, "null pointer argument");
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+    const bool dev = (flags & SCROOGE_DEVICE_PTRS) != 0;
+    cudaStream_t st = c->stream;
+    int rc;
+
+    AlignParams p;
+    memset(&p, 0, sizeof p);
+    p.n_pairs = n_pairs;
+    p.W = W;
+    p.O = O;
+    p.k = k;
+    if (dev) {
+        p.texts = texts;
+        p.text_off = text_offsets;
+        p.text_len = text_lengths;
+        p.patterns = patterns;
+        p.pat_off = pattern_offsets;
+        p.pat_len = pattern_lengths;
+        p.cigar_off = cigar_offsets;
+        p.edit_counts = edit_counts;
+        p.text_consumed = text_consumed;
+        p.cigar = cigar;
+        p.cigar_lens = cigar_lens;
+    } else {
+        // host pointers: check the layout, then stage everything on the device
+        int64_t text_words = 0, pat_words = 0;
+        for (int32_t q = 0; q < n_pairs; ++q) {
+            const int64_t to = text_offsets[q], po = pattern_offsets[q];
+            const int32_t tl = text_lengths[q], pl = pattern_lengths[q];
+            if (to < 0 || po < 0 || (to & 63) || (po & 63) || tl < 0 || pl < 0)
+                return fail(c, SCROOGE_E_INVAL, "pair %d: offsets must be >= 0 multiples of 64, lengths >= 0", q);
+            text_words = std::max(text_words, to / 16 + scrooge_packed_words(tl));
+            pat_words = std::max(pat_words, po / 16 + scrooge_packed_words(pl));
+            if (cigar_offsets[q + 1] < cigar_offsets[q])
+                return fail(c, SCROOGE_E_INVAL, "cigar_offsets must be non-decreasing (pair %d)", q);
+        }
+        if (cigar_offsets[0] < 0) return fail(c, SCROOGE_E_INVAL, "cigar_offsets[0] < 0");
+        const int64_t cig_total = cigar_offsets[n_pairs];
+        if (cig_total > 0 && !cigar) return fail(c, SCROOGE_E_INVAL, "null cigar buffer");
+        const size_t np = (size_t)n_pairs;
+        if ((rc = ensure(c, c->in_text, text_words * 4, "texts")) ||
+            (rc = ensure(c, c->in_pat, pat_words * 4, "patterns")) ||
+            (rc = ensure(c, c->in_toff, np * 8, "text offsets")) ||
+            (rc = ensure(c, c->in_tlen, np * 4, "text lengths")) ||
+            (rc = ensure(c, c->in_poff, np * 8, "pattern offsets")) ||
+            (rc = ensure(c, c->in_plen, np * 4, "pattern lengths")) ||
+            (rc = ensure(c, c->in_coff, (np + 1) * 8, "cigar offsets")) ||
+            (rc = ensure(c, c->out_ec, np * 4, "edit counts")) || (rc = ensure(c, c->out_tc, np * 4, "text consumed")) ||
+            (rc = ensure(c, c->out_cig, (size_t)std::max<int64_t>(cig_total, 1) * 4, "cigar")) ||
+            (rc = ensure(c, c->out_cl, np * 4, "cigar lengths")))
+            return rc;
+        struct {
+            void *d;
+            const void *h;
+            size_t b;
+        } cp[] = {{c->in_text.p, texts, (size_t)text_words * 4},   {c->in_pat.p, patterns, (size_t)pat_words * 4},
+                  {c->in_toff.p, text_offsets, np * 8},            {c->in_tlen.p, text_lengths, np * 4},
+                  {c->in_poff.p, pattern_offsets, np * 8},         {c->in_plen.p, pattern_lengths, np * 4},
+                  {c->in_coff.p, cigar_offsets, (np + 1) * 8}};
+        for (auto &x : cp)
+            if (x.b && (e = cudaMemcpyAsync(x.d, x.h, x.b, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+                return cuda_fail(c, e, "host-to-device copy");
+        p.texts = (const uint32_t *)c->in_text.p;
+        p.patterns = (const uint32_t *)c->in_pat.p;
+        p.text_off = (const int64_t *)c->in_toff.p;
+        p.text_len = (const int32_t *)c->in_tlen.p;
+        p.pat_off = (const int64_t *)c->in_poff.p;
+        p.pat_len = (const int32_t *)c->in_plen.p;
+        p.cigar_off = (const int64_t *)c->in_coff.p;
+        p.edit_counts = (int32_t *)c->out_ec.p;
+        p.text_consumed = (int32_t *)c->out_tc.p;
+        p.cigar = (uint32_t *)c->out_cig.p;
+        p.cigar_lens = (int32_t *)c->out_cl.p;
+    }
+
+    // kernel shape
+    const int words = words_for(W);
+    const KernelConfig kc = c->kcfg[kcfg_index(words)];
+    const int G = kc.lanes, PPW = 32 / G;
+    const int L = W - O;
+    const bool sene = !(flags & SCROOGE_NO_SENE);
+    const bool dent = !(flags & SCROOGE_NO_DENT);
+    p.et = (flags & SCROOGE_NO_ET) ? 0 : 1;
+    p.sene = sene ? 1 : 0;
+    p.ncol = dent ? std::min(L + 1, W) : W;
+    p.sw = dent ? std::min((L + 1 + 31) / 32, words) : words;
+    int rcap = std::min(kc.rows, k + 1);
+    const int stage = stage_words_per_warp(words, PPW);
+    int wpb = kc.wpb;
+    // keep the block's shared memory within the opt-in limit
+    while (rcap > 1 && (size_t)wpb * (table_words_per_warp(rcap, p.ncol, p.sw, p.sene, PPW) + stage) * 4 > c->smem_optin)
+        --rcap;
+    while (wpb > 1 && (size_t)wpb * (table_words_per_warp(rcap, p.ncol, p.sw, p.sene, PPW) + stage) * 4 > c->smem_optin)
+        --wpb;
+    p.rcap = rcap;
+    p.table_words_per_warp = (int32_t)table_words_per_warp(rcap, p.ncol, p.sw, p.sene, PPW);
+    p.smem_words_per_warp = p.table_words_per_warp + stage;
+    const size_t smem = (size_t)wpb * p.smem_words_per_warp * 4;
+    int per_sm = 0;
+    e = words == 1 ? occupancy_w32(G, sene, wpb, smem, &per_sm)
+                   : (words == 2 ? occupancy_w64(G, sene, wpb, smem, &per_sm) : occupancy_w128(G, sene, wpb, smem, &per_sm));
+    if (e != cudaSuccess) return cuda_fail(c, e, "occupancy query");
+    if (per_sm < 1) return fail(c, SCROOGE_E_INVAL, "kernel config does not fit on an SM (smem %zu B)", smem);
+    const int64_t groups = ((int64_t)n_pairs + PPW - 1) / PPW;
+    const int64_t want_blocks = (groups + wpb - 1) / wpb;
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(want_blocks, (int64_t)per_sm * c->sm_count));
+    const int spill_rows = std::max(0, k + 1 - rcap);
+    p.spill_words_per_pair = (int64_t)spill_rows * p.ncol * p.sw * (sene ? 1 : 3);
+    const size_t spill_bytes = (size_t)blocks * wpb * PPW * (size_t)std::max<int64_t>(p.spill_words_per_pair, 1) * 4;
+    if ((rc = ensure(c, c->spill, spill_bytes, "DP row scratch")) || (rc = ensure(c, c->status, 64, "status")))
+        return rc;
+    p.spill = (uint32_t *)c->spill.p;
+    p.status = (int32_t *)c->status.p;
+    p.st_windows = c->st_windows;
+    p.st_rows = c->st_rows;
+    p.st_cells = c->st_cells;
+    p.st_cycles = c->st_cycles;
+    if ((e = cudaMemsetAsync(p.status, 0, 4, st)) != cudaSuccess) return cuda_fail(c, e, "status reset");
+    e = words == 1 ? launch_align_w32(p, G, sene, wpb, blocks, smem, st)
+                   : (words == 2 ? launch_align_w64(p, G, sene, wpb, blocks, smem, st)
+                                 : launch_align_w128(p, G, sene, wpb, blocks, smem, st));
+    if (e != cudaSuccess) return cuda_fail(c, e, "alignment kernel launch");
+
+    const bool sync = !dev || (flags & SCROOGE_SYNC);
+    int32_t status_h = 0;
+    if (sync) {
+        if ((e = cudaMemcpyAsync(&status_h, p.status, 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+            return cuda_fail(c, e, "status copy");
+    }
+    if (!dev) {
+        const size_t np = (size_t)n_pairs;
+        const int64_t cig_total = cigar_offsets[n_pairs];
+        struct {
+            void *h;
+            const void *d;
+            size_t b;
+        } cp[] = {{edit_counts, p.edit_counts, np * 4},
+                  {text_consumed, p.text_consumed, np * 4},
+                  {cigar_lens, p.cigar_lens, np * 4},
+                  {cigar, p.cigar, (size_t)cig_total * 4}};
+        for (auto &x : cp)
+            if (x.b && (e = cudaMemcpyAsync(x.h, x.d, x.b, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+                return cuda_fail(c, e, "device-to-host copy");
+    }
+    if (sync) {
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(c, e, "stream synchronise");
+        if (status_h != 0) return fail(c, SCROOGE_E_INTERNAL, "kernel status %d (traceback found no open edge)", status_h);
+    }
+    return SCROOGE_OK;
+}
+
+}  // extern "C"

@@ -22,12 +22,14 @@ below stand in for them with the same length and error structure:
 * ``tiny_windows`` -- a 110 bp text with a 100 bp pattern at 2 % edits.
 
 Generation is chunked: pairs are produced in chunks of ``CHUNK`` pairs, each
-chunk from its own ``numpy.random.default_rng([seed, chunk_index])`` stream, so
-the first N pairs of any batch are identical whatever the total size asked for.
+chunk from its own ``numpy.random.default_rng([seed, chunk_index])`` stream and
+always drawn in full before it is cut, so the first N pairs of any batch are
+identical whatever the total size asked for.
 That lets a test regenerate a prefix of a million-pair workload cheaply.
 """
 from __future__ import annotations
 
+import os
 from dataclasses import dataclass
 
 import numpy as np
@@ -135,11 +137,16 @@ def mutate(rng: np.random.Generator, src: np.ndarray, src_off: np.ndarray, rate,
     total = int(src_off[-1])
     if total == 0:
         return np.zeros(0, np.uint8), np.zeros(n + 1, np.int64)
-    pid = np.repeat(np.arange(n), lens)
-    rate = np.broadcast_to(np.asarray(rate, dtype=np.float64), (n,))
+    src = np.asarray(src, dtype=np.uint8)
     mean_bases = (1.0 - homopolymer_frac) + homopolymer_frac * (1 + max_hp) / 2.0
-    q = rate[pid] / mean_bases
-    ev = np.flatnonzero(rng.random(total) < q)
+    rate = np.asarray(rate, dtype=np.float64)
+    u = rng.random(total, dtype=np.float32)
+    if rate.ndim == 0:
+        ev = np.flatnonzero(u < np.float32(rate / mean_bases))
+    else:
+        q = (np.broadcast_to(rate, (n,)) / mean_bases).astype(np.float32)
+        ev = np.flatnonzero(u < np.repeat(q, lens))
+    del u
     nev = ev.shape[0]
     hp = rng.random(nev) < homopolymer_frac
     kind = rng.random(nev)
@@ -148,10 +155,11 @@ def mutate(rng: np.random.Generator, src: np.ndarray, src_off: np.ndarray, rate,
     new_base = rng.integers(0, 4, nev).astype(np.uint8)
     sub_shift = rng.integers(1, 4, nev).astype(np.uint8)
 
-    pre_count = np.zeros(total, dtype=np.int64)
-    pre_base = np.zeros(total, dtype=np.uint8)
-    main_count = np.ones(total, dtype=np.int64)
-    main_base = src.astype(np.uint8).copy()
+    # per source position: bases emitted before it (insertions) and whether it is kept
+    pre_count = np.zeros(nev, dtype=np.int64)  # only event positions can have insertions
+    pre_base = np.zeros(nev, dtype=np.uint8)
+    keep = np.ones(total, dtype=bool)
+    main_base = src.copy()
 
     plain = ~hp
     sub = plain & (kind < 0.5)
@@ -159,15 +167,13 @@ def mutate(rng: np.random.Generator, src: np.ndarray, src_off: np.ndarray, rate,
     dele = plain & (kind >= 0.75)
     s = ev[sub]
     main_base[s] = (src[s] + sub_shift[sub]) % 4
-    s = ev[ins]
-    pre_count[s] = 1
-    pre_base[s] = new_base[ins]
-    main_count[ev[dele]] = 0
+    pre_count[ins] = 1
+    pre_base[ins] = new_base[ins]
+    keep[ev[dele]] = False
     # homopolymer insertions: r extra copies of the current base before it
     hi = hp & hp_ins
-    s = ev[hi]
-    pre_count[s] = rlen[hi]
-    pre_base[s] = src[s]
+    pre_count[hi] = rlen[hi]
+    pre_base[hi] = src[ev[hi]]
     # homopolymer deletions: the current base and up to r-1 more of its run
     hd = hp & ~hp_ins
     if hd.any():
@@ -175,21 +181,30 @@ def mutate(rng: np.random.Generator, src: np.ndarray, src_off: np.ndarray, rate,
         is_start[1:] = src[1:] != src[:-1]
         is_start[src_off[:-1][lens > 0]] = True
         starts = np.flatnonzero(is_start)
-        run_id = np.cumsum(is_start) - 1
-        run_end = np.append(starts[1:], total)[run_id]
         s = ev[hd]
-        dl = np.minimum(rlen[hd], run_end[s] - s)
-        diff = np.zeros(total + 1, dtype=np.int64)
+        nxt = np.searchsorted(starts, s, side="right")
+        run_end = np.where(nxt < starts.size, starts[np.minimum(nxt, starts.size - 1)], total)
+        dl = np.minimum(rlen[hd], run_end - s)
+        diff = np.zeros(total + 1, dtype=np.int32)
         np.add.at(diff, s, 1)
         np.add.at(diff, s + dl, -1)
-        gone = np.cumsum(diff[:-1]) > 0
-        main_count[gone] = 0
-        pre_count[gone] = 0
-    vals = np.stack([pre_base, main_base], 1).ravel()
-    cnts = np.stack([pre_count, main_count], 1).ravel()
-    out = np.repeat(vals, cnts)
-    per = np.bincount(pid, weights=pre_count + main_count, minlength=n).astype(np.int64)
-    return out.astype(np.uint8), _offsets(per)
+        keep &= np.cumsum(diff[:-1]) == 0
+    # an insertion before a deleted base is dropped with it
+    pre_count[~keep[ev]] = 0
+    cnt = keep.astype(np.int64)
+    np.add.at(cnt, ev, pre_count)
+    ends = np.cumsum(cnt)
+    out = np.empty(int(ends[-1]) if total else 0, dtype=np.uint8)
+    out[ends[keep] - 1] = main_base[keep]
+    has_pre = pre_count > 0
+    if has_pre.any():
+        first = ends[ev[has_pre]] - cnt[ev[has_pre]]
+        k = pre_count[has_pre]
+        pos = np.repeat(first, k) + (np.arange(int(k.sum())) - np.repeat(np.cumsum(k) - k, k))
+        out[pos] = np.repeat(pre_base[has_pre], k)
+    per = np.add.reduceat(cnt, src_off[:-1]) if n else np.zeros(0, np.int64)
+    per = np.where(lens > 0, per, 0)
+    return out, _offsets(per.astype(np.int64))
 
 
 def _random_codes(rng, lengths):
@@ -197,14 +212,34 @@ def _random_codes(rng, lengths):
     return rng.integers(0, 4, int(lengths.sum()), dtype=np.uint8), _offsets(lengths)
 
 
-def _chunked(seed: int, n_pairs: int, make_chunk, name: str) -> PairBatch:
-    parts = []
-    for c in range((n_pairs + CHUNK - 1) // CHUNK):
-        cnt = min(CHUNK, n_pairs - c * CHUNK)
-        parts.append(make_chunk(np.random.default_rng([seed, c]), cnt))
-    if not parts:
+def _run_chunk(args):
+    """One full chunk from its own stream, cut to the first ``cnt`` pairs."""
+    fn, seed, c, cnt, kw = args
+    b = globals()[fn](np.random.default_rng([seed, c]), CHUNK, **kw)
+    if cnt < CHUNK:
+        b = PairBatch(b.texts[: b.text_off[cnt]], b.text_off[: cnt + 1].copy(),
+                      b.patterns[: b.pattern_off[cnt]], b.pattern_off[: cnt + 1].copy())
+    return b
+
+
+def _chunked(seed: int, n_pairs: int, fn: str, name: str, **kw) -> PairBatch:
+    """Generate ``n_pairs`` pairs chunk by chunk with the module function ``fn``.
+
+    Large batches are generated by a pool of spawned worker processes; the
+    result does not depend on how many workers run.
+    """
+    jobs = [(fn, seed, c, min(CHUNK, n_pairs - c * CHUNK), kw) for c in range((n_pairs + CHUNK - 1) // CHUNK)]
+    if not jobs:
         z = np.zeros(1, np.int64)
         return PairBatch(np.zeros(0, np.uint8), z, np.zeros(0, np.uint8), z.copy(), name)
+    workers = min(len(jobs), os.cpu_count() or 1, 16)
+    if workers >= 4 and len(jobs) >= 8:
+        import multiprocessing as mp
+        from concurrent.futures import ProcessPoolExecutor
+        with ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
+            parts = list(ex.map(_run_chunk, jobs))
+    else:
+        parts = [_run_chunk(j) for j in jobs]
     return concat(parts, name)
 
 
@@ -224,62 +259,73 @@ def _with_padding(rng, src, src_off, pad_frac):
     return out, toff
 
 
+def _chunk_tiny(rng, cnt):
+    t, toff = _random_codes(rng, np.full(cnt, 110))
+    src = t.reshape(cnt, 110)[:, :100].ravel()
+    q, qoff = mutate(rng, src, _offsets(np.full(cnt, 100)), 0.02)
+    return PairBatch(t, toff, q, qoff)
+
+
 def tiny_windows(n_pairs: int = 1000, seed: int = 0) -> PairBatch:
     """110 bp uniform text; pattern = its first 100 bp with 2 % edits."""
-    def chunk(rng, cnt):
-        t, toff = _random_codes(rng, np.full(cnt, 110))
-        src = t.reshape(cnt, 110)[:, :100].ravel()
-        q, qoff = mutate(rng, src, _offsets(np.full(cnt, 100)), 0.02)
-        return PairBatch(t, toff, q, qoff)
-    return _chunked(seed, n_pairs, chunk, "tiny_windows")
+    return _chunked(seed, n_pairs, "_chunk_tiny", "tiny_windows")
+
+
+def _chunk_short(rng, cnt):
+    L = rng.integers(100, 251, cnt)
+    src, soff = _random_codes(rng, L)
+    t, toff = _with_padding(rng, src, soff, 0.05)
+    q, qoff = mutate(rng, src, soff, 0.05)
+    return PairBatch(t, toff, q, qoff)
 
 
 def short_reads(n_pairs: int = 1_000_000, seed: int = 1) -> PairBatch:
     """L ~ U{100..250}; text = L-bp source + 5 % padding; pattern = source at 5 % edits."""
-    def chunk(rng, cnt):
-        L = rng.integers(100, 251, cnt)
-        src, soff = _random_codes(rng, L)
-        t, toff = _with_padding(rng, src, soff, 0.05)
-        q, qoff = mutate(rng, src, soff, 0.05)
-        return PairBatch(t, toff, q, qoff)
-    return _chunked(seed, n_pairs, chunk, "short_reads")
+    return _chunked(seed, n_pairs, "_chunk_short", "short_reads")
+
+
+def _chunk_long(rng, cnt, text_len, pattern_len, rate):
+    t, toff = _random_codes(rng, np.full(cnt, text_len))
+    q, qoff = mutate(rng, t, toff, rate, homopolymer_frac=0.2)
+    ql = np.diff(qoff)
+    if (ql < pattern_len).any():
+        raise RuntimeError("mutated read shorter than the requested pattern length")
+    keep = np.repeat(qoff[:-1], pattern_len) + np.tile(np.arange(pattern_len), cnt)
+    return PairBatch(t, toff, q[keep], _offsets(np.full(cnt, pattern_len)))
 
 
 def long_reads(n_pairs: int = 100_000, seed: int = 2, text_len: int = 10_500,
                pattern_len: int = 10_000, rate: float = 0.10) -> PairBatch:
     """10.5 kbp text; pattern = text at 10 % edits (20 % homopolymer indels), cut to 10 kbp."""
-    def chunk(rng, cnt):
-        t, toff = _random_codes(rng, np.full(cnt, text_len))
-        q, qoff = mutate(rng, t, toff, rate, homopolymer_frac=0.2)
-        ql = np.diff(qoff)
-        if (ql < pattern_len).any():
-            raise RuntimeError("mutated read shorter than the requested pattern length")
-        keep = np.repeat(qoff[:-1], pattern_len) + np.tile(np.arange(pattern_len), cnt)
-        return PairBatch(t, toff, q[keep], _offsets(np.full(cnt, pattern_len)))
-    return _chunked(seed, n_pairs, chunk, "long_reads")
+    return _chunked(seed, n_pairs, "_chunk_long", "long_reads", text_len=text_len,
+                    pattern_len=pattern_len, rate=rate)
+
+
+def _chunk_uneven(rng, cnt, sigma):
+    L = np.clip(np.exp(rng.normal(np.log(8000.0), sigma, cnt)), 1000, 100_000).astype(np.int64)
+    rate = rng.uniform(0.01, 0.15, cnt)
+    src, soff = _random_codes(rng, L)
+    t, toff = _with_padding(rng, src, soff, 0.05)
+    q, qoff = mutate(rng, src, soff, rate)
+    return PairBatch(t, toff, q, qoff)
 
 
 def uneven_reads(n_pairs: int = 200_000, seed: int = 3, sigma: float = 0.75) -> PairBatch:
     """Log-normal lengths (median 8 kbp, clipped to [1, 100] kbp), per-pair rate U[1 %, 15 %]."""
-    def chunk(rng, cnt):
-        L = np.clip(np.exp(rng.normal(np.log(8000.0), sigma, cnt)), 1000, 100_000).astype(np.int64)
-        rate = rng.uniform(0.01, 0.15, cnt)
-        src, soff = _random_codes(rng, L)
-        t, toff = _with_padding(rng, src, soff, 0.05)
-        q, qoff = mutate(rng, src, soff, rate)
-        return PairBatch(t, toff, q, qoff)
-    return _chunked(seed, n_pairs, chunk, "uneven_reads")
+    return _chunked(seed, n_pairs, "_chunk_uneven", "uneven_reads", sigma=sigma)
+
+
+def _chunk_fixed(rng, cnt, rate, length):
+    src, soff = _random_codes(rng, np.full(cnt, length))
+    t, toff = _with_padding(rng, src, soff, 0.05)
+    q, qoff = mutate(rng, src, soff, rate)
+    return PairBatch(t, toff, q, qoff)
 
 
 def fixed_error(n_pairs: int = 20_000, rate: float = 0.10, seed: int = 6,
                 length: int = 10_000) -> PairBatch:
     """length-bp source + 5 % padding as text; pattern = source at ``rate`` edits."""
-    def chunk(rng, cnt):
-        src, soff = _random_codes(rng, np.full(cnt, length))
-        t, toff = _with_padding(rng, src, soff, 0.05)
-        q, qoff = mutate(rng, src, soff, rate)
-        return PairBatch(t, toff, q, qoff)
-    return _chunked(seed, n_pairs, chunk, f"fixed_error_{rate:g}")
+    return _chunked(seed, n_pairs, "_chunk_fixed", f"fixed_error_{rate:g}", rate=rate, length=length)
 
 
 def random_pairs(n_pairs: int, max_text: int, max_pattern: int, seed: int,

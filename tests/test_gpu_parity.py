@@ -1,0 +1,214 @@
+"""Parity of the CUDA path with the CPU oracle (needs a GB300).
+
+Every comparison is bit-exact: edit counts, text consumed, CIGAR lengths and
+every CIGAR run. Inputs are the seeded synthetic workloads; the oracle sees
+codes 0..3, the CUDA library the packed form produced by its own packer.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2208_09985_gb300 as sc
+from paper_2208_09985_gb300 import synth
+from tests._compare import assert_same, run_totals
+
+pytestmark = pytest.mark.gpu
+
+THREADS = os.cpu_count() or 4
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    oracle.build()
+    h = sc.scrooge_create(0)
+    yield h
+    sc.scrooge_destroy(h)
+
+
+def _both(ctx, batch, W=64, O=24, k=None, flags=0, cap=None):
+    pb = sc.PackedBatch(batch)
+    g = sc.align_host(ctx, pb, W, O, k, flags, cigar_capacity=cap)
+    r = oracle.align_batch(batch, W, O, k, threads=THREADS, cigar_capacity=cap)
+    return g, r
+
+
+def test_tiny_windows_full(ctx):
+    b = synth.tiny_windows(1000, seed=0)
+    g, r = _both(ctx, b)
+    assert_same(g, r, label="tiny_windows")
+    assert (g["edit_counts"] >= 0).all()
+
+
+@pytest.mark.parametrize("W", [32, 64, 128, 16, 40, 100, 1, 2])
+def test_random_edge_cases_all_lane_configs(ctx, W):
+    words = 1 if W <= 32 else (2 if W <= 64 else 4)
+    lanes_opts = {1: [1, 2, 4], 2: [2, 4, 8], 4: [8, 16]}[words]
+    rng = np.random.default_rng(W)
+    b = synth.random_pairs(300, max_text=4 * W + 5, max_pattern=4 * W + 5, seed=100 + W)
+    saved = sc.scrooge_get_kernel_config(ctx, words)
+    try:
+        for lanes in lanes_opts:
+            for rows in (1, 3, 40):
+                sc.scrooge_set_kernel_config(ctx, words, lanes, rows, 2)
+                O = int(rng.integers(0, W))
+                for k in (W, max(0, W // 8)):
+                    g, r = _both(ctx, b, W, O, k)
+                    assert_same(g, r, label=f"W={W} O={O} k={k} lanes={lanes} rows={rows}")
+    finally:
+        sc.scrooge_set_kernel_config(ctx, words, *saved)
+
+
+@pytest.mark.parametrize("flags", list(range(8)))
+def test_ablation_flags_identical(ctx, flags):
+    f = (sc.SCROOGE_NO_SENE if flags & 1 else 0) | (sc.SCROOGE_NO_DENT if flags & 2 else 0) | \
+        (sc.SCROOGE_NO_ET if flags & 4 else 0)
+    b = synth.concat([synth.tiny_windows(200, seed=5), synth.long_reads(6, seed=9),
+                      synth.random_pairs(100, 200, 200, seed=8)])
+    for W, O in ((64, 24), (64, 33), (32, 17), (128, 64)):
+        g, r = _both(ctx, b, W, O, flags=f)
+        assert_same(g, r, label=f"flags={f} W={W} O={O}")
+
+
+def test_kernel_shapes_w64(ctx):
+    b = synth.concat([synth.long_reads(8, seed=21), synth.short_reads(300, seed=22),
+                      synth.fixed_error(4, 0.15, seed=23)])
+    r = oracle.align_batch(b, 64, 24, threads=THREADS)
+    pb = sc.PackedBatch(b)
+    saved = sc.scrooge_get_kernel_config(ctx, 2)
+    try:
+        for lanes in (2, 4, 8):
+            for rows in (1, 6, 12, 65):
+                for wpb in (1, 3, 8):
+                    sc.scrooge_set_kernel_config(ctx, 2, lanes, rows, wpb)
+                    g = sc.align_host(ctx, pb, 64, 24)
+                    assert_same(g, r, label=f"lanes={lanes} rows={rows} wpb={wpb}")
+    finally:
+        sc.scrooge_set_kernel_config(ctx, 2, *saved)
+
+
+def test_device_pointers_match_host(ctx):
+    import torch
+    b = synth.short_reads(5000, seed=31)
+    pb = sc.PackedBatch(b)
+    h = sc.align_host(ctx, pb)
+    db = sc.DeviceBatch(pb)
+    sc.align_device(ctx, db, 64, 24, flags=sc.SCROOGE_SYNC)
+    torch.cuda.synchronize()
+    d = sc.device_results(db)
+    np.testing.assert_array_equal(d["edit_counts"], h["edit_counts"])
+    np.testing.assert_array_equal(d["text_consumed"], h["text_consumed"])
+    np.testing.assert_array_equal(d["cigar_lens"], h["cigar_lens"])
+    for p in range(0, b.n_pairs, 97):
+        o = int(h["cigar_off"][p])
+        n = int(h["cigar_lens"][p])
+        assert np.array_equal(d["cigar"][o:o + n], h["cigar"][o:o + n])
+
+
+def test_workload_subsets(ctx):
+    for b in (synth.short_reads(20_000), synth.long_reads(200), synth.uneven_reads(120),
+              synth.fixed_error(100, 0.05, seed=5), synth.fixed_error(100, 0.15, seed=7)):
+        g, r = _both(ctx, b)
+        assert_same(g, r, label=b.name)
+
+
+def test_k_failures_and_cigar_overflow(ctx):
+    b = synth.concat([synth.random_pairs(200, 150, 150, seed=41, rate_max=0.6), synth.tiny_windows(100, seed=3)])
+    for k in (0, 1, 3, 8):
+        g, r = _both(ctx, b, 64, 24, k)
+        assert_same(g, r, label=f"k={k}")
+        assert (g["edit_counts"] == -1).any() or k == 8
+    for cap in (1, 2, 5):
+        g, r = _both(ctx, b, 64, 24, cap=cap)
+        assert_same(g, r, label=f"cigar capacity {cap}")
+        assert (g["cigar_lens"] == -1).any()
+
+
+def test_bad_arguments(ctx):
+    b = synth.tiny_windows(4)
+    pb = sc.PackedBatch(b)
+    for W, O, k in ((0, 0, 0), (129, 0, 10), (64, 64, 64), (64, -1, 64), (64, 24, 65), (64, 24, -1)):
+        with pytest.raises(sc.ScroogeError) as e:
+            sc.align_host(ctx, pb, W, O, k)
+        assert e.value.code == sc.SCROOGE_E_INVAL
+    bad = sc.PackedBatch(b)
+    bad.text_off = bad.text_off.copy()
+    bad.text_off[1] += 16
+    with pytest.raises(sc.ScroogeError) as e:
+        sc.align_host(ctx, bad)
+    assert e.value.code == sc.SCROOGE_E_INVAL
+
+
+def test_allocation_failure_is_reported_and_recovers(ctx):
+    ctx2 = sc.scrooge_create(0)
+    try:
+        b = synth.tiny_windows(50)
+        pb = sc.PackedBatch(b)
+        sc.scrooge_debug_fail_next_allocs(ctx2, 1)
+        with pytest.raises(sc.ScroogeError) as e:
+            sc.align_host(ctx2, pb)
+        assert e.value.code == sc.SCROOGE_E_NOMEM
+        g = sc.align_host(ctx2, pb)
+        r = oracle.align_batch(b, 64, 24, threads=THREADS)
+        assert_same(g, r, label="after injected allocation failure")
+    finally:
+        sc.scrooge_destroy(ctx2)
+
+
+def test_stats_count_rows(ctx):
+    import torch
+    b = synth.long_reads(16, seed=77)
+    pb = sc.PackedBatch(b)
+    n = b.n_pairs
+    win = torch.zeros(n, dtype=torch.int32, device="cuda")
+    rows = torch.zeros(n, dtype=torch.int64, device="cuda")
+    cells = torch.zeros(n, dtype=torch.int64, device="cuda")
+    cyc = torch.zeros(n, dtype=torch.int64, device="cuda")
+    sc.scrooge_set_stats(ctx, win, rows, cells, cyc)
+    try:
+        sc.align_host(ctx, pb)
+    finally:
+        sc.scrooge_set_stats(ctx)
+    for p in range(n):
+        r = oracle.align_pair(b.text(p), b.pattern(p), 64, 24)
+        assert int(win[p]) == r["d_opt"].shape[0]
+        assert int(rows[p]) == int((r["d_opt"] + 1).sum())
+    assert (cyc.cpu().numpy() > 0).all()
+
+
+def test_full_size_long_reads_sampled(ctx):
+    """The 100,000-pair long-read workload in the default launch configuration.
+
+    Every pair's CIGAR must consume its whole pattern and exactly text_consumed
+    text bases with edit_count edits; 300 sampled pairs are checked against the
+    oracle run by run.
+    """
+    b = synth.long_reads(100_000)
+    pb = sc.PackedBatch(b)
+    cap = 4096
+    g = sc.align_host(ctx, pb, 64, 24, cigar_capacity=cap)
+    assert (g["cigar_lens"] > 0).all() and (g["edit_counts"] >= 0).all()
+    pat, txt, ed = run_totals(g, b.n_pairs)
+    np.testing.assert_array_equal(pat, np.diff(b.pattern_off))
+    np.testing.assert_array_equal(txt, g["text_consumed"])
+    np.testing.assert_array_equal(ed, g["edit_counts"])
+    sample = np.random.default_rng(99).choice(b.n_pairs, 300, replace=False)
+    sub = b.subset(sample)
+    r = oracle.align_batch(sub, 64, 24, threads=THREADS, cigar_capacity=cap)
+    assert_same(g, r, pairs=sample, label="long_reads full size (sample)")
+
+
+def test_full_size_short_reads_sampled(ctx):
+    b = synth.short_reads(1_000_000)
+    pb = sc.PackedBatch(b)
+    g = sc.align_host(ctx, pb, 64, 24)
+    pat, txt, ed = run_totals(g, b.n_pairs)
+    np.testing.assert_array_equal(pat, np.diff(b.pattern_off))
+    np.testing.assert_array_equal(txt, g["text_consumed"])
+    np.testing.assert_array_equal(ed, g["edit_counts"])
+    sample = np.random.default_rng(7).choice(b.n_pairs, 5000, replace=False)
+    r = oracle.align_batch(b.subset(sample), 64, 24, threads=THREADS)
+    assert_same(g, r, pairs=sample, label="short_reads full size (sample)")

@@ -215,3 +215,6 @@ def test_cigar_overflow_reported(oracle_mod):
             assert res["cigar_lens"][p] == -1
         else:
             assert res["cigar_lens"][p] == len(full["cigar"])
+        # the alignment itself is unaffected by the capacity
+        assert res["edit_counts"][p] == full["edit_count"]
+        assert res["text_consumed"][p] == full["text_consumed"]
