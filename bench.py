@@ -36,17 +36,17 @@ from paper_2208_09985_gb300 import synth  # noqa: E402
 
 WORKLOADS = {
     "long_reads": dict(
-        make=lambda n, seed: synth.long_reads(n, seed=seed), n=100_000, seed=2, W=64, O=24, cap=4096,
+        make=lambda n, seed: synth.long_reads(n, seed=seed), n=100_000, seed=2, W=64, O=24,
         desc="100,000 pairs: 10 kbp patterns vs 10.5 kbp texts, 10% edits (50/25/25, 20% homopolymer "
              "indels of 1-5 bases), W=64 O=24 k=64"),
     "short_reads": dict(
-        make=lambda n, seed: synth.short_reads(n, seed=seed), n=1_000_000, seed=1, W=64, O=24, cap=None,
+        make=lambda n, seed: synth.short_reads(n, seed=seed), n=1_000_000, seed=1, W=64, O=24,
         desc="1,000,000 pairs: patterns U{100..250} bp, texts +5% padding, 5% edits, W=64 O=24 k=64"),
     "uneven_reads": dict(
-        make=lambda n, seed: synth.uneven_reads(n, seed=seed), n=200_000, seed=3, W=64, O=24, cap=None,
+        make=lambda n, seed: synth.uneven_reads(n, seed=seed), n=200_000, seed=3, W=64, O=24,
         desc="200,000 pairs: log-normal lengths (median 8 kbp, 1-100 kbp), per-pair error U[1%,15%], W=64 O=24"),
     "tiny_windows": dict(
-        make=lambda n, seed: synth.tiny_windows(n, seed=seed), n=1000, seed=0, W=64, O=24, cap=None,
+        make=lambda n, seed: synth.tiny_windows(n, seed=seed), n=1000, seed=0, W=64, O=24,
         desc="1,000 pairs: 110 bp texts, 100 bp patterns, 2% edits, W=64 O=24"),
 }
 
@@ -204,7 +204,7 @@ def main():
     pb = sc.PackedBatch(batch)
     stream = torch.cuda.current_stream()
     ctx = sc.scrooge_create(local, stream)
-    db = sc.DeviceBatch(pb, cigar_capacity=wl["cap"])
+    db = sc.DeviceBatch(pb)
     flags = args.flags
     words = 1 if W <= 32 else (2 if W <= 64 else 4)
 
@@ -217,9 +217,9 @@ def main():
     total_cells = int(cells.sum().item())
     total_rows = int(rows.sum().item())
     ec = db.edit_counts.cpu().numpy()
-    cl = db.cigar_lens.cpu().numpy()
-    if (ec < 0).any() or (cl < 0).any():
-        raise SystemExit("bench: some pairs failed or overflowed their CIGAR capacity")
+    total_runs = int(db.cigar_off[-1].item())
+    if (ec < 0).any() or total_runs > db.cigar_capacity:
+        raise SystemExit("bench: some pairs failed or the CIGAR buffer is too small")
 
     for _ in range(args.warmup):
         sc.align_device(ctx, db, W, O, k, flags)
@@ -251,16 +251,16 @@ def main():
     if not args.no_e2e:
         pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
         h_in = [pin(x) for x in (pb.texts, pb.text_off, pb.text_len, pb.patterns, pb.pat_off, pb.pat_len)]
-        coff = pin(pb.cigar_offsets(wl["cap"]))
+        cap = db.cigar_capacity
         h_ec = torch.zeros(n_pairs, dtype=torch.int32).pin_memory().numpy()
         h_tc = torch.zeros(n_pairs, dtype=torch.int32).pin_memory().numpy()
-        h_cl = torch.zeros(n_pairs, dtype=torch.int32).pin_memory().numpy()
-        h_cig = torch.zeros(int(coff[-1]), dtype=torch.int32).pin_memory().numpy().view(np.uint32)
+        h_off = torch.zeros(n_pairs + 1, dtype=torch.int64).pin_memory().numpy()
+        h_cig = torch.zeros(cap, dtype=torch.int32).pin_memory().numpy().view(np.uint32)
         e2e_ctx = sc.scrooge_create(local, stream)
 
         def call():
             sc.scrooge_align_batch(e2e_ctx, h_in[0], h_in[1], h_in[2], h_in[3], h_in[4], h_in[5], n_pairs, W, O,
-                                   k, flags, h_ec, h_tc, h_cig, coff, h_cl)
+                                   k, flags, h_ec, h_tc, h_cig, cap, h_off)
         call()
         e2e_steps = max(2, min(args.steps, 5))
         torch.cuda.synchronize()
@@ -273,9 +273,9 @@ def main():
             t = torch.tensor([e2e_s], device="cuda")
             torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
             e2e_s = float(t.item())
-        h2d = sum(int(x.nbytes) for x in h_in) + int(coff.nbytes)
-        d2h = int(h_ec.nbytes + h_tc.nbytes + h_cl.nbytes + h_cig.nbytes)
-        if not (np.array_equal(h_ec, ec) and np.array_equal(h_cl, cl)):
+        h2d = sum(int(x.nbytes) for x in h_in)
+        d2h = int(h_ec.nbytes + h_tc.nbytes + h_off.nbytes) + 4 * int(h_off[-1])
+        if not (np.array_equal(h_ec, ec) and int(h_off[-1]) == total_runs):
             raise SystemExit("bench: end-to-end results differ from the device-resident run")
         e2e = {"value": world * n_pairs / e2e_s, "unit": "alignments/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "gbases_per_s": world * bases / e2e_s / 1e9}
@@ -308,7 +308,7 @@ def main():
                    "l2": "inputs larger than L2 (packed inputs %.0f MB)" % (pb.texts.nbytes / 1e6 + pb.patterns.nbytes / 1e6),
                    "parallelism": f"dp{world}" if world > 1 else "single GPU"},
         "gbases_per_s": world * bases / (ms / 1e3) / 1e9,
-        "mean_edits_per_pair": float(ec.mean()),
+        "mean_edits_per_pair": float(ec.mean()), "cigar_runs_per_step": total_runs,
         "dp_cells_per_step": total_cells, "dp_rows_per_step": total_rows,
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
                      "frac": achieved / peak_ops, "traffic": traffic,

@@ -43,6 +43,7 @@ typedef struct scrooge_ctx scrooge_ctx; /* opaque, owned by the library */
 #define SCROOGE_E_TIMEOUT (-4)  /* a bounded device wait gave up */
 #define SCROOGE_E_NOMODEL (-5)  /* SCROOGE_LEARNED without a loaded or trained model */
 #define SCROOGE_E_INTERNAL (-6) /* a kernel reported an impossible state */
+#define SCROOGE_E_CAPACITY (-7) /* the CIGAR output buffer is too small (see scrooge_align_batch) */
 
 /* ------------------------------------------------------------------- flags */
 /* All pointers passed to scrooge_align_batch are device pointers and the
@@ -115,19 +116,29 @@ int scrooge_pack_2bit(const uint8_t *seqs, const int64_t *offsets, int32_t n_seq
  *                        with no d <= k fails the pair (k = W never fails)
  *   flags                SCROOGE_* flags above
  * Outputs (caller-owned):
- *   edit_counts[n_pairs]    X + I + D operations of the pair's CIGAR, or -1
- *                           if some window failed (empty CIGAR)
- *   text_consumed[n_pairs]  text bases covered by the CIGAR (the text end is free)
- *   cigar                   run-length CIGAR runs (SCROOGE_OP_*); pair p may
- *                           write cigar[cigar_offsets[p] .. cigar_offsets[p+1])
- *   cigar_offsets[n_pairs+1] capacity layout (input); m + n + 1 runs always suffice
- *   cigar_lens[n_pairs]     runs written, or -1 if the capacity was too small
+ *   edit_counts[n_pairs]     X + I + D operations of the pair's CIGAR, or -1
+ *                            if some window failed (the pair then has no runs)
+ *   text_consumed[n_pairs]   text bases covered by the CIGAR (the text end is free)
+ *   cigar[cigar_capacity]    run-length CIGAR runs (SCROOGE_OP_*) of all pairs,
+ *                            back to back in pair order
+ *   cigar_offsets[n_pairs+1] runs of pair p are cigar[cigar_offsets[p] ..
+ *                            cigar_offsets[p+1]); cigar_offsets[n_pairs] is the
+ *                            total. A pair whose runs do not fit entirely below
+ *                            cigar_capacity is not written; a synchronous call
+ *                            then returns SCROOGE_E_CAPACITY (all other outputs
+ *                            are valid and cigar_offsets[n_pairs] tells the
+ *                            capacity needed). An asynchronous call reports it
+ *                            only through cigar_offsets[n_pairs].
+ * Device scratch: the library keeps per-pair run buffers of m + n + 1 runs.
+ * With SCROOGE_DEVICE_PTRS the call reads the pairs' total length back to
+ * size that scratch (one small synchronous copy before the alignment kernel);
+ * the rest is queued on the stream.
  * Returns SCROOGE_E_INVAL before any work on bad arguments. */
 int scrooge_align_batch(scrooge_ctx *ctx, const uint32_t *texts, const int64_t *text_offsets,
                         const int32_t *text_lengths, const uint32_t *patterns, const int64_t *pattern_offsets,
                         const int32_t *pattern_lengths, int32_t n_pairs, int32_t W, int32_t O, int32_t k,
                         uint32_t flags, int32_t *edit_counts, int32_t *text_consumed, uint32_t *cigar,
-                        const int64_t *cigar_offsets, int32_t *cigar_lens);
+                        int64_t cigar_capacity, int64_t *cigar_offsets);
 
 /* ------------------------------------------------------- kernel settings
  * Implementation parameters of the alignment kernel for windows of up to

@@ -29,6 +29,7 @@ SCROOGE_E_CUDA = -3
 SCROOGE_E_TIMEOUT = -4
 SCROOGE_E_NOMODEL = -5
 SCROOGE_E_INTERNAL = -6
+SCROOGE_E_CAPACITY = -7
 
 SCROOGE_DEVICE_PTRS = 1 << 0
 SCROOGE_SYNC = 1 << 1
@@ -68,7 +69,7 @@ def load():
                 "scrooge_set_stream": ([P, P], ctypes.c_int),
                 "scrooge_packed_words": ([i64], i64),
                 "scrooge_pack_2bit": ([P, P, i32, ctypes.c_int, P, i64, P, P], ctypes.c_int),
-                "scrooge_align_batch": ([P, P, P, P, P, P, P, i32, i32, i32, i32, u32, P, P, P, P, P],
+                "scrooge_align_batch": ([P, P, P, P, P, P, P, i32, i32, i32, i32, u32, P, P, P, i64, P],
                                         ctypes.c_int),
                 "scrooge_set_kernel_config": ([P, i32, i32, i32, i32], ctypes.c_int),
                 "scrooge_get_kernel_config": ([P, i32, P, P, P], ctypes.c_int),
@@ -160,12 +161,12 @@ def scrooge_pack_2bit(seqs: np.ndarray, offsets: np.ndarray, ascii: bool = False
 
 def scrooge_align_batch(ctx, texts, text_offsets, text_lengths, patterns, pattern_offsets, pattern_lengths,
                         n_pairs: int, W: int, O: int, k: int, flags: int, edit_counts, text_consumed, cigar,
-                        cigar_offsets, cigar_lens):
+                        cigar_capacity: int, cigar_offsets):
     """Direct call of the C entry point; raises ScroogeError on a non-zero return."""
     rc = load().scrooge_align_batch(ctx, _ptr(texts), _ptr(text_offsets), _ptr(text_lengths), _ptr(patterns),
                                     _ptr(pattern_offsets), _ptr(pattern_lengths), int(n_pairs), int(W), int(O),
                                     int(k), int(flags), _ptr(edit_counts), _ptr(text_consumed), _ptr(cigar),
-                                    _ptr(cigar_offsets), _ptr(cigar_lens))
+                                    int(cigar_capacity), _ptr(cigar_offsets))
     return _check(ctx, rc)
 
 
@@ -198,47 +199,53 @@ class PackedBatch:
         self.texts, self.text_off, self.text_len = scrooge_pack_2bit(batch.texts, batch.text_off)
         self.patterns, self.pat_off, self.pat_len = scrooge_pack_2bit(batch.patterns, batch.pattern_off)
 
-    def cigar_offsets(self, capacity=None) -> np.ndarray:
-        """Capacity layout: m + n + 1 runs per pair unless ``capacity`` (scalar or per pair) is given."""
-        if capacity is None:
-            cap = self.text_len.astype(np.int64) + self.pat_len.astype(np.int64) + 1
-        else:
-            cap = np.broadcast_to(np.asarray(capacity, dtype=np.int64), (self.n_pairs,))
-        off = np.zeros(self.n_pairs + 1, dtype=np.int64)
-        np.cumsum(cap, out=off[1:])
-        return off
+    def cigar_guess(self) -> int:
+        """A CIGAR capacity (runs) that holds typical outputs: a quarter run per pattern base."""
+        return int(self.pat_len.astype(np.int64).sum()) // 4 + 16 * self.n_pairs + 1024
 
 
 def align_host(ctx, pb: PackedBatch, W: int = 64, O: int = 24, k: int | None = None, flags: int = 0,
-               cigar_capacity=None) -> dict:
-    """Align a PackedBatch from host memory; returns host numpy results."""
+               cigar_capacity: int | None = None) -> dict:
+    """Align a PackedBatch from host memory; returns host numpy results.
+
+    Without ``cigar_capacity`` the CIGAR buffer starts at ``pb.cigar_guess()``
+    runs and the call is repeated once with the exact size if that was short.
+    """
     k = W if k is None else k
     n = pb.n_pairs
-    coff = pb.cigar_offsets(cigar_capacity)
     ec = np.zeros(n, np.int32)
     tc = np.zeros(n, np.int32)
-    cl = np.zeros(n, np.int32)
-    cig = np.zeros(max(int(coff[-1]), 1), np.uint32)
-    scrooge_align_batch(ctx, pb.texts, pb.text_off, pb.text_len, pb.patterns, pb.pat_off, pb.pat_len, n, W, O, k,
-                        flags & ~SCROOGE_DEVICE_PTRS, ec, tc, cig, coff, cl)
-    return {"edit_counts": ec, "text_consumed": tc, "cigar": cig, "cigar_off": coff, "cigar_lens": cl}
+    off = np.zeros(n + 1, np.int64)
+    cap = pb.cigar_guess() if cigar_capacity is None else int(cigar_capacity)
+    cig = np.zeros(max(cap, 1), np.uint32)
+    args = (pb.texts, pb.text_off, pb.text_len, pb.patterns, pb.pat_off, pb.pat_len, n, W, O, k,
+            flags & ~SCROOGE_DEVICE_PTRS, ec, tc)
+    try:
+        scrooge_align_batch(ctx, *args, cig, cap, off)
+    except ScroogeError as e:
+        if e.code != SCROOGE_E_CAPACITY or cigar_capacity is not None:
+            raise
+        cap = int(off[-1])
+        cig = np.zeros(max(cap, 1), np.uint32)
+        scrooge_align_batch(ctx, *args, cig, cap, off)
+    return {"edit_counts": ec, "text_consumed": tc, "cigar": cig, "cigar_off": off,
+            "cigar_lens": np.diff(off).astype(np.int32)}
 
 
 class DeviceBatch:
     """A PackedBatch resident on a CUDA device (torch tensors), with output buffers."""
 
-    def __init__(self, pb: PackedBatch, device="cuda", cigar_capacity=None):
+    def __init__(self, pb: PackedBatch, device="cuda", cigar_capacity: int | None = None):
         import torch
         t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(device)
         self.n_pairs = pb.n_pairs
         self.texts, self.text_off, self.text_len = t(pb.texts), t(pb.text_off), t(pb.text_len)
         self.patterns, self.pat_off, self.pat_len = t(pb.patterns), t(pb.pat_off), t(pb.pat_len)
-        coff = pb.cigar_offsets(cigar_capacity)
-        self.cigar_off = t(coff)
+        self.cigar_capacity = pb.cigar_guess() if cigar_capacity is None else int(cigar_capacity)
+        self.cigar_off = torch.zeros(self.n_pairs + 1, dtype=torch.int64, device=device)
         self.edit_counts = torch.zeros(self.n_pairs, dtype=torch.int32, device=device)
         self.text_consumed = torch.zeros_like(self.edit_counts)
-        self.cigar_lens = torch.zeros_like(self.edit_counts)
-        self.cigar = torch.zeros(max(int(coff[-1]), 1), dtype=torch.int32, device=device)
+        self.cigar = torch.zeros(max(self.cigar_capacity, 1), dtype=torch.int32, device=device)
 
 
 def align_device(ctx, db: DeviceBatch, W: int = 64, O: int = 24, k: int | None = None, flags: int = 0):
@@ -246,11 +253,12 @@ def align_device(ctx, db: DeviceBatch, W: int = 64, O: int = 24, k: int | None =
     k = W if k is None else k
     return scrooge_align_batch(ctx, db.texts, db.text_off, db.text_len, db.patterns, db.pat_off, db.pat_len,
                                db.n_pairs, W, O, k, flags | SCROOGE_DEVICE_PTRS, db.edit_counts, db.text_consumed,
-                               db.cigar, db.cigar_off, db.cigar_lens)
+                               db.cigar, db.cigar_capacity, db.cigar_off)
 
 
 def device_results(db: DeviceBatch) -> dict:
     """Copy a DeviceBatch's outputs to host numpy arrays."""
+    off = db.cigar_off.cpu().numpy()
     return {"edit_counts": db.edit_counts.cpu().numpy(), "text_consumed": db.text_consumed.cpu().numpy(),
-            "cigar": db.cigar.cpu().numpy().view(np.uint32), "cigar_off": db.cigar_off.cpu().numpy(),
-            "cigar_lens": db.cigar_lens.cpu().numpy()}
+            "cigar": db.cigar.cpu().numpy().view(np.uint32), "cigar_off": off,
+            "cigar_lens": np.diff(off).astype(np.int32)}

@@ -297,6 +297,8 @@ __global__ void __launch_bounds__(256) align_kernel(const AlignParams p) {
                 if (__all_sync(kFull, dc_done)) break;
             }
 
+            __syncwarp();  // entries written by every lane are visible to the traceback lane
+
             // ---- GenASM-TB on the traceback lane
             if (active && l == G - 1) {
                 st_windows += 1;
@@ -387,7 +389,8 @@ __global__ void __launch_bounds__(256) align_kernel(const AlignParams p) {
                     out.flush();
                     p.edit_counts[pair] = failed ? -1 : out.edits;
                     p.text_consumed[pair] = failed ? 0 : ti;
-                    p.cigar_lens[pair] = failed ? 0 : (out.n > out.cap ? -1 : out.n);
+                    if (out.n > out.cap) atomicOr(p.status, 2);  // impossible: capacity is m + n + 1
+                    p.cigar_lens[pair] = failed ? 0 : min(out.n, (int32_t)out.cap);
                     if (p.st_windows) p.st_windows[pair] = st_windows;
                     if (p.st_rows) p.st_rows[pair] = st_rows;
                     if (p.st_cells) p.st_cells[pair] = st_cells;

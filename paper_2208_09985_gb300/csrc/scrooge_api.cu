@@ -54,8 +54,9 @@ struct scrooge_ctx {
     KernelConfig kcfg[3] = {{2, 16, 2}, {4, 12, 2}, {8, 12, 2}};  // words 1, 2, 4
     int fail_allocs = 0;  // testing hook: fail the next N device allocations
     DevBuf spill, status;
-    DevBuf in_text, in_pat, in_toff, in_tlen, in_poff, in_plen, in_coff;
-    DevBuf out_ec, out_tc, out_cig, out_cl;
+    DevBuf in_text, in_pat, in_toff, in_tlen, in_poff, in_plen;
+    DevBuf out_ec, out_tc, out_cig, out_off;
+    DevBuf scr_runs, scr_off, scr_len, scr_cap, scan_tmp;
     int32_t *st_windows = nullptr;
     int64_t *st_rows = nullptr, *st_cells = nullptr, *st_cycles = nullptr;
 };
@@ -146,8 +147,9 @@ int scrooge_create(scrooge_ctx **out, int cuda_device, void *cuda_stream) {
 int scrooge_destroy(scrooge_ctx *c) {
     if (!c) return SCROOGE_OK;
     cudaSetDevice(c->device);
-    DevBuf *all[] = {&c->spill, &c->status, &c->in_text, &c->in_pat, &c->in_toff, &c->in_tlen, &c->in_poff,
-                     &c->in_plen, &c->in_coff, &c->out_ec, &c->out_tc, &c->out_cig, &c->out_cl};
+    DevBuf *all[] = {&c->spill,   &c->status,  &c->in_text, &c->in_pat,   &c->in_toff,  &c->in_tlen,
+                     &c->in_poff,   &c->in_plen, &c->out_ec,  &c->out_tc,   &c->out_cig,  &c->out_off,
+                     &c->scr_runs,  &c->scr_off, &c->scr_len, &c->scr_cap,  &c->scan_tmp};
     for (DevBuf *b : all) release(*b);
     delete c;
     return SCROOGE_OK;
@@ -268,24 +270,36 @@ int scrooge_align_batch(scrooge_ctx *c, const uint32_t *texts, const int64_t *te
                         const int32_t *text_lengths, const uint32_t *patterns, const int64_t *pattern_offsets,
                         const int32_t *pattern_lengths, int32_t n_pairs, int32_t W, int32_t O, int32_t k,
                         uint32_t flags, int32_t *edit_counts, int32_t *text_consumed, uint32_t *cigar,
-                        const int64_t *cigar_offsets, int32_t *cigar_lens) {
+                        int64_t cigar_capacity, int64_t *cigar_offsets) {
     if (!c) return SCROOGE_E_INVAL;
     c->err.clear();
     if (n_pairs < 0) return fail(c, SCROOGE_E_INVAL, "n_pairs < 0");
     if (W < 1 || W > 128) return fail(c, SCROOGE_E_INVAL, "W=%d outside 1..128", W);
     if (O < 0 || O >= W) return fail(c, SCROOGE_E_INVAL, "O=%d outside 0..W-1", O);
     if (k < 0 || k > W) return fail(c, SCROOGE_E_INVAL, "k=%d outside 0..W", k);
+    if (cigar_capacity < 0) return fail(c, SCROOGE_E_INVAL, "cigar_capacity < 0");
     if (flags & (SCROOGE_PERSISTENT | SCROOGE_LEARNED | SCROOGE_GRAPH))
         return fail(c, SCROOGE_E_INVAL, "scheduling flags are not available in this build");
-    if (n_pairs == 0) return SCROOGE_OK;
-    if (!texts || !text_offsets || !text_lengths || !patterns || !pattern_offsets || !pattern_lengths ||
-        !edit_counts || !text_consumed || !cigar_offsets || !cigar_lens)
-        return fail(c, SCROOGE_E_INVAL, "null pointer argument");
+    if (!cigar_offsets) return fail(c, SCROOGE_E_INVAL, "null cigar_offsets");
+    const bool dev = (flags & SCROOGE_DEVICE_PTRS) != 0;
     cudaError_t e = cudaSetDevice(c->device);
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
-    const bool dev = (flags & SCROOGE_DEVICE_PTRS) != 0;
     cudaStream_t st = c->stream;
+    if (n_pairs == 0) {
+        if (dev) {
+            if ((e = cudaMemsetAsync(cigar_offsets, 0, 8, st)) != cudaSuccess) return cuda_fail(c, e, "memset");
+            if ((flags & SCROOGE_SYNC) && (e = cudaStreamSynchronize(st)) != cudaSuccess)
+                return cuda_fail(c, e, "stream synchronise");
+        } else {
+            cigar_offsets[0] = 0;
+        }
+        return SCROOGE_OK;
+    }
+    if (!texts || !text_offsets || !text_lengths || !patterns || !pattern_offsets || !pattern_lengths ||
+        !edit_counts || !text_consumed || (cigar_capacity > 0 && !cigar))
+        return fail(c, SCROOGE_E_INVAL, "null pointer argument");
     int rc;
+    const size_t np = (size_t)n_pairs;
 
     AlignParams p;
     memset(&p, 0, sizeof p);
@@ -293,6 +307,11 @@ int scrooge_align_batch(scrooge_ctx *c, const uint32_t *texts, const int64_t *te
     p.W = W;
     p.O = O;
     p.k = k;
+    int64_t scratch_runs = 0;
+    if ((rc = ensure(c, c->scr_off, (np + 1) * 8, "CIGAR scratch offsets")) ||
+        (rc = ensure(c, c->scr_len, np * 4, "CIGAR run counts")) ||
+        (rc = ensure(c, c->scan_tmp, (size_t)scan_temp_words((int64_t)np + 1) * 8, "scan scratch")))
+        return rc;
     if (dev) {
         p.texts = texts;
         p.text_off = text_offsets;
@@ -300,14 +319,23 @@ int scrooge_align_batch(scrooge_ctx *c, const uint32_t *texts, const int64_t *te
         p.patterns = patterns;
         p.pat_off = pattern_offsets;
         p.pat_len = pattern_lengths;
-        p.cigar_off = cigar_offsets;
         p.edit_counts = edit_counts;
         p.text_consumed = text_consumed;
-        p.cigar = cigar;
-        p.cigar_lens = cigar_lens;
+        // size the run scratch from the device-resident lengths
+        int64_t *cap = (int64_t *)c->scr_len.p;  // reused below for the run counts
+        if ((rc = ensure(c, c->scr_cap, np * 8, "CIGAR capacities"))) return rc;
+        cap = (int64_t *)c->scr_cap.p;
+        if ((e = launch_capacity(text_lengths, pattern_lengths, n_pairs, cap, st)) != cudaSuccess ||
+            (e = exclusive_scan(cap, 1, n_pairs, (int64_t *)c->scr_off.p, (int64_t *)c->scan_tmp.p, st)) != cudaSuccess)
+            return cuda_fail(c, e, "CIGAR scratch layout");
+        if ((e = cudaMemcpyAsync(&scratch_runs, (int64_t *)c->scr_off.p + n_pairs, 8, cudaMemcpyDeviceToHost, st)) !=
+                cudaSuccess ||
+            (e = cudaStreamSynchronize(st)) != cudaSuccess)
+            return cuda_fail(c, e, "CIGAR scratch size");
     } else {
         // host pointers: check the layout, then stage everything on the device
         int64_t text_words = 0, pat_words = 0;
+        std::vector<int64_t> soff(np + 1, 0);
         for (int32_t q = 0; q < n_pairs; ++q) {
             const int64_t to = text_offsets[q], po = pattern_offsets[q];
             const int32_t tl = text_lengths[q], pl = pattern_lengths[q];
@@ -315,32 +343,26 @@ int scrooge_align_batch(scrooge_ctx *c, const uint32_t *texts, const int64_t *te
                 return fail(c, SCROOGE_E_INVAL, "pair %d: offsets must be >= 0 multiples of 64, lengths >= 0", q);
             text_words = std::max(text_words, to / 16 + scrooge_packed_words(tl));
             pat_words = std::max(pat_words, po / 16 + scrooge_packed_words(pl));
-            if (cigar_offsets[q + 1] < cigar_offsets[q])
-                return fail(c, SCROOGE_E_INVAL, "cigar_offsets must be non-decreasing (pair %d)", q);
+            soff[q + 1] = soff[q] + (int64_t)tl + pl + 1;
         }
-        if (cigar_offsets[0] < 0) return fail(c, SCROOGE_E_INVAL, "cigar_offsets[0] < 0");
-        const int64_t cig_total = cigar_offsets[n_pairs];
-        if (cig_total > 0 && !cigar) return fail(c, SCROOGE_E_INVAL, "null cigar buffer");
-        const size_t np = (size_t)n_pairs;
+        scratch_runs = soff[np];
         if ((rc = ensure(c, c->in_text, text_words * 4, "texts")) ||
             (rc = ensure(c, c->in_pat, pat_words * 4, "patterns")) ||
             (rc = ensure(c, c->in_toff, np * 8, "text offsets")) ||
             (rc = ensure(c, c->in_tlen, np * 4, "text lengths")) ||
             (rc = ensure(c, c->in_poff, np * 8, "pattern offsets")) ||
             (rc = ensure(c, c->in_plen, np * 4, "pattern lengths")) ||
-            (rc = ensure(c, c->in_coff, (np + 1) * 8, "cigar offsets")) ||
             (rc = ensure(c, c->out_ec, np * 4, "edit counts")) || (rc = ensure(c, c->out_tc, np * 4, "text consumed")) ||
-            (rc = ensure(c, c->out_cig, (size_t)std::max<int64_t>(cig_total, 1) * 4, "cigar")) ||
-            (rc = ensure(c, c->out_cl, np * 4, "cigar lengths")))
+            (rc = ensure(c, c->out_off, (np + 1) * 8, "cigar offsets")))
             return rc;
         struct {
             void *d;
             const void *h;
             size_t b;
-        } cp[] = {{c->in_text.p, texts, (size_t)text_words * 4},   {c->in_pat.p, patterns, (size_t)pat_words * 4},
-                  {c->in_toff.p, text_offsets, np * 8},            {c->in_tlen.p, text_lengths, np * 4},
-                  {c->in_poff.p, pattern_offsets, np * 8},         {c->in_plen.p, pattern_lengths, np * 4},
-                  {c->in_coff.p, cigar_offsets, (np + 1) * 8}};
+        } cp[] = {{c->in_text.p, texts, (size_t)text_words * 4}, {c->in_pat.p, patterns, (size_t)pat_words * 4},
+                  {c->in_toff.p, text_offsets, np * 8},          {c->in_tlen.p, text_lengths, np * 4},
+                  {c->in_poff.p, pattern_offsets, np * 8},       {c->in_plen.p, pattern_lengths, np * 4},
+                  {c->scr_off.p, soff.data(), (np + 1) * 8}};
         for (auto &x : cp)
             if (x.b && (e = cudaMemcpyAsync(x.d, x.h, x.b, cudaMemcpyHostToDevice, st)) != cudaSuccess)
                 return cuda_fail(c, e, "host-to-device copy");
@@ -350,12 +372,13 @@ int scrooge_align_batch(scrooge_ctx *c, const uint32_t *texts, const int64_t *te
         p.text_len = (const int32_t *)c->in_tlen.p;
         p.pat_off = (const int64_t *)c->in_poff.p;
         p.pat_len = (const int32_t *)c->in_plen.p;
-        p.cigar_off = (const int64_t *)c->in_coff.p;
         p.edit_counts = (int32_t *)c->out_ec.p;
         p.text_consumed = (int32_t *)c->out_tc.p;
-        p.cigar = (uint32_t *)c->out_cig.p;
-        p.cigar_lens = (int32_t *)c->out_cl.p;
     }
+    if ((rc = ensure(c, c->scr_runs, (size_t)std::max<int64_t>(scratch_runs, 1) * 4, "CIGAR run scratch"))) return rc;
+    p.cigar = (uint32_t *)c->scr_runs.p;
+    p.cigar_off = (const int64_t *)c->scr_off.p;
+    p.cigar_lens = (int32_t *)c->scr_len.p;
 
     // kernel shape
     const int words = words_for(W);
@@ -405,31 +428,52 @@ int scrooge_align_batch(scrooge_ctx *c, const uint32_t *texts, const int64_t *te
                                  : launch_align_w128(p, G, sene, wpb, blocks, smem, st));
     if (e != cudaSuccess) return cuda_fail(c, e, "alignment kernel launch");
 
-    const bool sync = !dev || (flags & SCROOGE_SYNC);
+    // dense CIGAR: prefix sums of the run counts, then the gather
+    int64_t *dense_off = dev ? cigar_offsets : (int64_t *)c->out_off.p;
+    if ((e = exclusive_scan(p.cigar_lens, 0, n_pairs, dense_off, (int64_t *)c->scan_tmp.p, st)) != cudaSuccess)
+        return cuda_fail(c, e, "CIGAR offsets");
     int32_t status_h = 0;
-    if (sync) {
-        if ((e = cudaMemcpyAsync(&status_h, p.status, 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
-            return cuda_fail(c, e, "status copy");
+    if (dev) {
+        if ((e = launch_compact(p.cigar, p.cigar_off, p.cigar_lens, dense_off, n_pairs, cigar, cigar_capacity,
+                                c->sm_count, st)) != cudaSuccess)
+            return cuda_fail(c, e, "CIGAR gather");
+        if (!(flags & SCROOGE_SYNC)) return SCROOGE_OK;
+        int64_t total = 0;
+        if ((e = cudaMemcpyAsync(&status_h, p.status, 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(&total, dense_off + n_pairs, 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(st)) != cudaSuccess)
+            return cuda_fail(c, e, "stream synchronise");
+        if (status_h != 0) return fail(c, SCROOGE_E_INTERNAL, "kernel status %d", status_h);
+        if (total > cigar_capacity)
+            return fail(c, SCROOGE_E_CAPACITY, "CIGAR needs %lld runs, capacity %lld", (long long)total,
+                        (long long)cigar_capacity);
+        return SCROOGE_OK;
     }
-    if (!dev) {
-        const size_t np = (size_t)n_pairs;
-        const int64_t cig_total = cigar_offsets[n_pairs];
-        struct {
-            void *h;
-            const void *d;
-            size_t b;
-        } cp[] = {{edit_counts, p.edit_counts, np * 4},
-                  {text_consumed, p.text_consumed, np * 4},
-                  {cigar_lens, p.cigar_lens, np * 4},
-                  {cigar, p.cigar, (size_t)cig_total * 4}};
-        for (auto &x : cp)
-            if (x.b && (e = cudaMemcpyAsync(x.h, x.d, x.b, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
-                return cuda_fail(c, e, "device-to-host copy");
-    }
-    if (sync) {
-        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(c, e, "stream synchronise");
-        if (status_h != 0) return fail(c, SCROOGE_E_INTERNAL, "kernel status %d (traceback found no open edge)", status_h);
-    }
+    // host pointers: learn the total, gather into a device buffer, copy back
+    if ((e = cudaMemcpyAsync(cigar_offsets, dense_off, (np + 1) * 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(&status_h, p.status, 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+        return cuda_fail(c, e, "CIGAR offsets copy");
+    if (status_h != 0) return fail(c, SCROOGE_E_INTERNAL, "kernel status %d", status_h);
+    const int64_t total = cigar_offsets[np];
+    const int64_t keep = std::min(total, cigar_capacity);
+    if ((rc = ensure(c, c->out_cig, (size_t)std::max<int64_t>(keep, 1) * 4, "cigar"))) return rc;
+    if ((e = launch_compact(p.cigar, p.cigar_off, p.cigar_lens, dense_off, n_pairs, (uint32_t *)c->out_cig.p, keep,
+                            c->sm_count, st)) != cudaSuccess)
+        return cuda_fail(c, e, "CIGAR gather");
+    struct {
+        void *h;
+        const void *d;
+        size_t b;
+    } cp[] = {{edit_counts, p.edit_counts, np * 4}, {text_consumed, p.text_consumed, np * 4},
+              {cigar, c->out_cig.p, (size_t)keep * 4}};
+    for (auto &x : cp)
+        if (x.b && (e = cudaMemcpyAsync(x.h, x.d, x.b, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+            return cuda_fail(c, e, "device-to-host copy");
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(c, e, "stream synchronise");
+    if (total > cigar_capacity)
+        return fail(c, SCROOGE_E_CAPACITY, "CIGAR needs %lld runs, capacity %lld", (long long)total,
+                    (long long)cigar_capacity);
     return SCROOGE_OK;
 }
 

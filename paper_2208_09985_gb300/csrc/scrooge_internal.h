@@ -23,9 +23,9 @@ struct AlignParams {
     int32_t sene;   // 1: store entries; 0: store GenASM's I, D, M edge vectors
     int32_t *edit_counts;
     int32_t *text_consumed;
-    uint32_t *cigar;
-    const int64_t *cigar_off;  // [n_pairs + 1]
-    int32_t *cigar_lens;
+    uint32_t *cigar;            // per-pair run scratch
+    const int64_t *cigar_off;   // [n_pairs + 1] scratch offsets (capacity m + n + 1 each)
+    int32_t *cigar_lens;        // [n_pairs] runs written
     uint32_t *spill;                // rows >= rcap, one region per resident pair slot
     int64_t spill_words_per_pair;
     int32_t smem_words_per_warp;
@@ -56,5 +56,16 @@ cudaError_t launch_align(const AlignParams &p, int words, int lanes, int warps_p
 cudaError_t align_occupancy(int words, int lanes, int warps_per_block, size_t smem_bytes, int *blocks_per_sm);
 
 bool align_supported(int words, int lanes);
+
+// Dense CIGAR output (cigar_compact.cu).
+int64_t scan_temp_words(int64_t n);
+// out[0..n]: exclusive prefix sums of in[0..n) (int32 if wide == 0, else int64) and the total.
+cudaError_t exclusive_scan(const void *in, int wide, int64_t n, int64_t *out, int64_t *tmp, cudaStream_t s);
+// cap[p] = text_len[p] + pat_len[p] + 1
+cudaError_t launch_capacity(const int32_t *text_len, const int32_t *pat_len, int32_t n, int64_t *cap, cudaStream_t s);
+// copies each pair's runs to dense[dense_off[p] ..] when they fit below capacity
+cudaError_t launch_compact(const uint32_t *scratch, const int64_t *scratch_off, const int32_t *lens,
+                           const int64_t *dense_off, int32_t n, uint32_t *dense, int64_t capacity, int sm_count,
+                           cudaStream_t s);
 
 }  // namespace scrooge
