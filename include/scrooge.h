@@ -161,6 +161,46 @@ int scrooge_get_kernel_config(const scrooge_ctx *ctx, int32_t words, int32_t *la
  * (d_opt + 1) * text window length), and SM clock cycles the pair took. */
 int scrooge_set_stats(scrooge_ctx *ctx, int32_t *windows, int64_t *rows, int64_t *cells, int64_t *cycles);
 
+/* ------------------------------------------------ allocation-free variant
+ * No counterpart in the paper. For callers that cannot allocate device
+ * memory -- code running while a stream is being captured into a CUDA graph,
+ * or a host application whose device memory is handed out by its own
+ * allocator -- this entry point aligns without calling cudaMalloc, cudaFree
+ * or any allocating routine, and needs no context.
+ *
+ * It runs the same alignment kernel. All pointers are device pointers; the
+ * work is queued on `cuda_stream` (a cudaStream_t, NULL = default stream) on
+ * the current device and the call returns at once unless flags holds
+ * SCROOGE_SYNC. Allowed flags: SCROOGE_SYNC, SCROOGE_NO_DENT, SCROOGE_NO_ET
+ * (SCROOGE_DEVICE_PTRS is implied and ignored).
+ *
+ * Scratch: DP rows that do not fit in shared memory go to a fixed 16 MiB
+ * array (plus one status word) compiled into the library; every GPU that
+ * loads the library holds it until the process exits. The static size caps
+ * how many pairs are resident at once, never how many pairs a call takes;
+ * a W/O/k whose rows would not fit for even one block of pairs returns
+ * SCROOGE_E_INVAL (no supported setting reaches that: the largest, W = 128
+ * without DENT, needs under 2 MiB per block).
+ * Every call shares that array and it keeps the last call's contents, so
+ * calls whose work overlaps on the GPU (different streams, or different
+ * host threads) race; queue them on one stream. The first call on each
+ * device looks up the array's device address and sets kernel attributes;
+ * make that first call before any stream capture.
+ *
+ * Outputs are those of scrooge_align_batch except the CIGAR layout: pair p
+ * writes at most cigar_offsets[p+1] - cigar_offsets[p] runs (cigar_offsets
+ * is an input capacity layout; m + n + 1 runs per pair always suffice) to
+ * cigar[cigar_offsets[p] ..], and cigar_lens[p] receives the runs written.
+ * `status` (device int32, may be NULL) receives 0, or bit 0 if a traceback
+ * found no open edge (impossible by Theorem 1), or bit 1 if some pair's
+ * capacity was too small (its runs are cut at the capacity). */
+int scrooge_align_batch_noalloc(const uint32_t *texts, const int64_t *text_offsets, const int32_t *text_lengths,
+                                const uint32_t *patterns, const int64_t *pattern_offsets,
+                                const int32_t *pattern_lengths, int32_t n_pairs, int32_t W, int32_t O, int32_t k,
+                                uint32_t flags, int32_t *edit_counts, int32_t *text_consumed, uint32_t *cigar,
+                                const int64_t *cigar_offsets, int32_t *cigar_lens, int32_t *status,
+                                void *cuda_stream);
+
 /* Testing hook: make the next `count` device allocations of this context
  * fail with SCROOGE_E_NOMEM (0 switches it off). */
 int scrooge_debug_fail_next_allocs(scrooge_ctx *ctx, int32_t count);

@@ -75,6 +75,8 @@ def load():
                 "scrooge_get_kernel_config": ([P, i32, P, P, P], ctypes.c_int),
                 "scrooge_set_stats": ([P, P, P, P, P], ctypes.c_int),
                 "scrooge_debug_fail_next_allocs": ([P, i32], ctypes.c_int),
+                "scrooge_align_batch_noalloc": ([P, P, P, P, P, P, i32, i32, i32, i32, u32, P, P, P, P, P, P, P],
+                                                ctypes.c_int),
             }
             for name, (args, res) in sig.items():
                 f = getattr(lib, name)
@@ -186,6 +188,20 @@ def scrooge_set_stats(ctx, windows=None, rows=None, cells=None, cycles=None):
 
 def scrooge_debug_fail_next_allocs(ctx, count: int):
     return _check(ctx, load().scrooge_debug_fail_next_allocs(ctx, int(count)))
+
+
+def scrooge_align_batch_noalloc(texts, text_offsets, text_lengths, patterns, pattern_offsets, pattern_lengths,
+                                n_pairs: int, W: int, O: int, k: int, flags: int, edit_counts, text_consumed, cigar,
+                                cigar_offsets, cigar_lens, status=None, stream=None):
+    """Allocation-free alignment (device tensors only); raises ScroogeError on a non-zero return."""
+    rc = load().scrooge_align_batch_noalloc(_ptr(texts), _ptr(text_offsets), _ptr(text_lengths), _ptr(patterns),
+                                            _ptr(pattern_offsets), _ptr(pattern_lengths), int(n_pairs), int(W),
+                                            int(O), int(k), int(flags), _ptr(edit_counts), _ptr(text_consumed),
+                                            _ptr(cigar), _ptr(cigar_offsets), _ptr(cigar_lens), _ptr(status),
+                                            getattr(stream, "cuda_stream", stream))
+    if rc != SCROOGE_OK:
+        raise ScroogeError(rc, "scrooge_align_batch_noalloc failed")
+    return rc
 
 
 # --------------------------------------------------------------- helpers
