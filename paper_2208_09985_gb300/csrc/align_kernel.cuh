@@ -17,10 +17,14 @@
 // R[0][d]: at most G-1 extra rows are touched by the other lanes.
 //
 // Storage. With SENE (Section 2.4.1) only entries are stored; with DENT
-// (Section 2.4.2) only columns 0..W-O and bits 0..W-O. Rows below `rcap` go
-// to shared memory, interleaved over the pairs of the warp; deeper rows go to
-// a per-pair device scratch area. Without SENE the three GenASM edge vectors
-// I, D, M of every cell are stored instead (ablation).
+// (Section 2.4.2) only columns 0..W-O (rounded up to whole lane chunks, so a
+// lane either stores all its columns or none) and the words holding bits
+// 0..W-O. A stored cell is one 4-, 8- or 16-byte vector store. Rows below
+// `rcap` go to shared memory, deeper rows to a per-warp device scratch area;
+// both use the layout [row][column][pair of the warp][word], so a step needs
+// one row pointer and every column store has a compile-time offset. Without
+// SENE the three GenASM edge vectors I, D, M of every cell are stored instead
+// (ablation).
 //
 // Traceback (GenASM-TB, Section 2.2.2) runs on lane G-1 of each pair. Along
 // the path every visited entry holds a 0 (Theorem 1), so when text[i] equals
@@ -104,13 +108,31 @@ struct CigarOut {
     }
 };
 
-template <int NW, int G, bool SENE>
+// Store / load one stored vector of SWP words (SWP = 1, 2 or 4; 4-, 8- or 16-byte aligned).
+template <int SWP, int NW>
+__device__ __forceinline__ void store_vec(uint32_t *p, const uint32_t (&v)[NW]) {
+    if (SWP == 1) {
+        *p = v[0];
+    } else if (SWP == 2) {
+        *reinterpret_cast<uint2 *>(p) = make_uint2(v[0], NW > 1 ? v[NW > 1 ? 1 : 0] : 0u);
+    } else {
+        *reinterpret_cast<uint4 *>(p) = make_uint4(v[0], v[NW > 1 ? 1 : 0], NW > 2 ? v[NW > 2 ? 2 : 0] : 0u,
+                                                    NW > 3 ? v[NW > 3 ? 3 : 0] : 0u);
+    }
+}
+
+__device__ __forceinline__ uint32_t bit_of(uint32_t word, int b) { return (word >> (31 - (b & 31))) & 1u; }
+
+template <int NW, int G, bool SENE, int SWP>
 __global__ void __launch_bounds__(256) align_kernel(const AlignParams p) {
     constexpr int WMAX = 32 * NW;
     constexpr int C = WMAX / G;
     constexpr int PPW = 32 / G;
-    constexpr int NV = SENE ? 1 : 3;  // stored vectors per cell
+    constexpr int NV = SENE ? 1 : 3;       // stored vectors per cell
+    constexpr int CELL = NV * SWP;          // words per stored cell
+    constexpr int COLW = PPW * CELL;        // words between two columns of one row
     static_assert(C * G == WMAX && C <= 32 && 32 % G == 0, "unsupported shape");
+    static_assert(SWP == 1 || SWP == 2 || SWP == 4, "stored words");
 
     extern __shared__ __align__(16) uint32_t smem[];
     const int lane = threadIdx.x & 31;
@@ -119,21 +141,24 @@ __global__ void __launch_bounds__(256) align_kernel(const AlignParams p) {
     const int l = lane - g * G;
     const int tbl = g * G + G - 1;  // traceback lane of this pair (owns column 0)
     const int W = p.W, L = p.W - p.O, k = p.k;
-    const int ncol = p.ncol, sw = p.sw, rcap = p.rcap;
+    const int ncolp = p.ncol, rcap = p.rcap;
     const int colbase = (G - 1 - l) * C;
+    const bool lane_stores = colbase < ncolp;  // stored columns come in whole lane chunks
+    uint32_t tbl_all = 0;                      // one bit per pair: its traceback lane
+#pragma unroll
+    for (int q = 0; q < PPW; ++q) tbl_all |= 1u << (q * G + G - 1);
 
     uint32_t *tab = smem + (int64_t)wib * p.smem_words_per_warp;
     uint32_t *stage = tab + p.table_words_per_warp + g * (4 * (NW + 1));
     const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    uint32_t *spill = p.spill + (gw * PPW + g) * p.spill_words_per_pair;
+    uint32_t *spill = p.spill + gw * p.spill_words_per_pair;  // per warp, same interleaved layout
 
-    // word `w` of stored vector `v` of cell (row, col) of this pair
-    auto cell_ptr = [&](int row, int col, int v) -> uint32_t * {
-        if (row < rcap) return tab + ((((int64_t)row * ncol + col) * NV + v) * sw) * PPW + g;
-        return spill + (((int64_t)(row - rcap) * ncol + col) * NV + v) * sw;
+    // word 0 of column 0 of `row` of this pair (shared memory or scratch)
+    auto row_base = [&](int row) -> uint32_t * {
+        return row < rcap ? tab + ((int64_t)row * ncolp * PPW + g) * CELL
+                          : spill + ((int64_t)(row - rcap) * ncolp * PPW + g) * CELL;
     };
-    auto cell_stride = [&](int row) -> int { return row < rcap ? PPW : 1; };
 
     for (int64_t base = gw * PPW; base < p.n_pairs; base += nwarps * PPW) {
         const int64_t slot = base + g;
@@ -172,7 +197,7 @@ __global__ void __launch_bounds__(256) align_kernel(const AlignParams p) {
             const int mw = active ? min(W, m - pj) : 0;
 
             // ---- window set-up: pattern planes, per-column masks PM[text[i]]
-            uint32_t XA[C][NW];  // X (SENE) or the insertion edge I of the next row
+            uint32_t XA[C][NW];             // X (SENE) or the insertion edge I of the next row
             uint32_t XB[SENE ? 1 : C][NW];  // without SENE: R[i+1][d-1] of the next row
             uint32_t PMC[C][NW];
             {
@@ -184,16 +209,17 @@ __global__ void __launch_bounds__(256) align_kernel(const AlignParams p) {
                 }
                 uint32_t T0, T1;
                 load32(tseq, active ? tblk : 0, ti + colbase, T0, T1);
+                const int real_cols = nw - colbase;  // columns of this lane inside the text window
 #pragma unroll
                 for (int c = 0; c < C; ++c) {
                     const uint32_t m0 = 0u - ((T0 >> (31 - c)) & 1u);
                     const uint32_t m1 = 0u - ((T1 >> (31 - c)) & 1u);
-                    const bool real = colbase + c < nw;
+                    const bool real = c < real_cols;
 #pragma unroll
                     for (int w = 0; w < NW; ++w) {
                         PMC[c][w] = real ? ((P0[w] ^ m0) | (P1[w] ^ m1)) : kFull;
                         XA[c][w] = mm[w];
-                        if (!SENE) XB[c][w] = kFull;
+                        if (!SENE) XB[SENE ? 0 : c][w] = kFull;
                     }
                 }
                 if (active && l == G - 1) {
@@ -211,13 +237,14 @@ __global__ void __launch_bounds__(256) align_kernel(const AlignParams p) {
             }
 
             // ---- GenASM-DC, rows in a pipeline over the lanes of each pair
-            bool dc_done = !active;
+            uint32_t done_mask = __ballot_sync(kFull, l == G - 1 && !active);
             int d_opt = -1;
             uint32_t bottom[NW];
 #pragma unroll
             for (int w = 0; w < NW; ++w) bottom[w] = 0u;
-            for (int s = 0;; ++s) {
+            for (int s = 0; done_mask != tbl_all; ++s) {
                 const int d = s - l;
+                const bool dc_done = (done_mask >> tbl) & 1u;
                 uint32_t pR[NW], pS[NW];
 #pragma unroll
                 for (int w = 0; w < NW; ++w) {
@@ -225,9 +252,10 @@ __global__ void __launch_bounds__(256) align_kernel(const AlignParams p) {
                     // lane 0 starts from the right column R[n][d] = 1..1 << d
                     pR[w] = (l == 0) ? prefix_mask(mw - d - 32 * w) : v;
                 }
-                int found = 0;
+                bool found = false;
                 if (!dc_done && d >= 0 && d <= k) {
                     shl1<NW>(pR, pS);
+                    uint32_t *rowp = row_base(d) + (int64_t)colbase * COLW;
 #pragma unroll
                     for (int c = C - 1; c >= 0; --c) {
                         uint32_t R[NW], S[NW];
@@ -238,7 +266,7 @@ __global__ void __launch_bounds__(256) align_kernel(const AlignParams p) {
                             // row 0 has no I/D/S edges: XA = mask, XB = all ones
                             uint32_t Dd[NW], Sd[NW];
 #pragma unroll
-                            for (int w = 0; w < NW; ++w) Dd[w] = XB[c][w];
+                            for (int w = 0; w < NW; ++w) Dd[w] = XB[SENE ? 0 : c][w];
                             shl1<NW>(Dd, Sd);
 #pragma unroll
                             for (int w = 0; w < NW; ++w) {
@@ -247,25 +275,20 @@ __global__ void __launch_bounds__(256) align_kernel(const AlignParams p) {
                             }
                         }
                         shl1<NW>(R, S);
-                        const int i = colbase + c;
-                        if (i < ncol) {
+                        if (lane_stores) {
                             if (SENE) {
-                                uint32_t *e = cell_ptr(d, i, 0);
-                                const int st = cell_stride(d);
-#pragma unroll
-                                for (int w = 0; w < NW; ++w)
-                                    if (w < sw) e[w * st] = R[w];
+                                store_vec<SWP, NW>(rowp + c * COLW, R);
                             } else if (d > 0) {
                                 // GenASM's stored edges: I, D (S = D << 1) and M
-                                const int st = cell_stride(d);
-                                uint32_t *eI = cell_ptr(d, i, 0), *eD = cell_ptr(d, i, 1), *eM = cell_ptr(d, i, 2);
+                                uint32_t M[NW], Dd[NW];
 #pragma unroll
-                                for (int w = 0; w < NW; ++w)
-                                    if (w < sw) {
-                                        eI[w * st] = XA[c][w];
-                                        eD[w * st] = XB[c][w];
-                                        eM[w * st] = pS[w] | PMC[c][w];
-                                    }
+                                for (int w = 0; w < NW; ++w) {
+                                    M[w] = pS[w] | PMC[c][w];
+                                    Dd[w] = XB[SENE ? 0 : c][w];
+                                }
+                                store_vec<SWP, NW>(rowp + c * COLW, XA[c]);
+                                store_vec<SWP, NW>(rowp + c * COLW + SWP, Dd);
+                                store_vec<SWP, NW>(rowp + c * COLW + 2 * SWP, M);
                             }
                         }
                         if (SENE) {
@@ -274,8 +297,8 @@ __global__ void __launch_bounds__(256) align_kernel(const AlignParams p) {
                         } else {
 #pragma unroll
                             for (int w = 0; w < NW; ++w) {
-                                XA[c][w] = S[w];   // I of cell (i, d+1)
-                                XB[c][w] = pR[w];  // D of cell (i, d+1)
+                                XA[c][w] = S[w];                 // I of cell (i, d+1)
+                                XB[SENE ? 0 : c][w] = pR[w];     // D of cell (i, d+1)
                             }
                         }
 #pragma unroll
@@ -288,13 +311,12 @@ __global__ void __launch_bounds__(256) align_kernel(const AlignParams p) {
                     for (int w = 0; w < NW; ++w) bottom[w] = pR[w];
                     found = (l == G - 1) && ((pR[0] >> 31) == 0u);
                 }
-                const int f = __shfl_sync(kFull, found, tbl);
+                // one vote per step: which pairs reached the window start in this row
+                const uint32_t fmask = __ballot_sync(kFull, found);
                 const int dl = s - (G - 1);  // row finished by the traceback lane
-                if (!dc_done) {
-                    if (f && d_opt < 0) d_opt = dl;
-                    if ((p.et && f) || dl >= k) dc_done = true;
-                }
-                if (__all_sync(kFull, dc_done)) break;
+                if (!dc_done && ((fmask >> tbl) & 1u) && d_opt < 0) d_opt = dl;
+                if (p.et) done_mask |= fmask;
+                if (dl >= k) done_mask = tbl_all;
             }
 
             __syncwarp();  // entries written by every lane are visible to the traceback lane
@@ -309,23 +331,6 @@ __global__ void __launch_bounds__(256) align_kernel(const AlignParams p) {
                     st_cells += (int64_t)(d_opt + 1) * nw;
                     const uint32_t *T0s = stage, *T1s = stage + (NW + 1);
                     const uint32_t *P0s = stage + 2 * (NW + 1), *P1s = stage + 3 * (NW + 1);
-                    // bit `bit` of entry R[col][row] (SENE) -- the right column is implicit
-                    auto entry_bit = [&](int col, int row, int bit) -> uint32_t {
-                        if (bit >= mw) return 0u;
-                        if (col >= nw) return bit < mw - row ? 1u : 0u;
-                        const uint32_t v = cell_ptr(row, col, 0)[(bit >> 5) * cell_stride(row)];
-                        return (v >> (31 - (bit & 31))) & 1u;
-                    };
-                    // bit of edge vector v (0 = I, 1 = D) of cell (col, row), row >= 1
-                    auto edge_bit = [&](int col, int row, int v, int bit) -> uint32_t {
-                        if (bit >= mw) return 0u;
-                        if (col >= nw) {  // right column: I = R[n][d-1] << 1
-                            const int b = bit + 1;
-                            return (b < mw && b < mw - (row - 1)) ? 1u : 0u;
-                        }
-                        const uint32_t w = cell_ptr(row, col, v)[(bit >> 5) * cell_stride(row)];
-                        return (w >> (31 - (bit & 31))) & 1u;
-                    };
                     int i = 0, j = 0, d = d_opt;
                     while (j < mw && i < L && j < L) {
                         const int lim = min(min(nw - i, mw - j), min(L - i, L - j));
@@ -354,13 +359,29 @@ __global__ void __launch_bounds__(256) align_kernel(const AlignParams p) {
                         const bool tx = i < nw;
                         uint32_t bS, bI, bD;
                         if (SENE) {
-                            bS = tx ? entry_bit(i + 1, d - 1, j + 1) : 1u;
-                            bI = entry_bit(i, d - 1, j + 1);
-                            bD = tx ? entry_bit(i + 1, d - 1, j) : 1u;
+                            // entries of row d-1; the right column R[n][d-1] is implicit
+                            const uint32_t *rp = row_base(d - 1);
+                            const int lim_r = mw - (d - 1);  // bits < lim_r of R[n][d-1] are 1
+                            auto ebit = [&](int col, int b) -> uint32_t {
+                                if (b >= mw) return 0u;
+                                if (col >= nw) return b < lim_r ? 1u : 0u;
+                                return bit_of(rp[(int64_t)col * COLW + (b >> 5)], b);
+                            };
+                            bS = tx ? ebit(i + 1, j + 1) : 1u;
+                            bI = ebit(i, j + 1);
+                            bD = tx ? ebit(i + 1, j) : 1u;
                         } else {
-                            bS = tx ? edge_bit(i, d, 1, j + 1) : 1u;
-                            bI = edge_bit(i, d, 0, j);
-                            bD = tx ? edge_bit(i, d, 1, j) : 1u;
+                            // stored edge vectors of cell (i, d)
+                            const uint32_t *rp = row_base(d);
+                            const int lim_r = mw - (d - 1);
+                            auto edge = [&](int v, int b) -> uint32_t {
+                                if (b >= mw) return 0u;
+                                return bit_of(rp[(int64_t)i * COLW + v * SWP + (b >> 5)], b);
+                            };
+                            bS = tx ? edge(1, j + 1) : 1u;
+                            // at the right column, I = R[n][d-1] << 1
+                            bI = tx ? edge(0, j) : ((j + 1 < mw && j + 1 < lim_r) ? 1u : 0u);
+                            bD = tx ? edge(1, j) : 1u;
                         }
                         if (tx && bS == 0u) {
                             out.emit(kOpX, 1);
@@ -389,7 +410,7 @@ __global__ void __launch_bounds__(256) align_kernel(const AlignParams p) {
                     out.flush();
                     p.edit_counts[pair] = failed ? -1 : out.edits;
                     p.text_consumed[pair] = failed ? 0 : ti;
-                    if (out.n > out.cap) atomicOr(p.status, 2);  // impossible: capacity is m + n + 1
+                    if (out.n > out.cap) atomicOr(p.status, 2);  // capacity too small for this pair
                     p.cigar_lens[pair] = failed ? 0 : min(out.n, (int32_t)out.cap);
                     if (p.st_windows) p.st_windows[pair] = st_windows;
                     if (p.st_rows) p.st_rows[pair] = st_rows;

@@ -40,9 +40,9 @@ struct Shape {
 };
 constexpr Shape kShapes[3] = {{2, 16, 2}, {4, 12, 2}, {8, 12, 2}};
 
-template <int NW, int G>
+template <int NW, int G, int SWP>
 cudaError_t prepare_kernel(size_t smem_optin) {
-    return cudaFuncSetAttribute(kern::align_kernel<NW, G, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(kern::align_kernel<NW, G, true, SWP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)smem_optin);
 }
 
@@ -63,8 +63,9 @@ int setup_device(int dev, NoAllocDevice **out) {
             cudaGetLastError();
             return SCROOGE_E_CUDA;
         }
-        if (prepare_kernel<1, 2>(optin) != cudaSuccess || prepare_kernel<2, 4>(optin) != cudaSuccess ||
-            prepare_kernel<4, 8>(optin) != cudaSuccess) {
+        if (prepare_kernel<1, 2, 1>(optin) != cudaSuccess || prepare_kernel<2, 4, 1>(optin) != cudaSuccess ||
+            prepare_kernel<2, 4, 2>(optin) != cudaSuccess || prepare_kernel<4, 8, 1>(optin) != cudaSuccess ||
+            prepare_kernel<4, 8, 2>(optin) != cudaSuccess || prepare_kernel<4, 8, 4>(optin) != cudaSuccess) {
             cudaGetLastError();
             return SCROOGE_E_CUDA;
         }
@@ -78,13 +79,23 @@ int setup_device(int dev, NoAllocDevice **out) {
     return SCROOGE_OK;
 }
 
-template <int NW, int G>
+template <int NW, int G, int SWP>
 cudaError_t launch(const AlignParams &p, int wpb, int blocks, size_t smem, cudaStream_t s, int *per_sm) {
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, kern::align_kernel<NW, G, true>,
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, kern::align_kernel<NW, G, true, SWP>,
                                                                   32 * wpb, smem);
     if (e != cudaSuccess || blocks <= 0) return e;
-    kern::align_kernel<NW, G, true><<<blocks, 32 * wpb, smem, s>>>(p);
+    kern::align_kernel<NW, G, true, SWP><<<blocks, 32 * wpb, smem, s>>>(p);
     return cudaGetLastError();
+}
+
+cudaError_t launch_any(int words, int swp, const AlignParams &p, int wpb, int blocks, size_t smem, cudaStream_t s,
+                       int *per_sm) {
+    if (words == 1) return launch<1, 2, 1>(p, wpb, blocks, smem, s, per_sm);
+    if (words == 2) return swp == 1 ? launch<2, 4, 1>(p, wpb, blocks, smem, s, per_sm)
+                                    : launch<2, 4, 2>(p, wpb, blocks, smem, s, per_sm);
+    return swp == 1 ? launch<4, 8, 1>(p, wpb, blocks, smem, s, per_sm)
+                    : (swp == 2 ? launch<4, 8, 2>(p, wpb, blocks, smem, s, per_sm)
+                                : launch<4, 8, 4>(p, wpb, blocks, smem, s, per_sm));
 }
 
 }  // namespace
@@ -119,8 +130,8 @@ extern "C" int scrooge_align_batch_noalloc(const uint32_t *texts, const int64_t 
     const int words = W <= 32 ? 1 : (W <= 64 ? 2 : 4);
     const Shape sh = kShapes[words == 1 ? 0 : (words == 2 ? 1 : 2)];
     const int PPW = 32 / sh.lanes;
-    const int L = W - O;
     const bool dent = !(flags & SCROOGE_NO_DENT);
+    const TableShape ts = table_shape(W, O, words, sh.lanes, dent, true);
     AlignParams p;
     memset(&p, 0, sizeof p);
     p.texts = texts;
@@ -135,19 +146,18 @@ extern "C" int scrooge_align_batch_noalloc(const uint32_t *texts, const int64_t 
     p.k = k;
     p.et = (flags & SCROOGE_NO_ET) ? 0 : 1;
     p.sene = 1;
-    p.ncol = dent ? std::min(L + 1, W) : W;
-    p.sw = dent ? std::min((L + 1 + 31) / 32, words) : words;
+    p.ncol = ts.ncol;
+    p.sw = ts.swp;
     int rcap = std::min(sh.rows, k + 1);
     const int stage = stage_words_per_warp(words, PPW);
-    while (rcap > 1 && (size_t)sh.wpb * (table_words_per_warp(rcap, p.ncol, p.sw, 1, PPW) + stage) * 4 > d->smem_optin)
-        --rcap;
+    while (rcap > 1 && (size_t)sh.wpb * (table_words_per_warp(rcap, ts, PPW) + stage) * 4 > d->smem_optin) --rcap;
     p.rcap = rcap;
-    p.table_words_per_warp = (int32_t)table_words_per_warp(rcap, p.ncol, p.sw, 1, PPW);
+    p.table_words_per_warp = (int32_t)table_words_per_warp(rcap, ts, PPW);
     p.smem_words_per_warp = p.table_words_per_warp + stage;
     const size_t smem = (size_t)sh.wpb * p.smem_words_per_warp * 4;
-    p.spill_words_per_pair = (int64_t)std::max(0, k + 1 - rcap) * p.ncol * p.sw;
-    // the static row scratch bounds how many pair slots may be resident
-    const int64_t words_per_block = (int64_t)sh.wpb * PPW * std::max<int64_t>(p.spill_words_per_pair, 1);
+    p.spill_words_per_pair = table_words_per_warp(std::max(0, k + 1 - rcap), ts, PPW);  // per warp
+    // the static row scratch bounds how many warps may be resident
+    const int64_t words_per_block = (int64_t)sh.wpb * std::max<int64_t>(p.spill_words_per_pair, 4);
     const int64_t fit_blocks = kNoAllocRowWords / words_per_block;
     if (fit_blocks < 1) return SCROOGE_E_INVAL;  // this W/O/k needs more than the static scratch holds
     p.spill = d->rows;
@@ -164,8 +174,7 @@ extern "C" int scrooge_align_batch_noalloc(const uint32_t *texts, const int64_t 
     int per_sm = 0;
     cudaError_t e;
     // first query occupancy (blocks = 0 launches nothing), then launch
-    e = words == 1 ? launch<1, 2>(p, sh.wpb, 0, smem, st, &per_sm)
-                   : (words == 2 ? launch<2, 4>(p, sh.wpb, 0, smem, st, &per_sm) : launch<4, 8>(p, sh.wpb, 0, smem, st, &per_sm));
+    e = launch_any(words, ts.swp, p, sh.wpb, 0, smem, st, &per_sm);
     if (e != cudaSuccess || per_sm < 1) {
         cudaGetLastError();
         return SCROOGE_E_CUDA;
@@ -173,8 +182,7 @@ extern "C" int scrooge_align_batch_noalloc(const uint32_t *texts, const int64_t 
     const int blocks = (int)std::max<int64_t>(
         1, std::min<int64_t>(std::min<int64_t>(want, (int64_t)per_sm * d->sm_count), fit_blocks));
     int dummy = 0;
-    e = words == 1 ? launch<1, 2>(p, sh.wpb, blocks, smem, st, &dummy)
-                   : (words == 2 ? launch<2, 4>(p, sh.wpb, blocks, smem, st, &dummy) : launch<4, 8>(p, sh.wpb, blocks, smem, st, &dummy));
+    e = launch_any(words, ts.swp, p, sh.wpb, blocks, smem, st, &dummy);
     if (e != cudaSuccess) return SCROOGE_E_CUDA;
     if (status && cudaMemcpyAsync(status, d->status, sizeof(int32_t), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
         return SCROOGE_E_CUDA;

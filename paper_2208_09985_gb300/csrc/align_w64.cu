@@ -3,56 +3,88 @@
 
 namespace scrooge {
 
-cudaError_t launch_align_w64(const AlignParams &p, int lanes, bool sene, int warps_per_block, int blocks,
-                                 size_t smem_bytes, cudaStream_t stream) {
+namespace {
+constexpr int key(int lanes, bool sene, int swp) { return (lanes * 2 + (sene ? 1 : 0)) * 8 + swp; }
+}  // namespace
+
+cudaError_t launch_align_w64(const AlignParams &p, int lanes, bool sene, int swp, int warps_per_block,
+                             int blocks, size_t smem_bytes, cudaStream_t stream) {
     const dim3 grid(blocks), block(32 * warps_per_block);
-    switch (lanes * 2 + (sene ? 1 : 0)) {
-        case 5:
-            kern::align_kernel<2, 2, true><<<grid, block, smem_bytes, stream>>>(p);
+    switch (key(lanes, sene, swp)) {
+        case key(2, true, 1):
+            kern::align_kernel<2, 2, true, 1><<<grid, block, smem_bytes, stream>>>(p);
             return cudaGetLastError();
-        case 4:
-            kern::align_kernel<2, 2, false><<<grid, block, smem_bytes, stream>>>(p);
+        case key(2, true, 2):
+            kern::align_kernel<2, 2, true, 2><<<grid, block, smem_bytes, stream>>>(p);
             return cudaGetLastError();
-        case 9:
-            kern::align_kernel<2, 4, true><<<grid, block, smem_bytes, stream>>>(p);
+        case key(4, true, 1):
+            kern::align_kernel<2, 4, true, 1><<<grid, block, smem_bytes, stream>>>(p);
             return cudaGetLastError();
-        case 8:
-            kern::align_kernel<2, 4, false><<<grid, block, smem_bytes, stream>>>(p);
+        case key(4, true, 2):
+            kern::align_kernel<2, 4, true, 2><<<grid, block, smem_bytes, stream>>>(p);
             return cudaGetLastError();
-        case 17:
-            kern::align_kernel<2, 8, true><<<grid, block, smem_bytes, stream>>>(p);
+        case key(8, true, 1):
+            kern::align_kernel<2, 8, true, 1><<<grid, block, smem_bytes, stream>>>(p);
             return cudaGetLastError();
-        case 16:
-            kern::align_kernel<2, 8, false><<<grid, block, smem_bytes, stream>>>(p);
+        case key(8, true, 2):
+            kern::align_kernel<2, 8, true, 2><<<grid, block, smem_bytes, stream>>>(p);
+            return cudaGetLastError();
+        case key(4, false, 1):
+            kern::align_kernel<2, 4, false, 1><<<grid, block, smem_bytes, stream>>>(p);
+            return cudaGetLastError();
+        case key(4, false, 2):
+            kern::align_kernel<2, 4, false, 2><<<grid, block, smem_bytes, stream>>>(p);
             return cudaGetLastError();
         default:
             return cudaErrorInvalidValue;
     }
 }
 
-cudaError_t occupancy_w64(int lanes, bool sene, int warps_per_block, size_t smem_bytes, int *blocks) {
+cudaError_t occupancy_w64(int lanes, bool sene, int swp, int warps_per_block, size_t smem_bytes, int *blocks) {
     const int threads = 32 * warps_per_block;
-    switch (lanes * 2 + (sene ? 1 : 0)) {
-        case 5:
-            cudaFuncSetAttribute(kern::align_kernel<2, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
-            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kern::align_kernel<2, 2, true>, threads, smem_bytes);
-        case 4:
-            cudaFuncSetAttribute(kern::align_kernel<2, 2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
-            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kern::align_kernel<2, 2, false>, threads, smem_bytes);
-        case 9:
-            cudaFuncSetAttribute(kern::align_kernel<2, 4, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
-            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kern::align_kernel<2, 4, true>, threads, smem_bytes);
-        case 8:
-            cudaFuncSetAttribute(kern::align_kernel<2, 4, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
-            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kern::align_kernel<2, 4, false>, threads, smem_bytes);
-        case 17:
-            cudaFuncSetAttribute(kern::align_kernel<2, 8, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
-            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kern::align_kernel<2, 8, true>, threads, smem_bytes);
-        case 16:
-            cudaFuncSetAttribute(kern::align_kernel<2, 8, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
-            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kern::align_kernel<2, 8, false>, threads, smem_bytes);
+    switch (key(lanes, sene, swp)) {
+        case key(2, true, 1):
+            cudaFuncSetAttribute(kern::align_kernel<2, 2, true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kern::align_kernel<2, 2, true, 1>, threads, smem_bytes);
+        case key(2, true, 2):
+            cudaFuncSetAttribute(kern::align_kernel<2, 2, true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kern::align_kernel<2, 2, true, 2>, threads, smem_bytes);
+        case key(4, true, 1):
+            cudaFuncSetAttribute(kern::align_kernel<2, 4, true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kern::align_kernel<2, 4, true, 1>, threads, smem_bytes);
+        case key(4, true, 2):
+            cudaFuncSetAttribute(kern::align_kernel<2, 4, true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kern::align_kernel<2, 4, true, 2>, threads, smem_bytes);
+        case key(8, true, 1):
+            cudaFuncSetAttribute(kern::align_kernel<2, 8, true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kern::align_kernel<2, 8, true, 1>, threads, smem_bytes);
+        case key(8, true, 2):
+            cudaFuncSetAttribute(kern::align_kernel<2, 8, true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kern::align_kernel<2, 8, true, 2>, threads, smem_bytes);
+        case key(4, false, 1):
+            cudaFuncSetAttribute(kern::align_kernel<2, 4, false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kern::align_kernel<2, 4, false, 1>, threads, smem_bytes);
+        case key(4, false, 2):
+            cudaFuncSetAttribute(kern::align_kernel<2, 4, false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kern::align_kernel<2, 4, false, 2>, threads, smem_bytes);
         default:
             return cudaErrorInvalidValue;
+    }
+}
+
+bool supported_w64(int lanes, bool sene, int swp) {
+    switch (key(lanes, sene, swp)) {
+        case key(2, true, 1):
+        case key(2, true, 2):
+        case key(4, true, 1):
+        case key(4, true, 2):
+        case key(8, true, 1):
+        case key(8, true, 2):
+        case key(4, false, 1):
+        case key(4, false, 2):
+            return true;
+        default:
+            return false;
     }
 }
 

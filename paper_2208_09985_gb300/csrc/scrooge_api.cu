@@ -13,12 +13,6 @@
 #include "scrooge_internal.h"
 
 namespace scrooge {
-cudaError_t launch_align_w32(const AlignParams &, int, bool, int, int, size_t, cudaStream_t);
-cudaError_t launch_align_w64(const AlignParams &, int, bool, int, int, size_t, cudaStream_t);
-cudaError_t launch_align_w128(const AlignParams &, int, bool, int, int, size_t, cudaStream_t);
-cudaError_t occupancy_w32(int, bool, int, size_t, int *);
-cudaError_t occupancy_w64(int, bool, int, size_t, int *);
-cudaError_t occupancy_w128(int, bool, int, size_t, int *);
 
 bool align_supported(int words, int lanes) {
     switch (words) {
@@ -383,37 +377,46 @@ int scrooge_align_batch(scrooge_ctx *c, const uint32_t *texts, const int64_t *te
     // kernel shape
     const int words = words_for(W);
     const KernelConfig kc = c->kcfg[kcfg_index(words)];
-    const int G = kc.lanes, PPW = 32 / G;
-    const int L = W - O;
     const bool sene = !(flags & SCROOGE_NO_SENE);
     const bool dent = !(flags & SCROOGE_NO_DENT);
+    int G = kc.lanes;
+    auto supported = [&](int lanes, int swp) {
+        return words == 1 ? supported_w32(lanes, sene, swp)
+                          : (words == 2 ? supported_w64(lanes, sene, swp) : supported_w128(lanes, sene, swp));
+    };
+    TableShape ts = table_shape(W, O, words, G, dent, sene);
+    if (!supported(G, ts.swp)) {  // the edge-storing ablation exists for the default lane count only
+        G = words == 1 ? 2 : (words == 2 ? 4 : 8);
+        ts = table_shape(W, O, words, G, dent, sene);
+        if (!supported(G, ts.swp)) return fail(c, SCROOGE_E_INVAL, "no kernel for this W/O/flags combination");
+    }
+    const int PPW = 32 / G;
     p.et = (flags & SCROOGE_NO_ET) ? 0 : 1;
     p.sene = sene ? 1 : 0;
-    p.ncol = dent ? std::min(L + 1, W) : W;
-    p.sw = dent ? std::min((L + 1 + 31) / 32, words) : words;
+    p.ncol = ts.ncol;
+    p.sw = ts.swp;
     int rcap = std::min(kc.rows, k + 1);
     const int stage = stage_words_per_warp(words, PPW);
     int wpb = kc.wpb;
     // keep the block's shared memory within the opt-in limit
-    while (rcap > 1 && (size_t)wpb * (table_words_per_warp(rcap, p.ncol, p.sw, p.sene, PPW) + stage) * 4 > c->smem_optin)
-        --rcap;
-    while (wpb > 1 && (size_t)wpb * (table_words_per_warp(rcap, p.ncol, p.sw, p.sene, PPW) + stage) * 4 > c->smem_optin)
-        --wpb;
+    while (rcap > 1 && (size_t)wpb * (table_words_per_warp(rcap, ts, PPW) + stage) * 4 > c->smem_optin) --rcap;
+    while (wpb > 1 && (size_t)wpb * (table_words_per_warp(rcap, ts, PPW) + stage) * 4 > c->smem_optin) --wpb;
     p.rcap = rcap;
-    p.table_words_per_warp = (int32_t)table_words_per_warp(rcap, p.ncol, p.sw, p.sene, PPW);
+    p.table_words_per_warp = (int32_t)table_words_per_warp(rcap, ts, PPW);
     p.smem_words_per_warp = p.table_words_per_warp + stage;
     const size_t smem = (size_t)wpb * p.smem_words_per_warp * 4;
     int per_sm = 0;
-    e = words == 1 ? occupancy_w32(G, sene, wpb, smem, &per_sm)
-                   : (words == 2 ? occupancy_w64(G, sene, wpb, smem, &per_sm) : occupancy_w128(G, sene, wpb, smem, &per_sm));
+    e = words == 1 ? occupancy_w32(G, sene, ts.swp, wpb, smem, &per_sm)
+                   : (words == 2 ? occupancy_w64(G, sene, ts.swp, wpb, smem, &per_sm)
+                                 : occupancy_w128(G, sene, ts.swp, wpb, smem, &per_sm));
     if (e != cudaSuccess) return cuda_fail(c, e, "occupancy query");
     if (per_sm < 1) return fail(c, SCROOGE_E_INVAL, "kernel config does not fit on an SM (smem %zu B)", smem);
     const int64_t groups = ((int64_t)n_pairs + PPW - 1) / PPW;
     const int64_t want_blocks = (groups + wpb - 1) / wpb;
     const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(want_blocks, (int64_t)per_sm * c->sm_count));
     const int spill_rows = std::max(0, k + 1 - rcap);
-    p.spill_words_per_pair = (int64_t)spill_rows * p.ncol * p.sw * (sene ? 1 : 3);
-    const size_t spill_bytes = (size_t)blocks * wpb * PPW * (size_t)std::max<int64_t>(p.spill_words_per_pair, 1) * 4;
+    p.spill_words_per_pair = table_words_per_warp(spill_rows, ts, PPW);  // per warp
+    const size_t spill_bytes = (size_t)blocks * wpb * (size_t)std::max<int64_t>(p.spill_words_per_pair, 4) * 4;
     if ((rc = ensure(c, c->spill, spill_bytes, "DP row scratch")) || (rc = ensure(c, c->status, 64, "status")))
         return rc;
     p.spill = (uint32_t *)c->spill.p;
@@ -423,9 +426,9 @@ int scrooge_align_batch(scrooge_ctx *c, const uint32_t *texts, const int64_t *te
     p.st_cells = c->st_cells;
     p.st_cycles = c->st_cycles;
     if ((e = cudaMemsetAsync(p.status, 0, 4, st)) != cudaSuccess) return cuda_fail(c, e, "status reset");
-    e = words == 1 ? launch_align_w32(p, G, sene, wpb, blocks, smem, st)
-                   : (words == 2 ? launch_align_w64(p, G, sene, wpb, blocks, smem, st)
-                                 : launch_align_w128(p, G, sene, wpb, blocks, smem, st));
+    e = words == 1 ? launch_align_w32(p, G, sene, ts.swp, wpb, blocks, smem, st)
+                   : (words == 2 ? launch_align_w64(p, G, sene, ts.swp, wpb, blocks, smem, st)
+                                 : launch_align_w128(p, G, sene, ts.swp, wpb, blocks, smem, st));
     if (e != cudaSuccess) return cuda_fail(c, e, "alignment kernel launch");
 
     // dense CIGAR: prefix sums of the run counts, then the gather

@@ -16,8 +16,8 @@ struct AlignParams {
     const int32_t *pat_len;
     int32_t n_pairs;
     int32_t W, O, k;
-    int32_t ncol;   // DP columns stored per row (DENT: W-O+1, else W)
-    int32_t sw;     // 32-bit words stored per entry (DENT: ceil((W-O+1)/32), else all)
+    int32_t ncol;   // DP columns stored per row (DENT: W-O+1 rounded up to whole lane chunks, else all)
+    int32_t sw;     // 32-bit words stored per vector (a power of two, the SWP template parameter)
     int32_t rcap;   // rows per pair held in shared memory
     int32_t et;     // 1: stop at the first row that reaches the window start
     int32_t sene;   // 1: store entries; 0: store GenASM's I, D, M edge vectors
@@ -26,8 +26,8 @@ struct AlignParams {
     uint32_t *cigar;            // per-pair run scratch
     const int64_t *cigar_off;   // [n_pairs + 1] scratch offsets (capacity m + n + 1 each)
     int32_t *cigar_lens;        // [n_pairs] runs written
-    uint32_t *spill;                // rows >= rcap, one region per resident pair slot
-    int64_t spill_words_per_pair;
+    uint32_t *spill;                // rows >= rcap, one region per resident warp
+    int64_t spill_words_per_pair;   // words of that region per warp
     int32_t smem_words_per_warp;
     int32_t table_words_per_warp;
     const int32_t *order;   // optional pair order (slot -> pair id)
@@ -39,21 +39,49 @@ struct AlignParams {
     int64_t *st_cycles;
 };
 
-// Words of a stored table row block: rows x columns x words x pairs-per-warp.
-inline int64_t table_words_per_warp(int rcap, int ncol, int sw, int sene, int ppw) {
-    return (int64_t)rcap * ncol * sw * (sene ? 1 : 3) * ppw;
+// Geometry of the stored DP table for one launch.
+struct TableShape {
+    int ncol;  // stored columns (multiple of the lane chunk)
+    int swp;   // stored 32-bit words per vector: 1, 2 or 4
+    int nv;    // stored vectors per cell: 1 (entries) or 3 (GenASM edges)
+};
+
+inline TableShape table_shape(int W, int O, int words, int lanes, bool dent, bool sene) {
+    const int wmax = 32 * words, chunk = wmax / lanes, L = W - O;
+    TableShape t;
+    const int ncol = dent ? (L + 1 < W ? L + 1 : W) : W;
+    t.ncol = ((ncol + chunk - 1) / chunk) * chunk;
+    if (t.ncol > wmax) t.ncol = wmax;
+    int sw = dent ? (L + 1 + 31) / 32 : words;
+    if (sw > words) sw = words;
+    t.swp = sw <= 1 ? 1 : (sw <= 2 ? 2 : 4);
+    t.nv = sene ? 1 : 3;
+    return t;
 }
 
-inline int stage_words_per_warp(int nw, int ppw) { return ppw * 4 * (nw + 1); }
+// Words of one warp's stored rows: rows x columns x pairs-per-warp x cell.
+inline int64_t table_words_per_warp(int rows, const TableShape &t, int ppw) {
+    const int64_t w = (int64_t)rows * t.ncol * ppw * t.nv * t.swp;
+    return (w + 3) & ~(int64_t)3;  // keep 16-byte alignment
+}
 
-// Launches the alignment kernel for `words` 32-bit words per bitvector and
-// `lanes` threads per pair. Returns cudaErrorInvalidValue for an unsupported
-// combination.
-cudaError_t launch_align(const AlignParams &p, int words, int lanes, int warps_per_block, int blocks,
-                         size_t smem_bytes, cudaStream_t stream);
+inline int stage_words_per_warp(int nw, int ppw) { return ((ppw * 4 * (nw + 1)) + 3) & ~3; }
 
-// Resident blocks per SM for that kernel with `smem_bytes` dynamic shared memory.
-cudaError_t align_occupancy(int words, int lanes, int warps_per_block, size_t smem_bytes, int *blocks_per_sm);
+// Per-width launchers of the alignment kernel (align_w32.cu, align_w64.cu,
+// align_w128.cu). `swp` is TableShape::swp. launch_* returns
+// cudaErrorInvalidValue for a combination that is not instantiated.
+cudaError_t launch_align_w32(const AlignParams &, int lanes, bool sene, int swp, int wpb, int blocks, size_t smem,
+                             cudaStream_t);
+cudaError_t launch_align_w64(const AlignParams &, int lanes, bool sene, int swp, int wpb, int blocks, size_t smem,
+                             cudaStream_t);
+cudaError_t launch_align_w128(const AlignParams &, int lanes, bool sene, int swp, int wpb, int blocks, size_t smem,
+                              cudaStream_t);
+cudaError_t occupancy_w32(int lanes, bool sene, int swp, int wpb, size_t smem, int *blocks_per_sm);
+cudaError_t occupancy_w64(int lanes, bool sene, int swp, int wpb, size_t smem, int *blocks_per_sm);
+cudaError_t occupancy_w128(int lanes, bool sene, int swp, int wpb, size_t smem, int *blocks_per_sm);
+bool supported_w32(int lanes, bool sene, int swp);
+bool supported_w64(int lanes, bool sene, int swp);
+bool supported_w128(int lanes, bool sene, int swp);
 
 bool align_supported(int words, int lanes);
 
