@@ -154,6 +154,23 @@ int scrooge_set_kernel_config(scrooge_ctx *ctx, int32_t words, int32_t lanes_per
 int scrooge_get_kernel_config(const scrooge_ctx *ctx, int32_t words, int32_t *lanes_per_pair,
                               int32_t *smem_rows, int32_t *warps_per_block);
 
+/* Autotuner (no counterpart in the paper: it picks implementation
+ * parameters only, so results never change). Times every supported
+ * (lanes_per_pair, smem_rows, warps_per_block) for the window width of W on
+ * the given batch -- arguments as for scrooge_align_batch with
+ * SCROOGE_DEVICE_PTRS, outputs overwritten -- keeping the fastest of
+ * `repeats` timed runs per configuration (CUDA events on the context stream,
+ * after one untimed run), and installs the fastest configuration in the
+ * context. If `results` is not NULL it receives up to max_results rows of 5
+ * int32: lanes, rows, warps, microseconds, 1; *n_results gets the row count.
+ * Synchronous. */
+int scrooge_autotune(scrooge_ctx *ctx, const uint32_t *texts, const int64_t *text_offsets,
+                     const int32_t *text_lengths, const uint32_t *patterns, const int64_t *pattern_offsets,
+                     const int32_t *pattern_lengths, int32_t n_pairs, int32_t W, int32_t O, int32_t k,
+                     uint32_t flags, int32_t *edit_counts, int32_t *text_consumed, uint32_t *cigar,
+                     int64_t cigar_capacity, int64_t *cigar_offsets, int32_t repeats, int32_t *results,
+                     int32_t max_results, int32_t *n_results);
+
 /* Per-pair statistics of the next scrooge_align_batch calls, written to
  * caller-owned DEVICE arrays of n_pairs entries (any may be NULL; all NULL
  * switches statistics off): windows aligned, DP rows computed up to each

@@ -75,6 +75,8 @@ def load():
                 "scrooge_get_kernel_config": ([P, i32, P, P, P], ctypes.c_int),
                 "scrooge_set_stats": ([P, P, P, P, P], ctypes.c_int),
                 "scrooge_debug_fail_next_allocs": ([P, i32], ctypes.c_int),
+                "scrooge_autotune": ([P, P, P, P, P, P, P, i32, i32, i32, i32, u32, P, P, P, i64, P, i32, P, i32,
+                                      P], ctypes.c_int),
                 "scrooge_align_batch_noalloc": ([P, P, P, P, P, P, i32, i32, i32, i32, u32, P, P, P, P, P, P, P],
                                                 ctypes.c_int),
             }
@@ -180,6 +182,30 @@ def scrooge_get_kernel_config(ctx, words: int):
     a, b, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
     _check(ctx, load().scrooge_get_kernel_config(ctx, words, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
     return a.value, b.value, c.value
+
+
+def scrooge_autotune(ctx, texts, text_offsets, text_lengths, patterns, pattern_offsets, pattern_lengths,
+                     n_pairs: int, W: int, O: int, k: int, flags: int, edit_counts, text_consumed, cigar,
+                     cigar_capacity: int, cigar_offsets, repeats: int = 2, max_results: int = 256):
+    """Time every kernel configuration on a device batch; returns rows (lanes, rows, warps, microseconds)."""
+    res = np.zeros((max_results, 5), dtype=np.int32)
+    nres = ctypes.c_int32(0)
+    rc = load().scrooge_autotune(ctx, _ptr(texts), _ptr(text_offsets), _ptr(text_lengths), _ptr(patterns),
+                                 _ptr(pattern_offsets), _ptr(pattern_lengths), int(n_pairs), int(W), int(O), int(k),
+                                 int(flags), _ptr(edit_counts), _ptr(text_consumed), _ptr(cigar),
+                                 int(cigar_capacity), _ptr(cigar_offsets), int(repeats), _ptr(res), max_results,
+                                 ctypes.byref(nres))
+    _check(ctx, rc)
+    return [tuple(int(x) for x in r[:4]) for r in res[: nres.value]]
+
+
+def autotune_device(ctx, db: "DeviceBatch", W: int = 64, O: int = 24, k: int | None = None, flags: int = 0,
+                    repeats: int = 2):
+    """scrooge_autotune on a DeviceBatch; the fastest configuration stays installed in ``ctx``."""
+    k = W if k is None else k
+    return scrooge_autotune(ctx, db.texts, db.text_off, db.text_len, db.patterns, db.pat_off, db.pat_len,
+                            db.n_pairs, W, O, k, flags, db.edit_counts, db.text_consumed, db.cigar,
+                            db.cigar_capacity, db.cigar_off, repeats)
 
 
 def scrooge_set_stats(ctx, windows=None, rows=None, cells=None, cycles=None):

@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(256) align_kernel(const AlignParams p) {
     const int l = lane - g * G;
     const int tbl = g * G + G - 1;  // traceback lane of this pair (owns column 0)
     const int W = p.W, L = p.W - p.O, k = p.k;
-    const int ncolp = p.ncol, rcap = p.rcap;
+    const int ncolp = p.ncol, rcap = p.rcap;  // ncolp: stored columns
     const int colbase = (G - 1 - l) * C;
     const bool lane_stores = colbase < ncolp;  // stored columns come in whole lane chunks
     uint32_t tbl_all = 0;                      // one bit per pair: its traceback lane
@@ -155,9 +155,10 @@ __global__ void __launch_bounds__(256) align_kernel(const AlignParams p) {
     uint32_t *spill = p.spill + gw * p.spill_words_per_pair;  // per warp, same interleaved layout
 
     // word 0 of column 0 of `row` of this pair (shared memory or scratch)
+    const int rstride = p.rstride;
     auto row_base = [&](int row) -> uint32_t * {
-        return row < rcap ? tab + ((int64_t)row * ncolp * PPW + g) * CELL
-                          : spill + ((int64_t)(row - rcap) * ncolp * PPW + g) * CELL;
+        return row < rcap ? tab + ((int64_t)row * rstride + g) * CELL
+                          : spill + ((int64_t)(row - rcap) * rstride + g) * CELL;
     };
 
     for (int64_t base = gw * PPW; base < p.n_pairs; base += nwarps * PPW) {

@@ -45,7 +45,7 @@ struct scrooge_ctx {
     int sm_count = 0;
     size_t smem_optin = 0;
     std::string err;
-    KernelConfig kcfg[3] = {{2, 16, 2}, {4, 12, 2}, {8, 12, 2}};  // words 1, 2, 4
+    KernelConfig kcfg[3] = {{2, 8, 4}, {4, 4, 2}, {8, 8, 2}};  // words 1, 2, 4 (autotuned on GB300)
     int fail_allocs = 0;  // testing hook: fail the next N device allocations
     DevBuf spill, status;
     DevBuf in_text, in_pat, in_toff, in_tlen, in_poff, in_plen;
@@ -395,14 +395,15 @@ int scrooge_align_batch(scrooge_ctx *c, const uint32_t *texts, const int64_t *te
     p.sene = sene ? 1 : 0;
     p.ncol = ts.ncol;
     p.sw = ts.swp;
+    p.rstride = row_stride_cells(ts, PPW, 32 * words / G);
     int rcap = std::min(kc.rows, k + 1);
     const int stage = stage_words_per_warp(words, PPW);
     int wpb = kc.wpb;
     // keep the block's shared memory within the opt-in limit
-    while (rcap > 1 && (size_t)wpb * (table_words_per_warp(rcap, ts, PPW) + stage) * 4 > c->smem_optin) --rcap;
-    while (wpb > 1 && (size_t)wpb * (table_words_per_warp(rcap, ts, PPW) + stage) * 4 > c->smem_optin) --wpb;
+    while (rcap > 1 && (size_t)wpb * (table_words_per_warp(rcap, ts, PPW, 32 * words / G) + stage) * 4 > c->smem_optin) --rcap;
+    while (wpb > 1 && (size_t)wpb * (table_words_per_warp(rcap, ts, PPW, 32 * words / G) + stage) * 4 > c->smem_optin) --wpb;
     p.rcap = rcap;
-    p.table_words_per_warp = (int32_t)table_words_per_warp(rcap, ts, PPW);
+    p.table_words_per_warp = (int32_t)table_words_per_warp(rcap, ts, PPW, 32 * words / G);
     p.smem_words_per_warp = p.table_words_per_warp + stage;
     const size_t smem = (size_t)wpb * p.smem_words_per_warp * 4;
     int per_sm = 0;
@@ -415,7 +416,7 @@ int scrooge_align_batch(scrooge_ctx *c, const uint32_t *texts, const int64_t *te
     const int64_t want_blocks = (groups + wpb - 1) / wpb;
     const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(want_blocks, (int64_t)per_sm * c->sm_count));
     const int spill_rows = std::max(0, k + 1 - rcap);
-    p.spill_words_per_pair = table_words_per_warp(spill_rows, ts, PPW);  // per warp
+    p.spill_words_per_pair = table_words_per_warp(spill_rows, ts, PPW, 32 * words / G);  // per warp
     const size_t spill_bytes = (size_t)blocks * wpb * (size_t)std::max<int64_t>(p.spill_words_per_pair, 4) * 4;
     if ((rc = ensure(c, c->spill, spill_bytes, "DP row scratch")) || (rc = ensure(c, c->status, 64, "status")))
         return rc;
@@ -478,6 +479,74 @@ int scrooge_align_batch(scrooge_ctx *c, const uint32_t *texts, const int64_t *te
         return fail(c, SCROOGE_E_CAPACITY, "CIGAR needs %lld runs, capacity %lld", (long long)total,
                     (long long)cigar_capacity);
     return SCROOGE_OK;
+}
+
+int scrooge_autotune(scrooge_ctx *c, const uint32_t *texts, const int64_t *text_offsets, const int32_t *text_lengths,
+                     const uint32_t *patterns, const int64_t *pattern_offsets, const int32_t *pattern_lengths,
+                     int32_t n_pairs, int32_t W, int32_t O, int32_t k, uint32_t flags, int32_t *edit_counts,
+                     int32_t *text_consumed, uint32_t *cigar, int64_t cigar_capacity, int64_t *cigar_offsets,
+                     int32_t repeats, int32_t *results, int32_t max_results, int32_t *n_results) {
+    if (!c || n_pairs < 1 || repeats < 1) return SCROOGE_E_INVAL;
+    if (W < 1 || W > 128) return fail(c, SCROOGE_E_INVAL, "W=%d outside 1..128", W);
+    const int words = words_for(W);
+    const int ix = kcfg_index(words);
+    const KernelConfig saved = c->kcfg[ix];
+    const int lanes_opts[3][3] = {{1, 2, 4}, {2, 4, 8}, {8, 16, 0}};
+    const int rows_opts[] = {1, 2, 3, 4, 6, 8, 10, 12, 16, 20};
+    const int wpb_opts[] = {1, 2, 4};
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return fail(c, SCROOGE_E_CUDA, "cudaEventCreate failed");
+    float best = -1.f;
+    KernelConfig best_cfg = saved;
+    int nres = 0, rc = SCROOGE_OK;
+    const uint32_t fl = (flags | SCROOGE_DEVICE_PTRS) & ~(uint32_t)SCROOGE_SYNC;
+    for (int li = 0; li < 3 && rc == SCROOGE_OK; ++li) {
+        const int lanes = lanes_opts[ix][li];
+        if (!lanes) continue;
+        for (int rows : rows_opts) {
+            for (int wpb : wpb_opts) {
+                c->kcfg[ix] = {lanes, rows, wpb};
+                // one untimed run, then `repeats` timed runs; keep the fastest
+                rc = scrooge_align_batch(c, texts, text_offsets, text_lengths, patterns, pattern_offsets,
+                                         pattern_lengths, n_pairs, W, O, k, fl, edit_counts, text_consumed, cigar,
+                                         cigar_capacity, cigar_offsets);
+                if (rc != SCROOGE_OK) break;
+                float tmin = -1.f;
+                for (int r = 0; r < repeats && rc == SCROOGE_OK; ++r) {
+                    cudaEventRecord(e0, c->stream);
+                    rc = scrooge_align_batch(c, texts, text_offsets, text_lengths, patterns, pattern_offsets,
+                                             pattern_lengths, n_pairs, W, O, k, fl, edit_counts, text_consumed,
+                                             cigar, cigar_capacity, cigar_offsets);
+                    cudaEventRecord(e1, c->stream);
+                    if (cudaEventSynchronize(e1) != cudaSuccess) rc = fail(c, SCROOGE_E_CUDA, "event sync failed");
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (tmin < 0.f || ms < tmin) tmin = ms;
+                }
+                if (rc != SCROOGE_OK) break;
+                if (results && nres < max_results) {
+                    int32_t *r = results + 5 * nres;
+                    r[0] = lanes;
+                    r[1] = rows;
+                    r[2] = wpb;
+                    r[3] = (int32_t)(tmin * 1000.f);
+                    r[4] = 1;
+                }
+                ++nres;
+                if (best < 0.f || tmin < best) {
+                    best = tmin;
+                    best_cfg = c->kcfg[ix];
+                }
+            }
+            if (rc != SCROOGE_OK) break;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->kcfg[ix] = rc == SCROOGE_OK ? best_cfg : saved;
+    if (n_results) *n_results = std::min(nres, max_results);
+    return rc;
 }
 
 }  // extern "C"

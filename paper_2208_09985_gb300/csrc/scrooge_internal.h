@@ -17,6 +17,7 @@ struct AlignParams {
     int32_t n_pairs;
     int32_t W, O, k;
     int32_t ncol;   // DP columns stored per row (DENT: W-O+1 rounded up to whole lane chunks, else all)
+    int32_t rstride;  // cells between two stored rows (ncol x pairs per warp, padded against bank conflicts)
     int32_t sw;     // 32-bit words stored per vector (a power of two, the SWP template parameter)
     int32_t rcap;   // rows per pair held in shared memory
     int32_t et;     // 1: stop at the first row that reaches the window start
@@ -59,9 +60,28 @@ inline TableShape table_shape(int W, int O, int words, int lanes, bool dent, boo
     return t;
 }
 
-// Words of one warp's stored rows: rows x columns x pairs-per-warp x cell.
-inline int64_t table_words_per_warp(int rows, const TableShape &t, int ppw) {
-    const int64_t w = (int64_t)rows * t.ncol * ppw * t.nv * t.swp;
+// Cells between two rows of one warp's table: ncol x pairs-per-warp, padded so
+// that the lanes of a pair, which store row d - l at column chunk G-1-l in the
+// same step, fall on different shared-memory banks.
+inline int row_stride_cells(const TableShape &t, int ppw, int chunk) {
+    const int cell = t.nv * t.swp;
+    const int group = ppw * cell;  // words one lane slot of all pairs writes per column
+    int rs = t.ncol * ppw;
+    if (group < 32) {
+        for (int pad = 0; pad < 32; ++pad) {
+            const int off = ((rs + pad + chunk * ppw) * cell) % 32;
+            if (off == group % 32) {
+                rs += pad;
+                break;
+            }
+        }
+    }
+    return rs;
+}
+
+// Words of one warp's stored rows.
+inline int64_t table_words_per_warp(int rows, const TableShape &t, int ppw, int chunk) {
+    const int64_t w = (int64_t)rows * row_stride_cells(t, ppw, chunk) * t.nv * t.swp;
     return (w + 3) & ~(int64_t)3;  // keep 16-byte alignment
 }
 
