@@ -58,9 +58,13 @@ typedef struct scrooge_ctx scrooge_ctx; /* opaque, owned by the library */
 #define SCROOGE_NO_DENT (1u << 3) /* store every column and every bit of each entry */
 #define SCROOGE_NO_ET (1u << 4)   /* compute all k+1 rows of every window */
 /* Scheduling (results are identical): */
-#define SCROOGE_PERSISTENT (1u << 5) /* persistent kernel pulling pairs from a device queue */
+#define SCROOGE_PERSISTENT (1u << 5) /* pair slots pull pairs from a device work queue (see scrooge_set_order) */
 #define SCROOGE_LEARNED (1u << 6)    /* order pairs by the MLP's predicted load (implies PERSISTENT) */
-#define SCROOGE_GRAPH (1u << 7)      /* capture the learned/persistent pipeline in a CUDA graph */
+/* Capture the launch sequence (ordering, alignment, CIGAR offsets and gather)
+ * in a CUDA graph, kept in the context and replayed while the same call
+ * (pointers, sizes, W/O/k, flags, kernel settings) repeats. Needs a stream
+ * other than the legacy default stream. */
+#define SCROOGE_GRAPH (1u << 7)
 
 /* CIGAR run encoding: (length << 4) | op, op in SAM codes. */
 #define SCROOGE_OP_I 1  /* base only in the pattern (read): insertion */
@@ -170,6 +174,59 @@ int scrooge_autotune(scrooge_ctx *ctx, const uint32_t *texts, const int64_t *tex
                      uint32_t flags, int32_t *edit_counts, int32_t *text_consumed, uint32_t *cigar,
                      int64_t cigar_capacity, int64_t *cigar_offsets, int32_t repeats, int32_t *results,
                      int32_t max_results, int32_t *n_results);
+
+/* Pair order of later SCROOGE_PERSISTENT calls: order[s] is the pair taken
+ * s-th from the device work queue (a DEVICE array holding a permutation of
+ * 0..n_pairs-1, owned by the caller and read during each call). It applies to
+ * calls with exactly n_pairs pairs; NULL restores the input order. Results do
+ * not depend on the order. */
+int scrooge_set_order(scrooge_ctx *ctx, const int32_t *order, int32_t n_pairs);
+
+/* ------------------------------------------------- learned pair ordering
+ * No counterpart in the paper: a small MLP predicts each pair's per-window
+ * load from cheap features; SCROOGE_LEARNED launches hand pairs to the
+ * persistent kernel heaviest-per-window first (bucketed by predicted load,
+ * then by length class, longest first), so pairs sharing a warp do similar
+ * early-termination work. The order never changes results.
+ *
+ * Features (float32, 6 per pair, row-major): log2(m+1), log2(n+1),
+ * (n-m)/max(m,1), the fraction of sampled pattern 12-mers found in the text
+ * within +-64 positions of the same offset, the spread of the offsets of
+ * those hits (standard deviation / 64), and the fraction of hits within +-16
+ * of their mean offset. Model: 6 -> 64 -> 64 -> 1 with ReLU, inputs
+ * standardised by stored feature means and deviations; the output estimates
+ * log(1 + mean DP rows per window). Parameters (scrooge_model_floats()
+ * floats): W1[64][6], b1[64], W2[64][64], b2[64], w3[64], b3, mean[6], sd[6]. */
+int32_t scrooge_model_floats(void);
+/* Install / read the model (host arrays of scrooge_model_floats() floats). */
+int scrooge_model_set(scrooge_ctx *ctx, const float *params, int32_t n);
+int scrooge_model_get(scrooge_ctx *ctx, float *params, int32_t n);
+/* Features of n_pairs packed pairs (device pointers, as for
+ * scrooge_align_batch) into the DEVICE array features[n_pairs * 6];
+ * asynchronous on the context stream. */
+int scrooge_features(scrooge_ctx *ctx, const uint32_t *texts, const int64_t *text_offsets,
+                     const int32_t *text_lengths, const uint32_t *patterns, const int64_t *pattern_offsets,
+                     const int32_t *pattern_lengths, int32_t n_pairs, float *features);
+/* Model output for n feature rows (device arrays); asynchronous. */
+int scrooge_model_predict(scrooge_ctx *ctx, const float *features, int32_t n, float *pred);
+/* Gradient of the mean squared error of the installed model over n rows
+ * (device features and targets) into the DEVICE array grad (model layout;
+ * the mean/sd entries stay 0); *loss (host, may be NULL) gets the mean
+ * squared error. Synchronous. */
+int scrooge_model_grad(scrooge_ctx *ctx, const float *features, const float *targets, int32_t n, float *grad,
+                       float *loss);
+/* Train a new model on n rows (device features and targets): feature
+ * scaling from the data, seeded initialisation, `epochs` passes of Adam over
+ * shuffled mini-batches of `batch` rows with learning rate lr. The model is
+ * installed in the context; loss_history (host, may be NULL) receives the
+ * mean squared error of each epoch. Synchronous. */
+int scrooge_model_train(scrooge_ctx *ctx, const float *features, const float *targets, int32_t n, int32_t epochs,
+                        int32_t batch, float lr, uint64_t seed, float *loss_history);
+/* The order SCROOGE_LEARNED would use for these pairs, into the DEVICE array
+ * order[n_pairs]; asynchronous. */
+int scrooge_learned_order(scrooge_ctx *ctx, const uint32_t *texts, const int64_t *text_offsets,
+                          const int32_t *text_lengths, const uint32_t *patterns, const int64_t *pattern_offsets,
+                          const int32_t *pattern_lengths, int32_t n_pairs, int32_t *order);
 
 /* Per-pair statistics of the next scrooge_align_batch calls, written to
  * caller-owned DEVICE arrays of n_pairs entries (any may be NULL; all NULL

@@ -74,6 +74,15 @@ def load():
                 "scrooge_set_kernel_config": ([P, i32, i32, i32, i32], ctypes.c_int),
                 "scrooge_get_kernel_config": ([P, i32, P, P, P], ctypes.c_int),
                 "scrooge_set_stats": ([P, P, P, P, P], ctypes.c_int),
+                "scrooge_set_order": ([P, P, i32], ctypes.c_int),
+                "scrooge_model_floats": ([], i32),
+                "scrooge_model_set": ([P, P, i32], ctypes.c_int),
+                "scrooge_model_get": ([P, P, i32], ctypes.c_int),
+                "scrooge_features": ([P, P, P, P, P, P, P, i32, P], ctypes.c_int),
+                "scrooge_model_predict": ([P, P, i32, P], ctypes.c_int),
+                "scrooge_model_grad": ([P, P, P, i32, P, P], ctypes.c_int),
+                "scrooge_model_train": ([P, P, P, i32, i32, i32, ctypes.c_float, ctypes.c_uint64, P], ctypes.c_int),
+                "scrooge_learned_order": ([P, P, P, P, P, P, P, i32, P], ctypes.c_int),
                 "scrooge_debug_fail_next_allocs": ([P, i32], ctypes.c_int),
                 "scrooge_autotune": ([P, P, P, P, P, P, P, i32, i32, i32, i32, u32, P, P, P, i64, P, i32, P, i32,
                                       P], ctypes.c_int),
@@ -206,6 +215,59 @@ def autotune_device(ctx, db: "DeviceBatch", W: int = 64, O: int = 24, k: int | N
     return scrooge_autotune(ctx, db.texts, db.text_off, db.text_len, db.patterns, db.pat_off, db.pat_len,
                             db.n_pairs, W, O, k, flags, db.edit_counts, db.text_consumed, db.cigar,
                             db.cigar_capacity, db.cigar_off, repeats)
+
+
+def scrooge_set_order(ctx, order=None, n_pairs: int = 0):
+    """Pair order (device int32 tensor) of later SCROOGE_PERSISTENT calls; None = input order."""
+    return _check(ctx, load().scrooge_set_order(ctx, _ptr(order), int(n_pairs) if order is not None else 0))
+
+
+def scrooge_model_floats() -> int:
+    return int(load().scrooge_model_floats())
+
+
+def scrooge_model_set(ctx, params: np.ndarray):
+    params = np.ascontiguousarray(params, dtype=np.float32)
+    return _check(ctx, load().scrooge_model_set(ctx, _ptr(params), params.shape[0]))
+
+
+def scrooge_model_get(ctx) -> np.ndarray:
+    out = np.zeros(scrooge_model_floats(), dtype=np.float32)
+    _check(ctx, load().scrooge_model_get(ctx, _ptr(out), out.shape[0]))
+    return out
+
+
+def scrooge_features(ctx, texts, text_offsets, text_lengths, patterns, pattern_offsets, pattern_lengths, n_pairs,
+                     features):
+    return _check(ctx, load().scrooge_features(ctx, _ptr(texts), _ptr(text_offsets), _ptr(text_lengths),
+                                               _ptr(patterns), _ptr(pattern_offsets), _ptr(pattern_lengths),
+                                               int(n_pairs), _ptr(features)))
+
+
+def scrooge_model_predict(ctx, features, n: int, pred):
+    return _check(ctx, load().scrooge_model_predict(ctx, _ptr(features), int(n), _ptr(pred)))
+
+
+def scrooge_model_grad(ctx, features, targets, n: int, grad) -> float:
+    loss = ctypes.c_float(0.0)
+    _check(ctx, load().scrooge_model_grad(ctx, _ptr(features), _ptr(targets), int(n), _ptr(grad),
+                                          ctypes.byref(loss)))
+    return loss.value
+
+
+def scrooge_model_train(ctx, features, targets, n: int, epochs: int = 30, batch: int = 1024, lr: float = 2e-3,
+                        seed: int = 1) -> np.ndarray:
+    hist = np.zeros(epochs, dtype=np.float32)
+    _check(ctx, load().scrooge_model_train(ctx, _ptr(features), _ptr(targets), int(n), int(epochs), int(batch),
+                                           float(lr), int(seed), _ptr(hist)))
+    return hist
+
+
+def scrooge_learned_order(ctx, texts, text_offsets, text_lengths, patterns, pattern_offsets, pattern_lengths,
+                          n_pairs, order):
+    return _check(ctx, load().scrooge_learned_order(ctx, _ptr(texts), _ptr(text_offsets), _ptr(text_lengths),
+                                                    _ptr(patterns), _ptr(pattern_offsets), _ptr(pattern_lengths),
+                                                    int(n_pairs), _ptr(order)))
 
 
 def scrooge_set_stats(ctx, windows=None, rows=None, cells=None, cycles=None):

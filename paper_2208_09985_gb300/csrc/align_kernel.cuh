@@ -161,39 +161,85 @@ __global__ void __launch_bounds__(256) align_kernel(const AlignParams p) {
                           : spill + ((int64_t)(row - rcap) * rstride + g) * CELL;
     };
 
-    for (int64_t base = gw * PPW; base < p.n_pairs; base += nwarps * PPW) {
-        const int64_t slot = base + g;
-        const bool live = slot < p.n_pairs;
-        const int pair = live ? (p.order ? p.order[slot] : (int)slot) : 0;
-        int n = 0, m = 0;
-        const uint2 *tseq = nullptr, *pseq = nullptr;
-        if (live) {
-            n = p.text_len[pair];
-            m = p.pat_len[pair];
-            tseq = reinterpret_cast<const uint2 *>(p.texts + (p.text_off[pair] >> 4));
-            pseq = reinterpret_cast<const uint2 *>(p.patterns + (p.pat_off[pair] >> 4));
+    // Each pair slot of the warp refills itself as soon as its pair is done:
+    // from a fixed stride over the input order (plain launch) or from the
+    // device work queue over `order` (persistent launch). Pairs with an empty
+    // pattern are finished at fetch time.
+    int64_t next_static = gw * PPW + g;
+    bool exhausted = false, active = false;
+    int pair = 0, n = 0, m = 0;
+    const uint2 *tseq = nullptr, *pseq = nullptr;
+    int64_t tblk = 0, pblk = 0;
+    int ti = 0, pj = 0;
+    CigarOut out;
+    out.dst = nullptr;
+    out.cap = 0;
+    out.n = 0;
+    out.cur = 0u;
+    out.edits = 0;
+    int64_t st_rows = 0, st_cells = 0;
+    int32_t st_windows = 0;
+    long long t_start = 0;
+    bool failed = false;
+    for (;;) {
+        if (!active && !exhausted) {
+            int next = -1;
+            if (l == G - 1) {
+                for (;;) {
+                    int64_t sl;
+                    if (p.queue) {
+                        sl = atomicAdd(p.queue, 1);
+                    } else {
+                        sl = next_static;
+                        next_static += nwarps * PPW;
+                    }
+                    if (sl >= p.n_pairs) break;
+                    const int pr = p.order ? p.order[sl] : (int)sl;
+                    if (p.pat_len[pr] > 0) {
+                        next = pr;
+                        break;
+                    }
+                    p.edit_counts[pr] = 0;
+                    p.text_consumed[pr] = 0;
+                    p.cigar_lens[pr] = 0;
+                    if (p.st_windows) p.st_windows[pr] = 0;
+                    if (p.st_rows) p.st_rows[pr] = 0;
+                    if (p.st_cells) p.st_cells[pr] = 0;
+                    if (p.st_cycles) p.st_cycles[pr] = 0;
+                }
+            }
+            const uint32_t gmask = (G == 32) ? kFull : (((1u << G) - 1u) << (g * G));
+            next = __shfl_sync(gmask, next, tbl);
+            if (next < 0) {
+                exhausted = true;
+            } else {
+                pair = next;
+                n = p.text_len[pair];
+                m = p.pat_len[pair];
+                tseq = reinterpret_cast<const uint2 *>(p.texts + (p.text_off[pair] >> 4));
+                pseq = reinterpret_cast<const uint2 *>(p.patterns + (p.pat_off[pair] >> 4));
+                tblk = (n + 31) >> 5;
+                pblk = (m + 31) >> 5;
+                ti = 0;
+                pj = 0;
+                failed = false;
+                st_rows = 0;
+                st_cells = 0;
+                st_windows = 0;
+                if (l == G - 1) {
+                    const int64_t c0 = p.cigar_off[pair];
+                    out.dst = p.cigar + c0;
+                    out.cap = p.cigar_off[pair + 1] - c0;
+                    out.n = 0;
+                    out.cur = 0u;
+                    out.edits = 0;
+                    t_start = clock64();
+                }
+                active = true;
+            }
         }
-        const int64_t tblk = (n + 31) >> 5, pblk = (m + 31) >> 5;
-        int ti = 0, pj = 0;
-        CigarOut out;
-        out.dst = nullptr;
-        out.cap = 0;
-        out.n = 0;
-        out.cur = 0u;
-        out.edits = 0;
-        int64_t st_rows = 0, st_cells = 0;
-        int32_t st_windows = 0;
-        long long t_start = 0;
-        bool failed = false;
-        if (live && l == G - 1) {
-            const int64_t c0 = p.cigar_off[pair];
-            out.dst = p.cigar + c0;
-            out.cap = p.cigar_off[pair + 1] - c0;
-            t_start = clock64();
-        }
-        bool active = live && m > 0;
-
-        while (__any_sync(kFull, active)) {
+        if (!__any_sync(kFull, active)) break;
+        {
             const int nw = active ? min(W, n - ti) : 0;
             const int mw = active ? min(W, m - pj) : 0;
 
@@ -423,15 +469,6 @@ __global__ void __launch_bounds__(256) align_kernel(const AlignParams p) {
             pj = __shfl_sync(kFull, pj, tbl);
             active = __shfl_sync(kFull, (int)active, tbl) != 0;
             __syncwarp();
-        }
-        if (live && m == 0 && l == G - 1) {
-            p.edit_counts[pair] = 0;
-            p.text_consumed[pair] = 0;
-            p.cigar_lens[pair] = 0;
-            if (p.st_windows) p.st_windows[pair] = 0;
-            if (p.st_rows) p.st_rows[pair] = 0;
-            if (p.st_cells) p.st_cells[pair] = 0;
-            if (p.st_cycles) p.st_cycles[pair] = 0;
         }
     }
 }

@@ -9,8 +9,7 @@
 #include <thread>
 #include <vector>
 
-#include "../../include/scrooge.h"
-#include "scrooge_internal.h"
+#include "scrooge_ctx.h"
 
 namespace scrooge {
 
@@ -24,88 +23,9 @@ bool align_supported(int words, int lanes) {
 }
 }  // namespace scrooge
 
+#include "scrooge_ctx.h"
+
 using namespace scrooge;
-
-namespace {
-
-struct DevBuf {
-    void *p = nullptr;
-    size_t bytes = 0;
-};
-
-struct KernelConfig {
-    int lanes, rows, wpb;
-};
-
-}  // namespace
-
-struct scrooge_ctx {
-    int device = 0;
-    cudaStream_t stream = nullptr;
-    int sm_count = 0;
-    size_t smem_optin = 0;
-    std::string err;
-    KernelConfig kcfg[3] = {{2, 8, 4}, {4, 4, 2}, {8, 8, 2}};  // words 1, 2, 4 (autotuned on GB300)
-    int fail_allocs = 0;  // testing hook: fail the next N device allocations
-    DevBuf spill, status;
-    DevBuf in_text, in_pat, in_toff, in_tlen, in_poff, in_plen;
-    DevBuf out_ec, out_tc, out_cig, out_off;
-    DevBuf scr_runs, scr_off, scr_len, scr_cap, scan_tmp;
-    int32_t *st_windows = nullptr;
-    int64_t *st_rows = nullptr, *st_cells = nullptr, *st_cycles = nullptr;
-};
-
-namespace {
-
-int fail(scrooge_ctx *c, int code, const char *fmt, ...) {
-    if (c) {
-        char buf[512];
-        va_list ap;
-        va_start(ap, fmt);
-        vsnprintf(buf, sizeof buf, fmt, ap);
-        va_end(ap);
-        c->err = buf;
-    }
-    return code;
-}
-
-int cuda_fail(scrooge_ctx *c, cudaError_t e, const char *what) {
-    return fail(c, SCROOGE_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
-}
-
-int kcfg_index(int words) { return words == 1 ? 0 : (words == 2 ? 1 : (words == 4 ? 2 : -1)); }
-
-// Grow a device buffer to at least `bytes` (contents are not kept).
-int ensure(scrooge_ctx *c, DevBuf &b, size_t bytes, const char *what) {
-    if (bytes == 0) bytes = 16;
-    if (b.bytes >= bytes) return SCROOGE_OK;
-    if (b.p) cudaFree(b.p);
-    b.p = nullptr;
-    b.bytes = 0;
-    if (c->fail_allocs > 0) {
-        c->fail_allocs -= 1;
-        return fail(c, SCROOGE_E_NOMEM, "device allocation of %zu bytes for %s failed (injected)", bytes, what);
-    }
-    size_t sz = bytes + bytes / 8;  // some headroom for growing batches
-    cudaError_t e = cudaMalloc(&b.p, sz);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return fail(c, SCROOGE_E_NOMEM, "device allocation of %zu bytes for %s failed: %s", sz, what,
-                    cudaGetErrorString(e));
-    }
-    b.bytes = sz;
-    return SCROOGE_OK;
-}
-
-void release(DevBuf &b) {
-    if (b.p) cudaFree(b.p);
-    b.p = nullptr;
-    b.bytes = 0;
-}
-
-int words_for(int W) { return W <= 32 ? 1 : (W <= 64 ? 2 : 4); }
-
-}  // namespace
 
 extern "C" {
 
@@ -143,7 +63,10 @@ int scrooge_destroy(scrooge_ctx *c) {
     cudaSetDevice(c->device);
     DevBuf *all[] = {&c->spill,   &c->status,  &c->in_text, &c->in_pat,   &c->in_toff,  &c->in_tlen,
                      &c->in_poff,   &c->in_plen, &c->out_ec,  &c->out_tc,   &c->out_cig,  &c->out_off,
-                     &c->scr_runs,  &c->scr_off, &c->scr_len, &c->scr_cap,  &c->scan_tmp};
+                     &c->scr_runs,  &c->scr_off, &c->scr_len, &c->scr_cap,  &c->scan_tmp, &c->queue,
+                     &c->model,     &c->grad,    &c->adam_m1, &c->adam_m2,  &c->loss,     &c->l_feat,
+                     &c->l_pred,    &c->l_key,   &c->l_order, &c->l_tmp,    &c->t_rows};
+    if (c->graph) cudaGraphExecDestroy(c->graph);
     for (DevBuf *b : all) release(*b);
     delete c;
     return SCROOGE_OK;
@@ -251,6 +174,13 @@ int scrooge_get_kernel_config(const scrooge_ctx *c, int32_t words, int32_t *lane
     return SCROOGE_OK;
 }
 
+int scrooge_set_order(scrooge_ctx *c, const int32_t *order, int32_t n_pairs) {
+    if (!c || n_pairs < 0 || (order && n_pairs == 0)) return SCROOGE_E_INVAL;
+    c->order = order;
+    c->order_n = order ? n_pairs : 0;
+    return SCROOGE_OK;
+}
+
 int scrooge_set_stats(scrooge_ctx *c, int32_t *windows, int64_t *rows, int64_t *cells, int64_t *cycles) {
     if (!c) return SCROOGE_E_INVAL;
     c->st_windows = windows;
@@ -272,8 +202,9 @@ int scrooge_align_batch(scrooge_ctx *c, const uint32_t *texts, const int64_t *te
     if (O < 0 || O >= W) return fail(c, SCROOGE_E_INVAL, "O=%d outside 0..W-1", O);
     if (k < 0 || k > W) return fail(c, SCROOGE_E_INVAL, "k=%d outside 0..W", k);
     if (cigar_capacity < 0) return fail(c, SCROOGE_E_INVAL, "cigar_capacity < 0");
-    if (flags & (SCROOGE_PERSISTENT | SCROOGE_LEARNED | SCROOGE_GRAPH))
-        return fail(c, SCROOGE_E_INVAL, "scheduling flags are not available in this build");
+    if (flags & SCROOGE_LEARNED) flags |= SCROOGE_PERSISTENT;
+    if ((flags & SCROOGE_LEARNED) && !c->model_ready)
+        return fail(c, SCROOGE_E_NOMODEL, "SCROOGE_LEARNED needs a model (scrooge_model_set or scrooge_model_train)");
     if (!cigar_offsets) return fail(c, SCROOGE_E_INVAL, "null cigar_offsets");
     const bool dev = (flags & SCROOGE_DEVICE_PTRS) != 0;
     cudaError_t e = cudaSetDevice(c->device);
@@ -422,25 +353,90 @@ int scrooge_align_batch(scrooge_ctx *c, const uint32_t *texts, const int64_t *te
         return rc;
     p.spill = (uint32_t *)c->spill.p;
     p.status = (int32_t *)c->status.p;
+    if (flags & SCROOGE_PERSISTENT) {
+        if ((rc = ensure(c, c->queue, 64, "work queue"))) return rc;
+        p.queue = (int32_t *)c->queue.p;
+        p.order = (c->order && c->order_n == n_pairs) ? c->order : nullptr;
+    }
+    if (flags & SCROOGE_LEARNED) {
+        // buffers of the ordering pipeline must exist before any capture
+        const size_t npp = (size_t)std::max(n_pairs, 1);
+        if ((rc = ensure(c, c->l_feat, npp * kFeatures * 4, "features")) ||
+            (rc = ensure(c, c->l_pred, npp * 4, "predictions")) || (rc = ensure(c, c->l_key, npp, "bucket keys")) ||
+            (rc = ensure(c, c->l_order, npp * 4, "pair order")) ||
+            (rc = ensure(c, c->l_tmp, (size_t)sort_temp_words(n_pairs) * 8, "sort scratch")))
+            return rc;
+        p.order = (const int32_t *)c->l_order.p;
+    }
     p.st_windows = c->st_windows;
     p.st_rows = c->st_rows;
     p.st_cells = c->st_cells;
     p.st_cycles = c->st_cycles;
-    if ((e = cudaMemsetAsync(p.status, 0, 4, st)) != cudaSuccess) return cuda_fail(c, e, "status reset");
-    e = words == 1 ? launch_align_w32(p, G, sene, ts.swp, wpb, blocks, smem, st)
-                   : (words == 2 ? launch_align_w64(p, G, sene, ts.swp, wpb, blocks, smem, st)
-                                 : launch_align_w128(p, G, sene, ts.swp, wpb, blocks, smem, st));
-    if (e != cudaSuccess) return cuda_fail(c, e, "alignment kernel launch");
-
-    // dense CIGAR: prefix sums of the run counts, then the gather
     int64_t *dense_off = dev ? cigar_offsets : (int64_t *)c->out_off.p;
-    if ((e = exclusive_scan(p.cigar_lens, 0, n_pairs, dense_off, (int64_t *)c->scan_tmp.p, st)) != cudaSuccess)
-        return cuda_fail(c, e, "CIGAR offsets");
+    // everything from the status reset to the CIGAR offsets, on `st`
+    auto enqueue = [&]() -> int {
+        if ((e = cudaMemsetAsync(p.status, 0, 4, st)) != cudaSuccess) return cuda_fail(c, e, "status reset");
+        if (p.queue && (e = cudaMemsetAsync(p.queue, 0, 4, st)) != cudaSuccess) return cuda_fail(c, e, "queue reset");
+        if (flags & SCROOGE_LEARNED) {
+            const int lrc = learned_order(c, p.texts, p.text_off, p.text_len, p.patterns, p.pat_off, p.pat_len,
+                                          n_pairs);
+            if (lrc) return lrc;
+        }
+        e = words == 1 ? launch_align_w32(p, G, sene, ts.swp, wpb, blocks, smem, st)
+                       : (words == 2 ? launch_align_w64(p, G, sene, ts.swp, wpb, blocks, smem, st)
+                                     : launch_align_w128(p, G, sene, ts.swp, wpb, blocks, smem, st));
+        if (e != cudaSuccess) return cuda_fail(c, e, "alignment kernel launch");
+        // dense CIGAR: prefix sums of the run counts (the gather follows)
+        if ((e = exclusive_scan(p.cigar_lens, 0, n_pairs, dense_off, (int64_t *)c->scan_tmp.p, st)) != cudaSuccess)
+            return cuda_fail(c, e, "CIGAR offsets");
+        if (dev && (e = launch_compact(p.cigar, p.cigar_off, p.cigar_lens, dense_off, n_pairs, cigar, cigar_capacity,
+                                       c->sm_count, st)) != cudaSuccess)
+            return cuda_fail(c, e, "CIGAR gather");
+        return SCROOGE_OK;
+    };
+    if (flags & SCROOGE_GRAPH) {
+        // one captured graph per distinct call; replayed while the call repeats
+        const unsigned long long key[24] = {(unsigned long long)(uintptr_t)p.texts, (unsigned long long)(uintptr_t)p.text_off,
+            (unsigned long long)(uintptr_t)p.text_len, (unsigned long long)(uintptr_t)p.patterns,
+            (unsigned long long)(uintptr_t)p.pat_off, (unsigned long long)(uintptr_t)p.pat_len,
+            (unsigned long long)(uintptr_t)p.edit_counts, (unsigned long long)(uintptr_t)p.text_consumed,
+            (unsigned long long)(uintptr_t)p.cigar, (unsigned long long)(uintptr_t)p.cigar_off,
+            (unsigned long long)(uintptr_t)dense_off, (unsigned long long)(uintptr_t)(dev ? cigar : nullptr),
+            (unsigned long long)cigar_capacity, (unsigned long long)n_pairs,
+            ((unsigned long long)W << 32) | ((unsigned long long)O << 16) | (unsigned long long)k,
+            (unsigned long long)flags, (unsigned long long)(uintptr_t)p.spill, (unsigned long long)(uintptr_t)p.order,
+            (unsigned long long)(uintptr_t)st, ((unsigned long long)G << 32) | (unsigned long long)rcap,
+            ((unsigned long long)wpb << 32) | (unsigned long long)blocks, (unsigned long long)(uintptr_t)c->st_rows,
+            (unsigned long long)(uintptr_t)c->st_cells, (unsigned long long)(uintptr_t)c->st_windows};
+        if (!c->graph || memcmp(key, c->graph_key, sizeof key) != 0) {
+            if (c->graph) {
+                cudaGraphExecDestroy(c->graph);
+                c->graph = nullptr;
+            }
+            cudaGraph_t g = nullptr;
+            if ((e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal)) != cudaSuccess)
+                return cuda_fail(c, e, "stream capture (the stream must not be the legacy default stream)");
+            const int erc = enqueue();
+            cudaError_t ee = cudaStreamEndCapture(st, &g);
+            if (erc) {
+                if (g) cudaGraphDestroy(g);
+                return erc;
+            }
+            if (ee != cudaSuccess) return cuda_fail(c, ee, "stream capture");
+            ee = cudaGraphInstantiate(&c->graph, g, 0);
+            cudaGraphDestroy(g);
+            if (ee != cudaSuccess) {
+                c->graph = nullptr;
+                return cuda_fail(c, ee, "graph instantiation");
+            }
+            memcpy(c->graph_key, key, sizeof key);
+        }
+        if ((e = cudaGraphLaunch(c->graph, st)) != cudaSuccess) return cuda_fail(c, e, "graph launch");
+    } else {
+        if ((rc = enqueue())) return rc;
+    }
     int32_t status_h = 0;
     if (dev) {
-        if ((e = launch_compact(p.cigar, p.cigar_off, p.cigar_lens, dense_off, n_pairs, cigar, cigar_capacity,
-                                c->sm_count, st)) != cudaSuccess)
-            return cuda_fail(c, e, "CIGAR gather");
         if (!(flags & SCROOGE_SYNC)) return SCROOGE_OK;
         int64_t total = 0;
         if ((e = cudaMemcpyAsync(&status_h, p.status, 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||

@@ -6,6 +6,12 @@
 
 namespace scrooge {
 
+// Learned ordering model: kFeatures -> kHidden -> kHidden -> 1, ReLU.
+constexpr int kFeatures = 6;
+constexpr int kHidden = 64;
+// W1, b1, W2, b2, w3, b3, then the feature means and standard deviations
+constexpr int kModelFloats = kHidden * kFeatures + kHidden + kHidden * kHidden + kHidden + kHidden + 1 + 2 * kFeatures;
+
 // Everything one alignment launch needs. All pointers are device pointers.
 struct AlignParams {
     const uint32_t *texts;     // packed bit-plane blocks
@@ -115,5 +121,19 @@ cudaError_t launch_capacity(const int32_t *text_len, const int32_t *pat_len, int
 cudaError_t launch_compact(const uint32_t *scratch, const int64_t *scratch_off, const int32_t *lens,
                            const int64_t *dense_off, int32_t n, uint32_t *dense, int64_t capacity, int sm_count,
                            cudaStream_t s);
+
+// Learned ordering (learn.cu).
+cudaError_t launch_features(const uint32_t *texts, const int64_t *text_off, const int32_t *text_len,
+                            const uint32_t *patterns, const int64_t *pat_off, const int32_t *pat_len, int32_t n,
+                            float *feat, int sm_count, cudaStream_t s);
+cudaError_t launch_mlp_forward(const float *model, const float *feat, int32_t n, float *pred, cudaStream_t s);
+// gradient of the mean squared error over feat/target rows `rows[0..n)` (rows == nullptr: 0..n)
+cudaError_t launch_mlp_grad(const float *model, const float *feat, const float *target, const int32_t *rows,
+                            int32_t n, float *grad, float *loss_sum, int sm_count, cudaStream_t s);
+cudaError_t launch_adam(float *model, const float *grad, float *m1, float *m2, float lr, int step, cudaStream_t s);
+cudaError_t launch_feature_stats(const float *feat, int32_t n, float *model, cudaStream_t s);
+int64_t sort_temp_words(int32_t n);
+cudaError_t launch_learned_order(const float *pred, const int32_t *pat_len, int32_t n, uint8_t *key, int32_t *order,
+                                 int64_t *tmp, cudaStream_t s);
 
 }  // namespace scrooge
