@@ -66,6 +66,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="time budget of the CPU baseline")
+    ap.add_argument("--model", default="", help="saved ordering model (JSON); default: train one first")
+    ap.add_argument("--train-pairs", type=int, default=50_000)
+    ap.add_argument("--train-epochs", type=int, default=30)
     return ap.parse_args()
 
 
@@ -185,6 +188,28 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+PATHS = ("plain", "persistent", "learned", "learned_graph")
+
+
+def path_flags(sc, name: str) -> int:
+    return {"plain": 0, "persistent": sc.SCROOGE_PERSISTENT, "learned": sc.SCROOGE_LEARNED,
+            "learned_graph": sc.SCROOGE_LEARNED | sc.SCROOGE_GRAPH}[name]
+
+
+def prepare_model(sc, ctx, args):
+    """Install the ordering model: from --model, else trained on 50,000 uneven pairs (seed 40)."""
+    from paper_2208_09985_gb300 import learned
+    if args.model:
+        return {"source": args.model, **learned.load_model(ctx, args.model)}
+    t0 = time.perf_counter()
+    train = synth.uneven_reads(args.train_pairs, seed=40)
+    tdb = sc.DeviceBatch(sc.PackedBatch(train))
+    _, hist = learned.train(ctx, tdb, 64, 24, epochs=args.train_epochs, batch=1024, lr=2e-3, seed=1)
+    del tdb
+    return {"source": f"trained here on {args.train_pairs} uneven pairs (seed 40), {args.train_epochs} epochs",
+            "final_mse": float(hist[-1]), "first_mse": float(hist[0]), "seconds": time.perf_counter() - t0}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -202,11 +227,13 @@ def main():
     W, O, k = wl["W"], wl["O"], wl["W"]
     batch = wl["make"](n_pairs, wl["seed"] + 1000 * rank)
     pb = sc.PackedBatch(batch)
-    stream = torch.cuda.current_stream()
+    stream = torch.cuda.Stream()  # graph capture needs a stream other than the legacy default one
+    torch.cuda.set_stream(stream)
     ctx = sc.scrooge_create(local, stream)
+    words = 1 if W <= 32 else (2 if W <= 64 else 4)
+    model_info = prepare_model(sc, ctx, args)
     db = sc.DeviceBatch(pb)
     flags = args.flags
-    words = 1 if W <= 32 else (2 if W <= 64 else 4)
 
     # untimed run with per-pair statistics: algorithmic DP cells of the method
     cells = torch.zeros(n_pairs, dtype=torch.int64, device="cuda")
@@ -217,38 +244,66 @@ def main():
     total_cells = int(cells.sum().item())
     total_rows = int(rows.sum().item())
     ec = db.edit_counts.cpu().numpy()
-    total_runs = int(db.cigar_off[-1].item())
+    ref_off = db.cigar_off.cpu().numpy()
+    total_runs = int(ref_off[-1])
     if (ec < 0).any() or total_runs > db.cigar_capacity:
         raise SystemExit("bench: some pairs failed or the CIGAR buffer is too small")
 
-    for _ in range(args.warmup):
-        sc.align_device(ctx, db, W, O, k, flags)
-    torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
-    clocks = ClockSampler(local)
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    torch.cuda.synchronize()
-    for a, b in evs:
-        a.record(stream)
-        sc.align_device(ctx, db, W, O, k, flags)
-        b.record(stream)
-    torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
-    clk = clocks.stop()
-    step_ms = [a.elapsed_time(b) for a, b in evs]
-    ms = sum(step_ms) / len(step_ms)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * n_pairs / (ms / 1e3)
+    def timed(fl, sampler=False, kernel_events=False):
+        """W warm-up steps, then K steps between CUDA events on the stream; max over ranks."""
+        for _ in range(args.warmup):
+            sc.align_device(ctx, db, W, O, k, fl)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        clocks = ClockSampler(local) if sampler else None
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for a, b in kev:
+            a.record(stream)
+            b.record(stream)
+        torch.cuda.synchronize()
+        for i, (a, b) in enumerate(evs):
+            if kernel_events:
+                sc.scrooge_set_timing_events(ctx, kev[i][0], kev[i][1])
+            a.record(stream)
+            sc.align_device(ctx, db, W, O, k, fl)
+            b.record(stream)
+        torch.cuda.synchronize()
+        sc.scrooge_set_timing_events(ctx)
+        if world > 1:
+            torch.distributed.barrier()
+        clk = clocks.stop() if clocks else None
+        step_ms = [a.elapsed_time(b) for a, b in evs]
+        ker_ms = [a.elapsed_time(b) for a, b in kev] if kernel_events else None
+        ms = sum(step_ms) / len(step_ms)
+        if world > 1:
+            t = torch.tensor([ms], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+        out = sc.device_results(db)
+        if not (np.array_equal(out["edit_counts"], ec) and np.array_equal(out["cigar_off"], ref_off)):
+            raise SystemExit(f"bench: flags {fl} changed the results")
+        return ms, step_ms, ker_ms, clk, sc.scrooge_last_kernel_count(ctx)
+
+    paths = {}
+    for name in PATHS:
+        fl = flags | path_flags(sc, name)
+        ms, step_ms, _, clk, nk = timed(fl, sampler=(name == "learned_graph"))
+        paths[name] = {"ms_per_step": ms, "alignments_per_s": world * n_pairs / (ms / 1e3),
+                       "kernels_per_step": nk, "step_ms": [round(x, 4) for x in step_ms]}
+        if name == "learned_graph":
+            head_ms, head_steps, head_clk, head_kernels = ms, step_ms, clk, nk
+    # the alignment kernel alone, timed inside the learned (non-graph) steps
+    _, _, ker_ms, _, _ = timed(flags | sc.SCROOGE_LEARNED, kernel_events=True)
+    kernel_ms = sum(ker_ms) / len(ker_ms)
+    value = world * n_pairs / (head_ms / 1e3)
     bases = int(np.diff(batch.pattern_off).sum())
 
-    # end to end through the C ABI with pinned host buffers
+    # end to end through the C ABI with pinned host buffers (learned + graph)
     e2e = None
     if not args.no_e2e:
+        fl = flags | sc.SCROOGE_LEARNED | sc.SCROOGE_GRAPH
         pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
         h_in = [pin(x) for x in (pb.texts, pb.text_off, pb.text_len, pb.patterns, pb.pat_off, pb.pat_len)]
         cap = db.cigar_capacity
@@ -256,12 +311,12 @@ def main():
         h_tc = torch.zeros(n_pairs, dtype=torch.int32).pin_memory().numpy()
         h_off = torch.zeros(n_pairs + 1, dtype=torch.int64).pin_memory().numpy()
         h_cig = torch.zeros(cap, dtype=torch.int32).pin_memory().numpy().view(np.uint32)
-        e2e_ctx = sc.scrooge_create(local, stream)
 
         def call():
-            sc.scrooge_align_batch(e2e_ctx, h_in[0], h_in[1], h_in[2], h_in[3], h_in[4], h_in[5], n_pairs, W, O,
-                                   k, flags, h_ec, h_tc, h_cig, cap, h_off)
-        call()
+            sc.scrooge_align_batch(ctx, h_in[0], h_in[1], h_in[2], h_in[3], h_in[4], h_in[5], n_pairs, W, O,
+                                   k, fl, h_ec, h_tc, h_cig, cap, h_off)
+        for _ in range(args.warmup):
+            call()
         e2e_steps = max(2, min(args.steps, 5))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -275,11 +330,11 @@ def main():
             e2e_s = float(t.item())
         h2d = sum(int(x.nbytes) for x in h_in)
         d2h = int(h_ec.nbytes + h_tc.nbytes + h_off.nbytes) + 4 * int(h_off[-1])
-        if not (np.array_equal(h_ec, ec) and int(h_off[-1]) == total_runs):
+        if not (np.array_equal(h_ec, ec) and np.array_equal(h_off, ref_off)):
             raise SystemExit("bench: end-to-end results differ from the device-resident run")
         e2e = {"value": world * n_pairs / e2e_s, "unit": "alignments/s", "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h, "gbases_per_s": world * bases / e2e_s / 1e9}
-        sc.scrooge_destroy(e2e_ctx)
+               "d2h_bytes_per_step": d2h, "gbases_per_s": world * bases / e2e_s / 1e9,
+               "path": "learned + persistent + graph, host buffers"}
 
     if rank != 0:
         sc.scrooge_destroy(ctx)
@@ -287,39 +342,44 @@ def main():
             torch.distributed.destroy_process_group()
         return
 
-    # roofline of the alignment kernel: LOP3/SHF integer pipe
+    # roofline of the alignment kernel: the LOP3/SHF integer pipe
     props = torch.cuda.get_device_properties(local)
     peaks = measured_peaks()
-    sm_max = float(peaks.get("sm_max_mhz") or (clk or {}).get("sm_max_mhz") or 2070.0)
+    sm_max = float(peaks.get("sm_max_mhz") or (head_clk or {}).get("sm_max_mhz") or 2070.0)
     peak_ops = props.multi_processor_count * INT_LOGIC_OPS_PER_CLK_PER_SM * sm_max * 1e6
     ops_per_cell = 3 * words - 1
-    achieved = total_cells * ops_per_cell / (ms / 1e3)
-    traffic = kernel_traffic(words)
+    achieved = total_cells * ops_per_cell / (kernel_ms / 1e3)
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(batch, W, O, args.cpu_seconds)
+    plain = paths["plain"]["alignments_per_s"]
     line = {
         "metric": METRIC, "value": value, "unit": "alignments/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": head_ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32 bit-vectors", "data": "synthetic",
         "config": {"workload": args.workload, "desc": wl["desc"], "pairs_per_gpu": n_pairs, "W": W, "O": O, "k": k,
-                   "path": "plain per-pair launch (static pair order)", "flags": flags,
+                   "path": "learned ordering + persistent work queue + CUDA graph (value); plain, persistent and "
+                           "learned without graph in `paths`", "flags": flags,
                    "kernel_config": list(sc.scrooge_get_kernel_config(ctx, words)),
                    "l2": "inputs larger than L2 (packed inputs %.0f MB)" % (pb.texts.nbytes / 1e6 + pb.patterns.nbytes / 1e6),
                    "parallelism": f"dp{world}" if world > 1 else "single GPU"},
-        "gbases_per_s": world * bases / (ms / 1e3) / 1e9,
+        "gbases_per_s": world * bases / (head_ms / 1e3) / 1e9,
+        "paths": paths, "learned_gain_vs_plain": value / plain,
+        "model": model_info,
         "mean_edits_per_pair": float(ec.mean()), "cigar_runs_per_step": total_runs,
         "dp_cells_per_step": total_cells, "dp_rows_per_step": total_rows,
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
-                     "frac": achieved / peak_ops, "traffic": traffic,
+                     "frac": achieved / peak_ops, "traffic": kernel_traffic(words),
+                     "kernel_ms": kernel_ms,
                      "basis": f"{ops_per_cell} LOP3/SHF ops per DP cell computed up to each window's edit "
-                              f"distance; peak = {props.multi_processor_count} SMs x "
-                              f"{INT_LOGIC_OPS_PER_CLK_PER_SM} ops/clk x {sm_max:.0f} MHz"},
-        "clocks": clk,
-        "gpu_launches": args.steps,
+                              f"distance; alignment kernel timed alone (events around it, learned order); "
+                              f"peak = {props.multi_processor_count} SMs x {INT_LOGIC_OPS_PER_CLK_PER_SM} ops/clk x "
+                              f"{sm_max:.0f} MHz"},
+        "clocks": head_clk,
+        "gpu_launches": args.steps * head_kernels,
         "e2e": e2e,
         "cpu_baseline": cpu,
-        "step_ms": [round(x, 4) for x in step_ms],
+        "step_ms": [round(x, 4) for x in head_steps],
     }
     print(json.dumps(line), flush=True)
     sc.scrooge_destroy(ctx)

@@ -228,6 +228,16 @@ int scrooge_learned_order(scrooge_ctx *ctx, const uint32_t *texts, const int64_t
                           const int32_t *text_lengths, const uint32_t *patterns, const int64_t *pattern_offsets,
                           const int32_t *pattern_lengths, int32_t n_pairs, int32_t *order);
 
+/* Events (cudaEvent_t, caller-owned, may both be NULL) that later
+ * scrooge_align_batch calls record on the context stream right before and
+ * after the alignment kernel, so callers can time that kernel alone. Not
+ * recorded in SCROOGE_GRAPH mode. */
+int scrooge_set_timing_events(scrooge_ctx *ctx, void *start, void *stop);
+
+/* Kernels launched (or replayed in a graph) by the last scrooge_align_batch
+ * call on this context. */
+int32_t scrooge_last_kernel_count(const scrooge_ctx *ctx);
+
 /* Per-pair statistics of the next scrooge_align_batch calls, written to
  * caller-owned DEVICE arrays of n_pairs entries (any may be NULL; all NULL
  * switches statistics off): windows aligned, DP rows computed up to each

@@ -76,6 +76,8 @@ def load():
                 "scrooge_set_stats": ([P, P, P, P, P], ctypes.c_int),
                 "scrooge_set_order": ([P, P, i32], ctypes.c_int),
                 "scrooge_model_floats": ([], i32),
+                "scrooge_set_timing_events": ([P, P, P], ctypes.c_int),
+                "scrooge_last_kernel_count": ([P], i32),
                 "scrooge_model_set": ([P, P, i32], ctypes.c_int),
                 "scrooge_model_get": ([P, P, i32], ctypes.c_int),
                 "scrooge_features": ([P, P, P, P, P, P, P, i32, P], ctypes.c_int),
@@ -220,6 +222,16 @@ def autotune_device(ctx, db: "DeviceBatch", W: int = 64, O: int = 24, k: int | N
 def scrooge_set_order(ctx, order=None, n_pairs: int = 0):
     """Pair order (device int32 tensor) of later SCROOGE_PERSISTENT calls; None = input order."""
     return _check(ctx, load().scrooge_set_order(ctx, _ptr(order), int(n_pairs) if order is not None else 0))
+
+
+def scrooge_set_timing_events(ctx, start=None, stop=None):
+    """torch.cuda.Event pair recorded around the alignment kernel of later calls (None, None = off)."""
+    h = lambda ev: None if ev is None else ev.cuda_event
+    return _check(ctx, load().scrooge_set_timing_events(ctx, h(start), h(stop)))
+
+
+def scrooge_last_kernel_count(ctx) -> int:
+    return int(load().scrooge_last_kernel_count(ctx))
 
 
 def scrooge_model_floats() -> int:

@@ -107,6 +107,12 @@ int64_t scan_temp_words(int64_t n) {
     return words + 2;
 }
 
+int scan_kernel_count(int64_t n) {
+    if (n <= 0) return 0;
+    const int64_t tiles = (n + kScanTile - 1) / kScanTile;
+    return 1 + (tiles > 1 ? scan_kernel_count(tiles) + 1 : 0) + 1;
+}
+
 cudaError_t exclusive_scan(const void *in, int wide, int64_t n, int64_t *out, int64_t *tmp, cudaStream_t s) {
     if (n <= 0) return cudaMemsetAsync(out, 0, sizeof(int64_t), s);
     const int64_t tiles = (n + kScanTile - 1) / kScanTile;

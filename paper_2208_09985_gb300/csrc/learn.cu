@@ -346,6 +346,12 @@ cudaError_t launch_feature_stats(const float *feat, int32_t n, float *model, cud
     return cudaGetLastError();
 }
 
+int learned_kernel_count(int32_t n) {
+    if (n <= 0) return 0;
+    const int64_t nb = ((int64_t)n + kSortTile - 1) / kSortTile;
+    return 2 /* features, MLP */ + 1 /* keys */ + 1 /* histogram */ + scan_kernel_count(256 * nb) + 1 /* scatter */;
+}
+
 int64_t sort_temp_words(int32_t n) {
     const int64_t nb = ((int64_t)n + kSortTile - 1) / kSortTile;
     return 256 * nb * 3 + scan_temp_words(256 * nb) + 8;

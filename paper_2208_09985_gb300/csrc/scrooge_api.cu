@@ -174,6 +174,15 @@ int scrooge_get_kernel_config(const scrooge_ctx *c, int32_t words, int32_t *lane
     return SCROOGE_OK;
 }
 
+int scrooge_set_timing_events(scrooge_ctx *c, void *start, void *stop) {
+    if (!c || (!start) != (!stop)) return SCROOGE_E_INVAL;
+    c->t_start = (cudaEvent_t)start;
+    c->t_stop = (cudaEvent_t)stop;
+    return SCROOGE_OK;
+}
+
+int32_t scrooge_last_kernel_count(const scrooge_ctx *c) { return c ? c->last_kernels : -1; }
+
 int scrooge_set_order(scrooge_ctx *c, const int32_t *order, int32_t n_pairs) {
     if (!c || n_pairs < 0 || (order && n_pairs == 0)) return SCROOGE_E_INVAL;
     c->order = order;
@@ -373,6 +382,8 @@ int scrooge_align_batch(scrooge_ctx *c, const uint32_t *texts, const int64_t *te
     p.st_cells = c->st_cells;
     p.st_cycles = c->st_cycles;
     int64_t *dense_off = dev ? cigar_offsets : (int64_t *)c->out_off.p;
+    c->last_kernels = 1 + scan_kernel_count(n_pairs) + 1;  // alignment, CIGAR offsets, gather
+    if (flags & SCROOGE_LEARNED) c->last_kernels += learned_kernel_count(n_pairs);
     // everything from the status reset to the CIGAR offsets, on `st`
     auto enqueue = [&]() -> int {
         if ((e = cudaMemsetAsync(p.status, 0, 4, st)) != cudaSuccess) return cuda_fail(c, e, "status reset");
@@ -382,10 +393,13 @@ int scrooge_align_batch(scrooge_ctx *c, const uint32_t *texts, const int64_t *te
                                           n_pairs);
             if (lrc) return lrc;
         }
+        const bool timed = c->t_start && c->t_stop && !(flags & SCROOGE_GRAPH);
+        if (timed) cudaEventRecord(c->t_start, st);
         e = words == 1 ? launch_align_w32(p, G, sene, ts.swp, wpb, blocks, smem, st)
                        : (words == 2 ? launch_align_w64(p, G, sene, ts.swp, wpb, blocks, smem, st)
                                      : launch_align_w128(p, G, sene, ts.swp, wpb, blocks, smem, st));
         if (e != cudaSuccess) return cuda_fail(c, e, "alignment kernel launch");
+        if (timed) cudaEventRecord(c->t_stop, st);
         // dense CIGAR: prefix sums of the run counts (the gather follows)
         if ((e = exclusive_scan(p.cigar_lens, 0, n_pairs, dense_off, (int64_t *)c->scan_tmp.p, st)) != cudaSuccess)
             return cuda_fail(c, e, "CIGAR offsets");

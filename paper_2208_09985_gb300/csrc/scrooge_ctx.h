@@ -45,6 +45,9 @@ struct scrooge_ctx {
     scrooge::DevBuf model, grad, adam_m1, adam_m2, loss;
     bool model_ready = false;
     scrooge::DevBuf l_feat, l_pred, l_key, l_order, l_tmp, t_rows;
+    // optional events recorded around the alignment kernel (not in graph mode)
+    cudaEvent_t t_start = nullptr, t_stop = nullptr;
+    int32_t last_kernels = 0;  // kernels launched by the last alignment call
     // CUDA graph of the learned pipeline, keyed by the call it was captured for
     cudaGraphExec_t graph = nullptr;
     unsigned long long graph_key[24] = {0};

@@ -113,6 +113,7 @@ bool align_supported(int words, int lanes);
 
 // Dense CIGAR output (cigar_compact.cu).
 int64_t scan_temp_words(int64_t n);
+int scan_kernel_count(int64_t n);
 // out[0..n]: exclusive prefix sums of in[0..n) (int32 if wide == 0, else int64) and the total.
 cudaError_t exclusive_scan(const void *in, int wide, int64_t n, int64_t *out, int64_t *tmp, cudaStream_t s);
 // cap[p] = text_len[p] + pat_len[p] + 1
@@ -133,6 +134,7 @@ cudaError_t launch_mlp_grad(const float *model, const float *feat, const float *
 cudaError_t launch_adam(float *model, const float *grad, float *m1, float *m2, float lr, int step, cudaStream_t s);
 cudaError_t launch_feature_stats(const float *feat, int32_t n, float *model, cudaStream_t s);
 int64_t sort_temp_words(int32_t n);
+int learned_kernel_count(int32_t n);
 cudaError_t launch_learned_order(const float *pred, const int32_t *pat_len, int32_t n, uint8_t *key, int32_t *order,
                                  int64_t *tmp, cudaStream_t s);
 
