@@ -125,15 +125,16 @@ def measured_peaks():
 def kernel_traffic(words: int):
     """DRAM bytes per launch of the alignment kernel from the committed ncu summary,
     or None when the kernel source changed since the counters were taken."""
-    path = os.path.join(ROOT, "profiles", "align_kernel_traffic.json")
+    path = os.path.join(ROOT, "profiles", "align_kernel_traffic.txt")
     try:
-        rec = json.load(open(path))
+        rec = dict(line.split(": ", 1) for line in open(path).read().splitlines()
+                   if line and not line.startswith("#"))
     except (OSError, ValueError):
         return None
     src = open(os.path.join(ROOT, "paper_2208_09985_gb300", "csrc", "align_kernel.cuh"), "rb").read()
-    if rec.get("source_sha256") != hashlib.sha256(src).hexdigest():
+    if words != 2 or rec.get("source_sha256") != hashlib.sha256(src).hexdigest():
         return None
-    return rec.get("dram_bytes_per_launch")
+    return int(rec["dram_bytes_per_launch"])
 
 
 def cpu_baseline(batch, W, O, budget_s: float):
