@@ -151,7 +151,7 @@ int scrooge_align_batch(scrooge_ctx *ctx, const uint32_t *texts, const int64_t *
  *                    words=2: 2,4,8; words=4: 8,16)
  *   smem_rows        DP rows of each pair kept in shared memory (>= 1); rows
  *                    beyond go to a device scratch area
- *   warps_per_block  1..8
+ *   warps_per_block  1 or 2 (the kernel is compiled for blocks of at most 64 threads)
  * scrooge_get_kernel_config reports the current values. */
 int scrooge_set_kernel_config(scrooge_ctx *ctx, int32_t words, int32_t lanes_per_pair, int32_t smem_rows,
                               int32_t warps_per_block);

@@ -90,15 +90,17 @@ struct CigarOut {
     uint32_t cur;  // pending run (len << 4 | op), 0 = none
     int32_t edits;
 
-    __device__ __forceinline__ void emit(int op, int len) {
-        if (op != kOpEq) edits += len;
-        if (cur != 0u && (int)(cur & 15u) == op) {
-            cur += (uint32_t)len << 4;
-            return;
-        }
-        flush();
-        cur = ((uint32_t)len << 4) | (uint32_t)op;
+    // Append `len` >= 0 operations `op`, merging with the pending run (branch-free).
+    __device__ __forceinline__ void emit_maybe(int op, int len) {
+        const bool any = len > 0;
+        edits += (any && op != kOpEq) ? len : 0;
+        const bool same = cur != 0u && (int)(cur & 15u) == op;
+        const bool spill = any && cur != 0u && !same;
+        if (spill && n < cap) dst[n] = cur;
+        n += spill ? 1 : 0;
+        cur = !any ? cur : (same ? cur + ((uint32_t)len << 4) : (((uint32_t)len << 4) | (uint32_t)op));
     }
+    __device__ __forceinline__ void emit(int op, int len) { emit_maybe(op, len); }
     __device__ __forceinline__ void flush() {
         if (cur != 0u) {
             if (n < cap) dst[n] = cur;
@@ -124,7 +126,7 @@ __device__ __forceinline__ void store_vec(uint32_t *p, const uint32_t (&v)[NW]) 
 __device__ __forceinline__ uint32_t bit_of(uint32_t word, int b) { return (word >> (31 - (b & 31))) & 1u; }
 
 template <int NW, int G, bool SENE, int SWP>
-__global__ void __launch_bounds__(256) align_kernel(const AlignParams p) {
+__global__ void __launch_bounds__(64, 6) align_kernel(const AlignParams p) {
     constexpr int WMAX = 32 * NW;
     constexpr int C = WMAX / G;
     constexpr int PPW = 32 / G;
@@ -368,90 +370,95 @@ __global__ void __launch_bounds__(256) align_kernel(const AlignParams p) {
 
             __syncwarp();  // entries written by every lane are visible to the traceback lane
 
-            // ---- GenASM-TB on the traceback lane
-            if (active && l == G - 1) {
-                st_windows += 1;
-                if (d_opt < 0) {
-                    failed = true;
-                } else {
+            // ---- GenASM-TB: all traceback lanes of the warp step together. One
+            // step takes a run of matches (one XOR + CLZ over 32 packed bases)
+            // and then, unless the window's traceback ends, one S/I/D edge read
+            // from the stored entries; the code is branch-free so the lanes of
+            // different pairs do not diverge.
+            if (l == G - 1) {
+                const bool tb_live = active && d_opt >= 0;
+                if (active) st_windows += 1;
+                if (active && d_opt < 0) failed = true;
+                if (tb_live) {
                     st_rows += d_opt + 1;
                     st_cells += (int64_t)(d_opt + 1) * nw;
-                    const uint32_t *T0s = stage, *T1s = stage + (NW + 1);
-                    const uint32_t *P0s = stage + 2 * (NW + 1), *P1s = stage + 3 * (NW + 1);
-                    int i = 0, j = 0, d = d_opt;
-                    while (j < mw && i < L && j < L) {
+                }
+                const uint32_t *T0s = stage, *T1s = stage + (NW + 1);
+                const uint32_t *P0s = stage + 2 * (NW + 1), *P1s = stage + 3 * (NW + 1);
+                int i = 0, j = 0, d = d_opt;
+                bool going = tb_live && (j < mw && i < L && j < L);
+                while (__any_sync(tbl_all, going)) {
+                    if (going) {
                         const int lim = min(min(nw - i, mw - j), min(L - i, L - j));
-                        if (lim > 0) {
-                            int run = 0;
-                            for (;;) {
-                                const uint32_t x = (stage_ext(T0s, i + run) ^ stage_ext(P0s, j + run)) |
-                                                   (stage_ext(T1s, i + run) ^ stage_ext(P1s, j + run));
-                                const int z = __clz(x);
-                                run += z;
-                                if (z < 32 || run >= lim) break;
-                            }
-                            run = min(run, lim);
-                            if (run > 0) {
-                                out.emit(kOpEq, run);
-                                i += run;
-                                j += run;
-                                if (!(j < mw && i < L && j < L)) break;
-                            }
-                        }
-                        if (d <= 0) {  // no edge can leave row 0 here (Theorem 1)
+                        const uint32_t x = (stage_ext(T0s, i) ^ stage_ext(P0s, j)) |
+                                           (stage_ext(T1s, i) ^ stage_ext(P1s, j));
+                        const int z = __clz(x);
+                        const int run = min(z, lim);
+                        out.emit_maybe(kOpEq, run);
+                        i += run;
+                        j += run;
+                        const bool cont = j < mw && i < L && j < L;
+                        // z == 32 with room left: keep matching in the next step
+                        const bool edit = cont && !(z == 32 && run < lim);
+                        if (edit && d <= 0) {  // no edge can leave row 0 here (Theorem 1)
                             atomicOr(p.status, 1);
                             failed = true;
-                            break;
-                        }
-                        const bool tx = i < nw;
-                        uint32_t bS, bI, bD;
-                        if (SENE) {
-                            // entries of row d-1; the right column R[n][d-1] is implicit
-                            const uint32_t *rp = row_base(d - 1);
-                            const int lim_r = mw - (d - 1);  // bits < lim_r of R[n][d-1] are 1
-                            auto ebit = [&](int col, int b) -> uint32_t {
-                                if (b >= mw) return 0u;
-                                if (col >= nw) return b < lim_r ? 1u : 0u;
-                                return bit_of(rp[(int64_t)col * COLW + (b >> 5)], b);
-                            };
-                            bS = tx ? ebit(i + 1, j + 1) : 1u;
-                            bI = ebit(i, j + 1);
-                            bD = tx ? ebit(i + 1, j) : 1u;
+                            going = false;
+                        } else if (edit) {
+                            const bool tx = i < nw;
+                            const bool j1 = j + 1 < mw;  // bit j+1 exists (else it is the shifted-in 0)
+                            uint32_t bS = 1u, bI = 1u, bD = 1u;
+                            if (SENE) {
+                                // entries of row d-1; the right column R[n][d-1] is implicit
+                                const uint32_t *rp = row_base(d - 1);
+                                const int lim_r = mw - (d - 1);  // bits < lim_r of R[n][d-1] are 1
+                                const int c1 = i + 1, c0 = i;
+                                const uint32_t w1a = (tx && c1 < nw) ? rp[(int64_t)c1 * COLW + (j >> 5)] : 0u;
+                                const uint32_t w1b = (tx && c1 < nw && j1) ? rp[(int64_t)c1 * COLW + ((j + 1) >> 5)] : 0u;
+                                const uint32_t w0b = (c0 < nw && j1) ? rp[(int64_t)c0 * COLW + ((j + 1) >> 5)] : 0u;
+                                const uint32_t r1j = (c1 >= nw) ? (j < lim_r ? 1u : 0u) : bit_of(w1a, j);
+                                const uint32_t r1j1 = !j1 ? 0u : ((c1 >= nw) ? (j + 1 < lim_r ? 1u : 0u) : bit_of(w1b, j + 1));
+                                const uint32_t r0j1 = !j1 ? 0u : ((c0 >= nw) ? (j + 1 < lim_r ? 1u : 0u) : bit_of(w0b, j + 1));
+                                bS = tx ? r1j1 : 1u;
+                                bI = r0j1;
+                                bD = tx ? r1j : 1u;
+                            } else {
+                                // stored edge vectors of cell (i, d)
+                                const uint32_t *rp = row_base(d) + (int64_t)i * COLW;
+                                const int lim_r = mw - (d - 1);
+                                const uint32_t wDa = tx ? rp[SWP + (j >> 5)] : 0u;
+                                const uint32_t wDb = (tx && j1) ? rp[SWP + ((j + 1) >> 5)] : 0u;
+                                const uint32_t wI = tx ? rp[j >> 5] : 0u;
+                                bS = tx ? (j1 ? bit_of(wDb, j + 1) : 0u) : 1u;
+                                // at the right column, I = R[n][d-1] << 1
+                                bI = tx ? bit_of(wI, j) : ((j1 && j + 1 < lim_r) ? 1u : 0u);
+                                bD = tx ? bit_of(wDa, j) : 1u;
+                            }
+                            const bool tS = tx && bS == 0u;
+                            const bool tI = !tS && bI == 0u;
+                            const bool tD = !tS && !tI && tx && bD == 0u;
+                            if (!(tS || tI || tD)) {
+                                atomicOr(p.status, 1);
+                                failed = true;
+                                going = false;
+                            } else {
+                                out.emit(tS ? kOpX : (tI ? kOpI : kOpD), 1);
+                                i += (tS || tD) ? 1 : 0;
+                                j += (tS || tI) ? 1 : 0;
+                                d -= 1;
+                                going = j < mw && i < L && j < L;
+                            }
                         } else {
-                            // stored edge vectors of cell (i, d)
-                            const uint32_t *rp = row_base(d);
-                            const int lim_r = mw - (d - 1);
-                            auto edge = [&](int v, int b) -> uint32_t {
-                                if (b >= mw) return 0u;
-                                return bit_of(rp[(int64_t)i * COLW + v * SWP + (b >> 5)], b);
-                            };
-                            bS = tx ? edge(1, j + 1) : 1u;
-                            // at the right column, I = R[n][d-1] << 1
-                            bI = tx ? edge(0, j) : ((j + 1 < mw && j + 1 < lim_r) ? 1u : 0u);
-                            bD = tx ? edge(1, j) : 1u;
-                        }
-                        if (tx && bS == 0u) {
-                            out.emit(kOpX, 1);
-                            ++i;
-                            ++j;
-                            --d;
-                        } else if (bI == 0u) {
-                            out.emit(kOpI, 1);
-                            ++j;
-                            --d;
-                        } else if (tx && bD == 0u) {
-                            out.emit(kOpD, 1);
-                            ++i;
-                            --d;
-                        } else {
-                            atomicOr(p.status, 1);
-                            failed = true;
-                            break;
+                            going = cont;
                         }
                     }
+                }
+                if (tb_live) {
                     ti += i;
                     pj += j;
                 }
+            }
+            if (active && l == G - 1) {
                 if (failed || pj >= m) {
                     active = false;
                     out.flush();

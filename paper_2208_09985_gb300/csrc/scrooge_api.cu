@@ -157,7 +157,7 @@ int scrooge_pack_2bit(const uint8_t *seqs, const int64_t *offsets, int32_t n_seq
 int scrooge_set_kernel_config(scrooge_ctx *c, int32_t words, int32_t lanes, int32_t rows, int32_t wpb) {
     if (!c) return SCROOGE_E_INVAL;
     const int ix = kcfg_index(words);
-    if (ix < 0 || !align_supported(words, lanes) || rows < 1 || rows > 129 || wpb < 1 || wpb > 8)
+    if (ix < 0 || !align_supported(words, lanes) || rows < 1 || rows > 129 || wpb < 1 || wpb > 2)
         return fail(c, SCROOGE_E_INVAL, "unsupported kernel config words=%d lanes=%d rows=%d warps=%d", words,
                     lanes, rows, wpb);
     c->kcfg[ix] = {lanes, rows, wpb};
@@ -503,7 +503,7 @@ int scrooge_autotune(scrooge_ctx *c, const uint32_t *texts, const int64_t *text_
     const KernelConfig saved = c->kcfg[ix];
     const int lanes_opts[3][3] = {{1, 2, 4}, {2, 4, 8}, {8, 16, 0}};
     const int rows_opts[] = {1, 2, 3, 4, 6, 8, 10, 12, 16, 20};
-    const int wpb_opts[] = {1, 2, 4};
+    const int wpb_opts[] = {1, 2};
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         return fail(c, SCROOGE_E_CUDA, "cudaEventCreate failed");

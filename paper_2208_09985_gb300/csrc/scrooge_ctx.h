@@ -30,7 +30,7 @@ struct scrooge_ctx {
     int sm_count = 0;
     size_t smem_optin = 0;
     std::string err;
-    scrooge::KernelConfig kcfg[3] = {{2, 8, 4}, {4, 4, 2}, {8, 8, 2}};  // words 1, 2, 4 (autotuned on GB300)
+    scrooge::KernelConfig kcfg[3] = {{2, 8, 2}, {4, 4, 2}, {8, 8, 2}};  // words 1, 2, 4 (autotuned on GB300)
     int fail_allocs = 0;  // testing hook: fail the next N device allocations
     scrooge::DevBuf spill, status;
     scrooge::DevBuf in_text, in_pat, in_toff, in_tlen, in_poff, in_plen;
