@@ -65,6 +65,10 @@ typedef struct scrooge_ctx scrooge_ctx; /* opaque, owned by the library */
  * (pointers, sizes, W/O/k, flags, kernel settings) repeats. Needs a stream
  * other than the legacy default stream. */
 #define SCROOGE_GRAPH (1u << 7)
+/* Implementation choice, never a change of results: windows of 33..64 bases
+ * with SENE and ET use the banded kernel unless this flag asks for the
+ * full-width one (see "kernel settings"). */
+#define SCROOGE_NO_BAND (1u << 8)
 
 /* CIGAR run encoding: (length << 4) | op, op in SAM codes. */
 #define SCROOGE_OP_I 1  /* base only in the pattern (read): insertion */
@@ -145,8 +149,14 @@ int scrooge_align_batch(scrooge_ctx *ctx, const uint32_t *texts, const int64_t *
                         int64_t cigar_capacity, int64_t *cigar_offsets);
 
 /* ------------------------------------------------------- kernel settings
- * Implementation parameters of the alignment kernel for windows of up to
- * 32 * words bases (words = 1, 2 or 4). They never change results.
+ * Implementation parameters of the alignment kernels. They never change
+ * results. words = 1, 2 or 4 selects the full-width kernel for windows of up
+ * to 32 * words bases; words = 0 selects the banded kernel, which serves
+ * windows of 33..64 bases when SENE and ET are on (and SCROOGE_NO_BAND is
+ * not given): it keeps the 32 diagonals j - i = -15..16 of each DP entry in
+ * one word, which is exact for every window whose edit distance is at most
+ * 15, and recomputes the other windows at full width (lanes_per_pair 2, 4 or
+ * 8).
  *   lanes_per_pair   threads that share one pair's window (words=1: 1,2,4;
  *                    words=2: 2,4,8; words=4: 8,16)
  *   smem_rows        DP rows of each pair kept in shared memory (>= 1); rows

@@ -39,6 +39,7 @@ SCROOGE_NO_ET = 1 << 4
 SCROOGE_PERSISTENT = 1 << 5
 SCROOGE_LEARNED = 1 << 6
 SCROOGE_GRAPH = 1 << 7
+SCROOGE_NO_BAND = 1 << 8
 
 SCROOGE_OP_I, SCROOGE_OP_D, SCROOGE_OP_EQ, SCROOGE_OP_X = 1, 2, 7, 8
 
@@ -208,6 +209,13 @@ def scrooge_autotune(ctx, texts, text_offsets, text_lengths, patterns, pattern_o
                                  ctypes.byref(nres))
     _check(ctx, rc)
     return [tuple(int(x) for x in r[:4]) for r in res[: nres.value]]
+
+
+def settings_slot(W: int, flags: int = 0) -> int:
+    """The kernel-settings slot (``words`` of scrooge_set_kernel_config) a call with W and flags uses."""
+    if 32 < W <= 64 and not flags & (SCROOGE_NO_SENE | SCROOGE_NO_ET | SCROOGE_NO_BAND):
+        return 0
+    return 1 if W <= 32 else (2 if W <= 64 else 4)
 
 
 def autotune_device(ctx, db: "DeviceBatch", W: int = 64, O: int = 24, k: int | None = None, flags: int = 0,

@@ -1,0 +1,376 @@
+// Banded GenASM alignment kernel for windows of 64 bases (Scrooge, arXiv
+// 2208.09985), with its instantiations and launchers.
+//
+// Coordinates. The full-width kernel (align_kernel.cuh) keeps, for text
+// column i, the W-bit vector R[i][d] indexed by the pattern position j. This
+// kernel keeps only the 32 bits of a band around the main diagonal, indexed
+// by k = j - i + 15, i.e. the diagonals j - i = -15..16, in one 32-bit word
+// V[i][d] (bit k is bit 31 - k, as everywhere). In these coordinates the
+// edges of Algorithm 1 (Section 2.2.1) read
+//     match / substitution (i+1, j+1): V[i+1] bit k      (no shift)
+//     deletion             (i+1, j)  : V[i+1] bit k - 1  (V >> 1)
+//     insertion            (i, j+1)  : V[i]   bit k + 1  (V << 1)
+// so a cell is
+//     V[i][d] = X[i] & (V[i+1][d] | PMrel[i]),
+//     X[i]    = V[i+1][d-1] & (V[i+1][d-1] >> 1) & (V[i][d-1] << 1),
+// where PMrel[i] is the 32-bit window of PM[text[i]] starting at j = i - 15,
+// and the bits shifted in at the band edges are 1 (no path there). The chain
+// along a row is a single 3-input logic op per cell (the shifts act on the
+// previous row), and a cell is one word instead of two.
+//
+// Exactness. A path of the GenASM DP (Theorem 1) that starts at (0, 0) and
+// spends at most d edits keeps |j - i| <= d. Hence for d <= 15:
+//   * bit j = 0 of R[0][d] is 0 in the band exactly when it is 0 in the full
+//     table, so ET (Section 2.4.3) finds the same d_opt;
+//   * every entry the traceback (Section 2.2.2) reads -- (i+1, j+1), (i, j+1),
+//     (i+1, j) at row d-1 from a point reached after d_opt - d edits -- is 0
+//     in the full table only if a path of at most d_opt edits from (0, 0) runs
+//     through it, which stays inside the band; an entry the band does not hold
+//     is therefore 1 in the full table too.
+// So with d_opt <= 15 the band gives the same d_opt and the same traceback,
+// bit for bit. A window with no d_opt <= 15 (about 0.3% of windows at 10%
+// edits) is recomputed at full width (two words per cell, rows in a per-warp
+// device area) by the lanes of its pair before the traceback.
+//
+// The rest -- lanes per pair, the row pipeline over the lanes, rows below
+// `rcap` in shared memory and deeper ones in device scratch, DENT columns,
+// the traceback by runs of matches, the pair queue -- is as in the full-width
+// kernel. ET is always on here.
+#include "align_kernel.cuh"
+
+namespace scrooge {
+namespace kern {
+
+// resident blocks of two warps the register budget is sized for
+template <int G>
+struct BandMinBlocks {
+    static constexpr int value = G == 8 ? 12 : (G == 4 ? 8 : 6);
+};
+
+// Full-width DC of the windows in `full_mask` (Algorithm 1 on two words per
+// entry, as in the full-width kernel), rows stored to `rows` (this lane's first
+// column of row 0; [row][column][pair][2 words]); d_opt of those windows is set
+// on their traceback lanes. Kept out of line: it is rare, and its registers
+// must not count against the banded loop.
+template <int G>
+__device__ __noinline__ void full_width_dc(const uint2 *pseq, int64_t pblk, int pj, const uint2 *tseq, int64_t tblk,
+                                           int ti, int nw, int mw, int k, int l, int tbl, uint32_t tbl_all,
+                                           uint32_t full_mask, bool lane_stores, uint32_t *rows, int row_words,
+                                           int &d_opt) {
+    constexpr int C = 64 / G;
+    constexpr int PPW = 32 / G;
+    const bool full = (full_mask >> tbl) & 1u;
+    const int colbase = (G - 1 - l) * C;
+    uint32_t P0[2], P1[2], T0, T1;
+    load32(pseq, pblk, (int64_t)pj, P0[0], P1[0]);
+    load32(pseq, pblk, (int64_t)pj + 32, P0[1], P1[1]);
+    load32(tseq, tblk, (int64_t)ti + colbase, T0, T1);
+    const int real_cols = nw - colbase;
+    uint32_t FX0[C], FX1[C];  // X of the next row, words 0 and 1
+    const uint32_t mm0 = prefix_mask(mw), mm1 = prefix_mask(mw - 32);
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+        FX0[c] = mm0;
+        FX1[c] = mm1;
+    }
+    uint32_t fdone = tbl_all & ~full_mask;
+    uint32_t bot0 = 0u, bot1 = 0u;
+    for (int st = 0; fdone != tbl_all; ++st) {
+        const int d = st - l;
+        const bool ddone = (fdone >> tbl) & 1u;
+        const uint32_t v0 = __shfl_up_sync(kFull, bot0, 1);
+        const uint32_t v1 = __shfl_up_sync(kFull, bot1, 1);
+        uint32_t pR0 = (l == 0) ? prefix_mask(mw - d) : v0;
+        uint32_t pR1 = (l == 0) ? prefix_mask(mw - d - 32) : v1;
+        bool found = false;
+        if (!ddone && d >= 0 && d <= k) {
+            uint32_t pS0 = __funnelshift_l(pR1, pR0, 1), pS1 = pR1 << 1;
+            uint32_t *rowp = rows + (int64_t)d * row_words;
+#pragma unroll
+            for (int c = C - 1; c >= 0; --c) {
+                // PM[text[i]] of both words from the pattern planes
+                const uint32_t m0 = 0u - ((T0 >> (31 - c)) & 1u);
+                const uint32_t m1 = 0u - ((T1 >> (31 - c)) & 1u);
+                const bool real = c < real_cols;
+                const uint32_t pm0 = real ? ((P0[0] ^ m0) | (P1[0] ^ m1)) : kFull;
+                const uint32_t pm1 = real ? ((P0[1] ^ m0) | (P1[1] ^ m1)) : kFull;
+                const uint32_t R0 = FX0[c] & (pS0 | pm0), R1 = FX1[c] & (pS1 | pm1);
+                const uint32_t S0 = __funnelshift_l(R1, R0, 1), S1 = R1 << 1;
+                if (lane_stores) *reinterpret_cast<uint2 *>(rowp + c * 2 * PPW) = make_uint2(R0, R1);
+                FX0[c] = S0 & pR0 & pS0;
+                FX1[c] = S1 & pR1 & pS1;
+                pR0 = R0;
+                pR1 = R1;
+                pS0 = S0;
+                pS1 = S1;
+            }
+            bot0 = pR0;
+            bot1 = pR1;
+            found = (l == G - 1) && ((pR0 >> 31) == 0u);
+        }
+        const uint32_t fm = __ballot_sync(kFull, found);
+        const int dl = st - (G - 1);
+        if (full && !ddone && ((fm >> tbl) & 1u) && d_opt < 0) d_opt = dl;
+        fdone |= fm;
+        if (dl >= k) fdone = tbl_all;
+    }
+}
+
+template <int G>
+__global__ void __launch_bounds__(64, BandMinBlocks<G>::value) align_band_kernel(const AlignParams p) {
+    constexpr int WMAX = 64;
+    constexpr int C = WMAX / G;
+    constexpr int PPW = 32 / G;
+    constexpr int COLW = PPW;  // words between two columns of one stored band row
+    constexpr int B0 = kBandDiag;
+    static_assert(C * G == WMAX && C <= 32 && 32 % G == 0, "unsupported shape");
+
+    extern __shared__ __align__(16) uint32_t smem[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int g = lane / G;
+    const int l = lane - g * G;
+    const int tbl = g * G + G - 1;  // traceback lane of this pair (owns column 0)
+    const int W = p.W, L = p.W - p.O, k = p.k;
+    const int ncolp = p.ncol, rcap = p.rcap, rstride = p.rstride;
+    const int dmax = min(k, kBandRows - 1);  // deepest row the band computes
+    const int colbase = (G - 1 - l) * C;
+    const bool lane_stores = colbase < ncolp;
+    uint32_t tbl_all = 0;
+#pragma unroll
+    for (int q = 0; q < PPW; ++q) tbl_all |= 1u << (q * G + G - 1);
+
+    uint32_t *tab = smem + (int64_t)wib * p.smem_words_per_warp;
+    uint32_t *stage = tab + p.table_words_per_warp + g * (4 * 3);
+    const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    uint32_t *spill = p.spill + gw * p.spill_words_per_pair;
+    // full-width fallback rows: [row][column][pair][2 words]
+    uint32_t *fb = p.fb ? p.fb + gw * p.fb_words_per_warp : nullptr;
+    const int fb_row = ncolp * PPW * 2;
+
+    // word of (row, column 0) of this pair's band rows (shared memory or scratch)
+    auto band_row = [&](int row) -> uint32_t * {
+        return row < rcap ? tab + row * rstride + g : spill + (row - rcap) * rstride + g;
+    };
+
+    Slot s;
+    slot_init(s, gw * PPW + g);
+    CigarOut out;
+    out.dst = nullptr;
+    out.cap = 0;
+    out.n = 0;
+    out.cur = 0u;
+    out.edits = 0;
+    for (;;) {
+        slot_fetch<G>(p, s, out, l, g, tbl, nwarps * PPW);
+        if (!__any_sync(kFull, s.active)) break;
+        const bool active = s.active;
+        const int nw = active ? min(W, s.n - s.ti) : 0;
+        const int mw = active ? min(W, s.m - s.pj) : 0;
+        const int64_t tblk = active ? s.tblk : 0, pblk = active ? s.pblk : 0;
+
+        // ---- window set-up: band pattern masks and row-0 masks of this lane's columns
+        uint32_t XA[C];   // X of the next row (row 0: bits with j >= m_w cleared)
+        uint32_t PMC[C];  // PMrel[text[i]]
+        {
+            // pattern planes from pj + colbase - 16: column colbase + c starts c + 1 bits in
+            uint32_t Pa0, Pa1, Pb0, Pb1, T0, T1;
+            load32(s.pseq, pblk, (int64_t)s.pj + colbase - 16, Pa0, Pa1);
+            load32(s.pseq, pblk, (int64_t)s.pj + colbase + 16, Pb0, Pb1);
+            load32(s.tseq, tblk, (int64_t)s.ti + colbase, T0, T1);
+            const int real_cols = nw - colbase;
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                const uint32_t m0 = 0u - ((T0 >> (31 - c)) & 1u);
+                const uint32_t m1 = 0u - ((T1 >> (31 - c)) & 1u);
+                const uint32_t w0 = __funnelshift_lc(Pb0, Pa0, c + 1);
+                const uint32_t w1 = __funnelshift_lc(Pb1, Pa1, c + 1);
+                PMC[c] = c < real_cols ? ((w0 ^ m0) | (w1 ^ m1)) : kFull;
+                XA[c] = prefix_mask(mw - (colbase + c) + B0);
+            }
+            if (active && l == G - 1) {
+#pragma unroll
+                for (int w = 0; w <= 2; ++w) {
+                    uint32_t a, b;
+                    load32(s.tseq, s.tblk, (int64_t)s.ti + 32 * w, a, b);
+                    stage[w] = a;
+                    stage[3 + w] = b;
+                    load32(s.pseq, s.pblk, (int64_t)s.pj + 32 * w, a, b);
+                    stage[6 + w] = a;
+                    stage[9 + w] = b;
+                }
+            }
+        }
+
+        // ---- GenASM-DC in the band, rows in a pipeline over the lanes of each pair
+        uint32_t done_mask = __ballot_sync(kFull, l == G - 1 && !active);
+        int d_opt = -1;
+        uint32_t bottom = 0u;
+        for (int st = 0; done_mask != tbl_all; ++st) {
+            const int d = st - l;
+            const bool dc_done = (done_mask >> tbl) & 1u;
+            const uint32_t v = __shfl_up_sync(kFull, bottom, 1);
+            // lane 0 starts from column 64, whose bits j < m_w - d are 1
+            uint32_t pR = (l == 0) ? prefix_mask(mw - d - WMAX + B0) : v;
+            bool found = false;
+            if (!dc_done && d >= 0 && d <= dmax) {
+                uint32_t *rowp = band_row(d) + colbase * COLW;
+#pragma unroll
+                for (int c = C - 1; c >= 0; --c) {
+                    const uint32_t R = XA[c] & (pR | PMC[c]);
+                    if (lane_stores) rowp[c * COLW] = R;
+                    // next row: S = V[i+1][d], D = V[i+1][d] >> 1, I = V[i][d] << 1 (1s shifted in)
+                    XA[c] = pR & __funnelshift_r(pR, kFull, 1) & __funnelshift_l(kFull, R, 1);
+                    pR = R;
+                }
+                bottom = pR;
+                found = (l == G - 1) && (((pR >> (31 - B0)) & 1u) == 0u);
+            }
+            const uint32_t fmask = __ballot_sync(kFull, found);
+            const int dl = st - (G - 1);  // row finished by the traceback lane
+            if (!dc_done && ((fmask >> tbl) & 1u) && d_opt < 0) d_opt = dl;
+            done_mask |= fmask;
+            if (dl >= dmax) done_mask = tbl_all;
+        }
+
+        // ---- windows beyond the band: full-width DC (Algorithm 1 on two words)
+        const uint32_t full_mask = __ballot_sync(kFull, l == G - 1 && active && d_opt < 0 && k >= kBandRows);
+        const bool full = (full_mask >> tbl) & 1u;
+        if (full_mask)
+            full_width_dc<G>(s.pseq, pblk, s.pj, s.tseq, tblk, s.ti, nw, mw, k, l, tbl, tbl_all, full_mask,
+                             lane_stores, fb + ((int64_t)colbase * PPW + g) * 2, fb_row, d_opt);
+
+        __syncwarp();  // entries written by every lane are visible to the traceback lane
+
+        // ---- GenASM-TB (branch-free over the warp's traceback lanes, as in the full-width kernel)
+        if (l == G - 1) {
+            const bool tb_live = active && d_opt >= 0;
+            if (active) s.st_windows += 1;
+            if (active && d_opt < 0) s.failed = true;
+            if (tb_live) {
+                s.st_rows += d_opt + 1;
+                s.st_cells += (int64_t)(d_opt + 1) * nw;
+            }
+            const uint64_t qT0 = ((uint64_t)stage[0] << 32) | stage[1];
+            const uint64_t qT1 = ((uint64_t)stage[3] << 32) | stage[4];
+            const uint64_t qP0 = ((uint64_t)stage[6] << 32) | stage[7];
+            const uint64_t qP1 = ((uint64_t)stage[9] << 32) | stage[10];
+            int i = 0, j = 0, d = d_opt;
+            bool going = tb_live && (j < mw && i < L && j < L);
+            while (__any_sync(tbl_all, going)) {
+                if (going) {
+                    const int lim = min(min(nw - i, mw - j), min(L - i, L - j));
+                    // a match run never reaches past the window: the zeros shifted in are never compared
+                    const uint32_t x = (uint32_t)(((qT0 << i) ^ (qP0 << j)) >> 32) |
+                                       (uint32_t)(((qT1 << i) ^ (qP1 << j)) >> 32);
+                    const int z = __clz(x);
+                    const int run = min(z, lim);
+                    out.emit_maybe(kOpEq, run);
+                    i += run;
+                    j += run;
+                    const bool cont = j < mw && i < L && j < L;
+                    const bool edit = cont && !(z == 32 && run < lim);
+                    if (edit && d <= 0) {  // no edge can leave row 0 here (Theorem 1)
+                        atomicOr(p.status, 1);
+                        s.failed = true;
+                        going = false;
+                    } else if (edit) {
+                        const bool tx = i < nw;
+                        const bool j1 = j + 1 < mw;
+                        const int lim_r = mw - (d - 1);  // bits < lim_r of the right column R[n][d-1] are 1
+                        const int r = d - 1;
+                        const bool ld1 = tx && i + 1 < nw;
+                        // entries (i+1, d-1) and (i, d-1) as 64-bit words; t1 = bits j, j+1 of the
+                        // first, r0b = bit j+1 of the second
+                        uint64_t q1, q0;
+                        int s1, s0;
+                        if (!full) {
+                            const uint32_t *rp = band_row(r) + i * COLW;
+                            const uint32_t v1 = ld1 ? rp[COLW] : 0u;
+                            const uint32_t v0 = tx ? rp[0] : 0u;
+                            const int kk = j - i + B0;  // band bit of (i, j); 0..30 on the path
+                            q1 = (1ull << 63) | ((uint64_t)v1 << 31);  // band bit kk-1 at position kk
+                            q0 = (uint64_t)v0 << 32;
+                            s1 = kk;
+                            s0 = kk + 1;
+                        } else {
+                            const uint2 *fp = reinterpret_cast<const uint2 *>(fb + (int64_t)r * fb_row) + (i * PPW + g);
+                            const uint2 a = ld1 ? fp[PPW] : make_uint2(0u, 0u);
+                            const uint2 b = tx ? fp[0] : make_uint2(0u, 0u);
+                            q1 = ((uint64_t)a.x << 32) | a.y;
+                            q0 = ((uint64_t)b.x << 32) | b.y;
+                            s1 = j;
+                            s0 = j + 1;
+                        }
+                        const uint32_t t1 = (uint32_t)((q1 << s1) >> 62);
+                        const uint32_t r0b = (uint32_t)((q0 << (s0 & 63)) >> 63);  // s0 == 64 only when !j1
+                        const uint32_t r1j = ld1 ? (t1 >> 1) : (j < lim_r ? 1u : 0u);
+                        const uint32_t r1j1 = !j1 ? 0u : (ld1 ? (t1 & 1u) : (j + 1 < lim_r ? 1u : 0u));
+                        const uint32_t r0j1 = !j1 ? 0u : (tx ? r0b : (j + 1 < lim_r ? 1u : 0u));
+                        const uint32_t bS = tx ? r1j1 : 1u;
+                        const uint32_t bI = r0j1;
+                        const uint32_t bD = tx ? r1j : 1u;
+                        const bool tS = tx && bS == 0u;
+                        const bool tI = !tS && bI == 0u;
+                        const bool tD = !tS && !tI && tx && bD == 0u;
+                        if (!(tS || tI || tD)) {
+                            atomicOr(p.status, 1);
+                            s.failed = true;
+                            going = false;
+                        } else {
+                            out.emit(tS ? kOpX : (tI ? kOpI : kOpD), 1);
+                            i += (tS || tD) ? 1 : 0;
+                            j += (tS || tI) ? 1 : 0;
+                            d -= 1;
+                            going = j < mw && i < L && j < L;
+                        }
+                    } else {
+                        going = cont;
+                    }
+                }
+            }
+            if (tb_live) {
+                s.ti += i;
+                s.pj += j;
+            }
+        }
+        slot_window_done<G>(p, s, out, l, tbl);
+    }
+}
+
+template <int G>
+cudaError_t launch_g(const AlignParams &p, int wpb, int blocks, size_t smem, cudaStream_t st) {
+    align_band_kernel<G><<<blocks, 32 * wpb, smem, st>>>(p);
+    return cudaGetLastError();
+}
+
+template <int G>
+cudaError_t occupancy_g(int wpb, size_t smem, int *per_sm) {
+    cudaFuncSetAttribute(align_band_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, align_band_kernel<G>, 32 * wpb, smem);
+}
+
+}  // namespace kern
+
+cudaError_t launch_align_band(const AlignParams &p, int lanes, int wpb, int blocks, size_t smem, cudaStream_t st) {
+    switch (lanes) {
+        case 2: return kern::launch_g<2>(p, wpb, blocks, smem, st);
+        case 4: return kern::launch_g<4>(p, wpb, blocks, smem, st);
+        case 8: return kern::launch_g<8>(p, wpb, blocks, smem, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t occupancy_band(int lanes, int wpb, size_t smem, int *per_sm) {
+    switch (lanes) {
+        case 2: return kern::occupancy_g<2>(wpb, smem, per_sm);
+        case 4: return kern::occupancy_g<4>(wpb, smem, per_sm);
+        case 8: return kern::occupancy_g<8>(wpb, smem, per_sm);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+bool supported_band(int lanes) { return lanes == 2 || lanes == 4 || lanes == 8; }
+
+}  // namespace scrooge

@@ -125,6 +125,137 @@ __device__ __forceinline__ void store_vec(uint32_t *p, const uint32_t (&v)[NW]) 
 
 __device__ __forceinline__ uint32_t bit_of(uint32_t word, int b) { return (word >> (31 - (b & 31))) & 1u; }
 
+// Bits j and j+1 of a stored entry of SWP words, as (bit j) << 1 | bit j+1;
+// a bit past the stored words reads 0. One vector load per entry.
+template <int SWP>
+__device__ __forceinline__ uint32_t entry_bits2(const uint32_t *e, int j) {
+    if (SWP == 1) {
+        const uint64_t q = (uint64_t)(*e) << 32;
+        return (uint32_t)((q << j) >> 62);
+    } else if (SWP == 2) {
+        const uint2 v = *reinterpret_cast<const uint2 *>(e);
+        const uint64_t q = ((uint64_t)v.x << 32) | v.y;
+        return (uint32_t)((q << j) >> 62);
+    } else {
+        const uint4 v = *reinterpret_cast<const uint4 *>(e);
+        const int w = j >> 5;
+        const uint32_t a = w == 0 ? v.x : (w == 1 ? v.y : (w == 2 ? v.z : v.w));
+        const uint32_t b = w == 0 ? v.y : (w == 1 ? v.z : (w == 2 ? v.w : 0u));
+        const uint64_t q = ((uint64_t)a << 32) | b;
+        return (uint32_t)((q << (j & 31)) >> 62);
+    }
+}
+
+// Bookkeeping of one pair slot (the G lanes of a pair): its pair, cursors
+// and statistics. Used by the banded kernel.
+struct Slot {
+    int pair, n, m, ti, pj;
+    const uint2 *tseq, *pseq;
+    int64_t tblk, pblk, next_static;
+    bool active, exhausted, failed;
+    int64_t st_rows, st_cells;
+    int32_t st_windows;
+    long long t_start;
+};
+
+__device__ __forceinline__ void slot_init(Slot &s, int64_t first_static) {
+    s.pair = s.n = s.m = s.ti = s.pj = 0;
+    s.tseq = s.pseq = nullptr;
+    s.tblk = s.pblk = 0;
+    s.next_static = first_static;
+    s.active = s.exhausted = s.failed = false;
+    s.st_rows = s.st_cells = 0;
+    s.st_windows = 0;
+    s.t_start = 0;
+}
+
+// An idle slot takes its next pair: lane G-1 draws it from the device queue over
+// `order` (persistent launch) or from a fixed stride over the input (plain
+// launch) and shares it with the slot's lanes. Pairs with an empty pattern are
+// finished at fetch time.
+template <int G>
+__device__ __forceinline__ void slot_fetch(const AlignParams &p, Slot &s, CigarOut &out, int l, int g, int tbl,
+                                           int64_t stride) {
+    if (s.active || s.exhausted) return;
+    int next = -1;
+    if (l == G - 1) {
+        for (;;) {
+            int64_t sl;
+            if (p.queue) {
+                sl = atomicAdd(p.queue, 1);
+            } else {
+                sl = s.next_static;
+                s.next_static += stride;
+            }
+            if (sl >= p.n_pairs) break;
+            const int pr = p.order ? p.order[sl] : (int)sl;
+            if (p.pat_len[pr] > 0) {
+                next = pr;
+                break;
+            }
+            p.edit_counts[pr] = 0;
+            p.text_consumed[pr] = 0;
+            p.cigar_lens[pr] = 0;
+            if (p.st_windows) p.st_windows[pr] = 0;
+            if (p.st_rows) p.st_rows[pr] = 0;
+            if (p.st_cells) p.st_cells[pr] = 0;
+            if (p.st_cycles) p.st_cycles[pr] = 0;
+        }
+    }
+    const uint32_t gmask = (G == 32) ? kFull : (((1u << G) - 1u) << (g * G));
+    next = __shfl_sync(gmask, next, tbl);
+    if (next < 0) {
+        s.exhausted = true;
+        return;
+    }
+    s.pair = next;
+    s.n = p.text_len[next];
+    s.m = p.pat_len[next];
+    s.tseq = reinterpret_cast<const uint2 *>(p.texts + (p.text_off[next] >> 4));
+    s.pseq = reinterpret_cast<const uint2 *>(p.patterns + (p.pat_off[next] >> 4));
+    s.tblk = (s.n + 31) >> 5;
+    s.pblk = (s.m + 31) >> 5;
+    s.ti = 0;
+    s.pj = 0;
+    s.failed = false;
+    s.st_rows = 0;
+    s.st_cells = 0;
+    s.st_windows = 0;
+    if (l == G - 1) {
+        const int64_t c0 = p.cigar_off[next];
+        out.dst = p.cigar + c0;
+        out.cap = p.cigar_off[next + 1] - c0;
+        out.n = 0;
+        out.cur = 0u;
+        out.edits = 0;
+        s.t_start = clock64();
+    }
+    s.active = true;
+}
+
+// After a window: the traceback lane finishes its pair when the pattern is
+// consumed (or a window failed), then the slot's lanes take over its cursors.
+template <int G>
+__device__ __forceinline__ void slot_window_done(const AlignParams &p, Slot &s, CigarOut &out, int l, int tbl) {
+    if (s.active && l == G - 1 && (s.failed || s.pj >= s.m)) {
+        s.active = false;
+        out.flush();
+        const int pair = s.pair;
+        p.edit_counts[pair] = s.failed ? -1 : out.edits;
+        p.text_consumed[pair] = s.failed ? 0 : s.ti;
+        if (out.n > out.cap) atomicOr(p.status, 2);  // capacity too small for this pair
+        p.cigar_lens[pair] = s.failed ? 0 : min(out.n, (int32_t)out.cap);
+        if (p.st_windows) p.st_windows[pair] = s.st_windows;
+        if (p.st_rows) p.st_rows[pair] = s.st_rows;
+        if (p.st_cells) p.st_cells[pair] = s.st_cells;
+        if (p.st_cycles) p.st_cycles[pair] = clock64() - s.t_start;
+    }
+    s.ti = __shfl_sync(kFull, s.ti, tbl);
+    s.pj = __shfl_sync(kFull, s.pj, tbl);
+    s.active = __shfl_sync(kFull, (int)s.active, tbl) != 0;
+    __syncwarp();
+}
+
 template <int NW, int G, bool SENE, int SWP>
 __global__ void __launch_bounds__(64, 6) align_kernel(const AlignParams p) {
     constexpr int WMAX = 32 * NW;
@@ -385,13 +516,26 @@ __global__ void __launch_bounds__(64, 6) align_kernel(const AlignParams p) {
                 }
                 const uint32_t *T0s = stage, *T1s = stage + (NW + 1);
                 const uint32_t *P0s = stage + 2 * (NW + 1), *P1s = stage + 3 * (NW + 1);
+                // windows of up to 64 bases: the four planes in 64-bit registers. A
+                // match run never reaches past the window, so the zeros shifted in
+                // at the end are never compared.
+                uint64_t qT0 = 0, qT1 = 0, qP0 = 0, qP1 = 0;
+                if (NW <= 2) {
+                    qT0 = ((uint64_t)T0s[0] << 32) | T0s[1];
+                    qT1 = ((uint64_t)T1s[0] << 32) | T1s[1];
+                    qP0 = ((uint64_t)P0s[0] << 32) | P0s[1];
+                    qP1 = ((uint64_t)P1s[0] << 32) | P1s[1];
+                }
+                auto ext = [&](uint64_t q, const uint32_t *plane, int pos) -> uint32_t {
+                    if (NW <= 2) return (uint32_t)((q << pos) >> 32);
+                    return stage_ext(plane, pos);
+                };
                 int i = 0, j = 0, d = d_opt;
                 bool going = tb_live && (j < mw && i < L && j < L);
                 while (__any_sync(tbl_all, going)) {
                     if (going) {
                         const int lim = min(min(nw - i, mw - j), min(L - i, L - j));
-                        const uint32_t x = (stage_ext(T0s, i) ^ stage_ext(P0s, j)) |
-                                           (stage_ext(T1s, i) ^ stage_ext(P1s, j));
+                        const uint32_t x = (ext(qT0, T0s, i) ^ ext(qP0, P0s, j)) | (ext(qT1, T1s, i) ^ ext(qP1, P1s, j));
                         const int z = __clz(x);
                         const int run = min(z, lim);
                         out.emit_maybe(kOpEq, run);
@@ -407,25 +551,31 @@ __global__ void __launch_bounds__(64, 6) align_kernel(const AlignParams p) {
                         } else if (edit) {
                             const bool tx = i < nw;
                             const bool j1 = j + 1 < mw;  // bit j+1 exists (else it is the shifted-in 0)
-                            uint32_t bS = 1u, bI = 1u, bD = 1u;
+                            const int lim_r = mw - (d - 1);  // bits < lim_r of the right column R[n][d-1] are 1
+                            uint32_t bS, bI, bD;
                             if (SENE) {
-                                // entries of row d-1; the right column R[n][d-1] is implicit
-                                const uint32_t *rp = row_base(d - 1);
-                                const int lim_r = mw - (d - 1);  // bits < lim_r of R[n][d-1] are 1
-                                const int c1 = i + 1, c0 = i;
-                                const uint32_t w1a = (tx && c1 < nw) ? rp[(int64_t)c1 * COLW + (j >> 5)] : 0u;
-                                const uint32_t w1b = (tx && c1 < nw && j1) ? rp[(int64_t)c1 * COLW + ((j + 1) >> 5)] : 0u;
-                                const uint32_t w0b = (c0 < nw && j1) ? rp[(int64_t)c0 * COLW + ((j + 1) >> 5)] : 0u;
-                                const uint32_t r1j = (c1 >= nw) ? (j < lim_r ? 1u : 0u) : bit_of(w1a, j);
-                                const uint32_t r1j1 = !j1 ? 0u : ((c1 >= nw) ? (j + 1 < lim_r ? 1u : 0u) : bit_of(w1b, j + 1));
-                                const uint32_t r0j1 = !j1 ? 0u : ((c0 >= nw) ? (j + 1 < lim_r ? 1u : 0u) : bit_of(w0b, j + 1));
+                                // entries (i+1, d-1) and (i, d-1): shared memory or scratch
+                                const int r = d - 1;
+                                const bool ld1 = tx && i + 1 < nw;
+                                uint32_t e1 = 0u, e0 = 0u;
+                                if (r < rcap) {
+                                    const uint32_t *rp = tab + (r * rstride + g) * CELL + i * COLW;
+                                    if (ld1) e1 = entry_bits2<SWP>(rp + COLW, j);
+                                    if (tx) e0 = entry_bits2<SWP>(rp, j);
+                                } else {
+                                    const uint32_t *rp = spill + ((r - rcap) * rstride + g) * CELL + i * COLW;
+                                    if (ld1) e1 = entry_bits2<SWP>(rp + COLW, j);
+                                    if (tx) e0 = entry_bits2<SWP>(rp, j);
+                                }
+                                const uint32_t r1j = ld1 ? (e1 >> 1) : (j < lim_r ? 1u : 0u);
+                                const uint32_t r1j1 = !j1 ? 0u : (ld1 ? (e1 & 1u) : (j + 1 < lim_r ? 1u : 0u));
+                                const uint32_t r0j1 = !j1 ? 0u : (tx ? (e0 & 1u) : (j + 1 < lim_r ? 1u : 0u));
                                 bS = tx ? r1j1 : 1u;
                                 bI = r0j1;
                                 bD = tx ? r1j : 1u;
                             } else {
                                 // stored edge vectors of cell (i, d)
                                 const uint32_t *rp = row_base(d) + (int64_t)i * COLW;
-                                const int lim_r = mw - (d - 1);
                                 const uint32_t wDa = tx ? rp[SWP + (j >> 5)] : 0u;
                                 const uint32_t wDb = (tx && j1) ? rp[SWP + ((j + 1) >> 5)] : 0u;
                                 const uint32_t wI = tx ? rp[j >> 5] : 0u;

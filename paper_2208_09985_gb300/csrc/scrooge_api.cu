@@ -18,6 +18,7 @@ bool align_supported(int words, int lanes) {
         case 1: return lanes == 1 || lanes == 2 || lanes == 4;
         case 2: return lanes == 2 || lanes == 4 || lanes == 8;
         case 4: return lanes == 8 || lanes == 16;
+        case 0: return supported_band(lanes);
         default: return false;
     }
 }
@@ -65,7 +66,7 @@ int scrooge_destroy(scrooge_ctx *c) {
                      &c->in_poff,   &c->in_plen, &c->out_ec,  &c->out_tc,   &c->out_cig,  &c->out_off,
                      &c->scr_runs,  &c->scr_off, &c->scr_len, &c->scr_cap,  &c->scan_tmp, &c->queue,
                      &c->model,     &c->grad,    &c->adam_m1, &c->adam_m2,  &c->loss,     &c->l_feat,
-                     &c->l_pred,    &c->l_key,   &c->l_order, &c->l_tmp,    &c->t_rows};
+                     &c->l_pred,    &c->l_key,   &c->l_order, &c->l_tmp,    &c->t_rows,   &c->fallback};
     if (c->graph) cudaGraphExecDestroy(c->graph);
     for (DevBuf *b : all) release(*b);
     delete c;
@@ -316,16 +317,18 @@ int scrooge_align_batch(scrooge_ctx *c, const uint32_t *texts, const int64_t *te
 
     // kernel shape
     const int words = words_for(W);
-    const KernelConfig kc = c->kcfg[kcfg_index(words)];
     const bool sene = !(flags & SCROOGE_NO_SENE);
     const bool dent = !(flags & SCROOGE_NO_DENT);
+    const bool band = use_band(W, flags);
+    const KernelConfig kc = c->kcfg[kcfg_index(band ? 0 : words)];
     int G = kc.lanes;
     auto supported = [&](int lanes, int swp) {
         return words == 1 ? supported_w32(lanes, sene, swp)
                           : (words == 2 ? supported_w64(lanes, sene, swp) : supported_w128(lanes, sene, swp));
     };
     TableShape ts = table_shape(W, O, words, G, dent, sene);
-    if (!supported(G, ts.swp)) {  // the edge-storing ablation exists for the default lane count only
+    if (band) ts.swp = 1;  // one 32-bit band word per stored entry
+    if (!band && !supported(G, ts.swp)) {  // the edge-storing ablation exists for the default lane count only
         G = words == 1 ? 2 : (words == 2 ? 4 : 8);
         ts = table_shape(W, O, words, G, dent, sene);
         if (!supported(G, ts.swp)) return fail(c, SCROOGE_E_INVAL, "no kernel for this W/O/flags combination");
@@ -336,7 +339,8 @@ int scrooge_align_batch(scrooge_ctx *c, const uint32_t *texts, const int64_t *te
     p.ncol = ts.ncol;
     p.sw = ts.swp;
     p.rstride = row_stride_cells(ts, PPW, 32 * words / G);
-    int rcap = std::min(kc.rows, k + 1);
+    const int rows_needed = band ? std::min(k, kBandRows - 1) + 1 : k + 1;  // rows the kernel may store
+    int rcap = std::min(kc.rows, rows_needed);
     const int stage = stage_words_per_warp(words, PPW);
     int wpb = kc.wpb;
     // keep the block's shared memory within the opt-in limit
@@ -347,20 +351,30 @@ int scrooge_align_batch(scrooge_ctx *c, const uint32_t *texts, const int64_t *te
     p.smem_words_per_warp = p.table_words_per_warp + stage;
     const size_t smem = (size_t)wpb * p.smem_words_per_warp * 4;
     int per_sm = 0;
-    e = words == 1 ? occupancy_w32(G, sene, ts.swp, wpb, smem, &per_sm)
-                   : (words == 2 ? occupancy_w64(G, sene, ts.swp, wpb, smem, &per_sm)
-                                 : occupancy_w128(G, sene, ts.swp, wpb, smem, &per_sm));
+    e = band ? occupancy_band(G, wpb, smem, &per_sm)
+             : (words == 1 ? occupancy_w32(G, sene, ts.swp, wpb, smem, &per_sm)
+                           : (words == 2 ? occupancy_w64(G, sene, ts.swp, wpb, smem, &per_sm)
+                                         : occupancy_w128(G, sene, ts.swp, wpb, smem, &per_sm)));
     if (e != cudaSuccess) return cuda_fail(c, e, "occupancy query");
     if (per_sm < 1) return fail(c, SCROOGE_E_INVAL, "kernel config does not fit on an SM (smem %zu B)", smem);
     const int64_t groups = ((int64_t)n_pairs + PPW - 1) / PPW;
     const int64_t want_blocks = (groups + wpb - 1) / wpb;
     const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(want_blocks, (int64_t)per_sm * c->sm_count));
-    const int spill_rows = std::max(0, k + 1 - rcap);
+    const int spill_rows = std::max(0, rows_needed - rcap);
     p.spill_words_per_pair = table_words_per_warp(spill_rows, ts, PPW, 32 * words / G);  // per warp
     const size_t spill_bytes = (size_t)blocks * wpb * (size_t)std::max<int64_t>(p.spill_words_per_pair, 4) * 4;
     if ((rc = ensure(c, c->spill, spill_bytes, "DP row scratch")) || (rc = ensure(c, c->status, 64, "status")))
         return rc;
     p.spill = (uint32_t *)c->spill.p;
+    if (band) {
+        p.fb_words_per_warp = band_fallback_words(k, ts.ncol, PPW);
+        if (p.fb_words_per_warp > 0) {
+            if ((rc = ensure(c, c->fallback, (size_t)blocks * wpb * (size_t)p.fb_words_per_warp * 4,
+                             "full-width fallback scratch")))
+                return rc;
+            p.fb = (uint32_t *)c->fallback.p;
+        }
+    }
     p.status = (int32_t *)c->status.p;
     if (flags & SCROOGE_PERSISTENT) {
         if ((rc = ensure(c, c->queue, 64, "work queue"))) return rc;
@@ -395,9 +409,10 @@ int scrooge_align_batch(scrooge_ctx *c, const uint32_t *texts, const int64_t *te
         }
         const bool timed = c->t_start && c->t_stop && !(flags & SCROOGE_GRAPH);
         if (timed) cudaEventRecord(c->t_start, st);
-        e = words == 1 ? launch_align_w32(p, G, sene, ts.swp, wpb, blocks, smem, st)
-                       : (words == 2 ? launch_align_w64(p, G, sene, ts.swp, wpb, blocks, smem, st)
-                                     : launch_align_w128(p, G, sene, ts.swp, wpb, blocks, smem, st));
+        e = band ? launch_align_band(p, G, wpb, blocks, smem, st)
+                 : (words == 1 ? launch_align_w32(p, G, sene, ts.swp, wpb, blocks, smem, st)
+                               : (words == 2 ? launch_align_w64(p, G, sene, ts.swp, wpb, blocks, smem, st)
+                                             : launch_align_w128(p, G, sene, ts.swp, wpb, blocks, smem, st)));
         if (e != cudaSuccess) return cuda_fail(c, e, "alignment kernel launch");
         if (timed) cudaEventRecord(c->t_stop, st);
         // dense CIGAR: prefix sums of the run counts (the gather follows)
@@ -410,7 +425,7 @@ int scrooge_align_batch(scrooge_ctx *c, const uint32_t *texts, const int64_t *te
     };
     if (flags & SCROOGE_GRAPH) {
         // one captured graph per distinct call; replayed while the call repeats
-        const unsigned long long key[24] = {(unsigned long long)(uintptr_t)p.texts, (unsigned long long)(uintptr_t)p.text_off,
+        const unsigned long long key[26] = {(unsigned long long)(uintptr_t)p.texts, (unsigned long long)(uintptr_t)p.text_off,
             (unsigned long long)(uintptr_t)p.text_len, (unsigned long long)(uintptr_t)p.patterns,
             (unsigned long long)(uintptr_t)p.pat_off, (unsigned long long)(uintptr_t)p.pat_len,
             (unsigned long long)(uintptr_t)p.edit_counts, (unsigned long long)(uintptr_t)p.text_consumed,
@@ -421,7 +436,8 @@ int scrooge_align_batch(scrooge_ctx *c, const uint32_t *texts, const int64_t *te
             (unsigned long long)flags, (unsigned long long)(uintptr_t)p.spill, (unsigned long long)(uintptr_t)p.order,
             (unsigned long long)(uintptr_t)st, ((unsigned long long)G << 32) | (unsigned long long)rcap,
             ((unsigned long long)wpb << 32) | (unsigned long long)blocks, (unsigned long long)(uintptr_t)c->st_rows,
-            (unsigned long long)(uintptr_t)c->st_cells, (unsigned long long)(uintptr_t)c->st_windows};
+            (unsigned long long)(uintptr_t)c->st_cells, (unsigned long long)(uintptr_t)c->st_windows,
+            (unsigned long long)(uintptr_t)p.fb, (unsigned long long)band};
         if (!c->graph || memcmp(key, c->graph_key, sizeof key) != 0) {
             if (c->graph) {
                 cudaGraphExecDestroy(c->graph);
@@ -499,9 +515,9 @@ int scrooge_autotune(scrooge_ctx *c, const uint32_t *texts, const int64_t *text_
     if (!c || n_pairs < 1 || repeats < 1) return SCROOGE_E_INVAL;
     if (W < 1 || W > 128) return fail(c, SCROOGE_E_INVAL, "W=%d outside 1..128", W);
     const int words = words_for(W);
-    const int ix = kcfg_index(words);
+    const int ix = kcfg_index(use_band(W, flags) ? 0 : words);
     const KernelConfig saved = c->kcfg[ix];
-    const int lanes_opts[3][3] = {{1, 2, 4}, {2, 4, 8}, {8, 16, 0}};
+    const int lanes_opts[4][3] = {{1, 2, 4}, {2, 4, 8}, {8, 16, 0}, {2, 4, 8}};
     const int rows_opts[] = {1, 2, 3, 4, 6, 8, 10, 12, 16, 20};
     const int wpb_opts[] = {1, 2};
     cudaEvent_t e0, e1;

@@ -30,9 +30,10 @@ struct scrooge_ctx {
     int sm_count = 0;
     size_t smem_optin = 0;
     std::string err;
-    scrooge::KernelConfig kcfg[3] = {{2, 8, 2}, {4, 4, 2}, {8, 8, 2}};  // words 1, 2, 4 (autotuned on GB300)
+    // full-width kernels of 1, 2, 4 words, then the banded kernel (autotuned on GB300)
+    scrooge::KernelConfig kcfg[4] = {{2, 8, 2}, {4, 4, 2}, {8, 8, 2}, {4, 8, 2}};
     int fail_allocs = 0;  // testing hook: fail the next N device allocations
-    scrooge::DevBuf spill, status;
+    scrooge::DevBuf spill, status, fallback;
     scrooge::DevBuf in_text, in_pat, in_toff, in_tlen, in_poff, in_plen;
     scrooge::DevBuf out_ec, out_tc, out_cig, out_off;
     scrooge::DevBuf scr_runs, scr_off, scr_len, scr_cap, scan_tmp;
@@ -50,7 +51,7 @@ struct scrooge_ctx {
     int32_t last_kernels = 0;  // kernels launched by the last alignment call
     // CUDA graph of the learned pipeline, keyed by the call it was captured for
     cudaGraphExec_t graph = nullptr;
-    unsigned long long graph_key[24] = {0};
+    unsigned long long graph_key[26] = {0};
 };
 
 namespace scrooge {
@@ -71,7 +72,10 @@ inline int cuda_fail(scrooge_ctx *c, cudaError_t e, const char *what) {
     return fail(c, SCROOGE_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-inline int kcfg_index(int words) { return words == 1 ? 0 : (words == 2 ? 1 : (words == 4 ? 2 : -1)); }
+// words 1, 2, 4: full-width kernels; 0: the banded kernel
+inline int kcfg_index(int words) {
+    return words == 1 ? 0 : (words == 2 ? 1 : (words == 4 ? 2 : (words == 0 ? 3 : -1)));
+}
 
 // Grow a device buffer to at least `bytes` (contents are not kept).
 inline int ensure(scrooge_ctx *c, DevBuf &b, size_t bytes, const char *what) {
@@ -102,6 +106,11 @@ inline void release(DevBuf &b) {
 }
 
 inline int words_for(int W) { return W <= 32 ? 1 : (W <= 64 ? 2 : 4); }
+
+// The banded kernel serves windows of 33..64 bases with SENE and ET on.
+inline bool use_band(int W, uint32_t flags) {
+    return W > 32 && W <= 64 && !(flags & (SCROOGE_NO_SENE | SCROOGE_NO_ET | SCROOGE_NO_BAND));
+}
 
 // Order of the pairs by predicted load (learn_api.cu): features, MLP, bucket
 // keys, stable sort; writes ctx->l_order. Device pointers; asynchronous.

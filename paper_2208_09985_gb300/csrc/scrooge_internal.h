@@ -35,6 +35,8 @@ struct AlignParams {
     int32_t *cigar_lens;        // [n_pairs] runs written
     uint32_t *spill;                // rows >= rcap, one region per resident warp
     int64_t spill_words_per_pair;   // words of that region per warp
+    uint32_t *fb;                   // banded kernel: full-width rows and state of windows beyond the band
+    int64_t fb_words_per_warp;      // words of that region per warp
     int32_t smem_words_per_warp;
     int32_t table_words_per_warp;
     const int32_t *order;   // optional pair order (slot -> pair id)
@@ -105,6 +107,16 @@ cudaError_t launch_align_w128(const AlignParams &, int lanes, bool sene, int swp
 cudaError_t occupancy_w32(int lanes, bool sene, int swp, int wpb, size_t smem, int *blocks_per_sm);
 cudaError_t occupancy_w64(int lanes, bool sene, int swp, int wpb, size_t smem, int *blocks_per_sm);
 cudaError_t occupancy_w128(int lanes, bool sene, int swp, int wpb, size_t smem, int *blocks_per_sm);
+// Banded kernel for windows of 64 bases (align_band.cu): lanes 2, 4 or 8.
+constexpr int kBandDiag = 15;  // band bit of the main diagonal j == i
+constexpr int kBandRows = 16;  // rows d = 0..15 are exact inside the 32-bit band
+cudaError_t launch_align_band(const AlignParams &, int lanes, int wpb, int blocks, size_t smem, cudaStream_t);
+cudaError_t occupancy_band(int lanes, int wpb, size_t smem, int *blocks_per_sm);
+bool supported_band(int lanes);
+// words of the full-width fallback region of one warp of the banded kernel
+inline int64_t band_fallback_words(int k, int ncol, int ppw) {
+    return k >= kBandRows ? (int64_t)(k + 1) * ncol * ppw * 2 : 0;
+}
 bool supported_w32(int lanes, bool sene, int swp);
 bool supported_w64(int lanes, bool sene, int swp);
 bool supported_w128(int lanes, bool sene, int swp);

@@ -90,7 +90,7 @@ def _tune_key(gpu: str, W: int, O: int, flags: int) -> str:
 def autotune_cached(ctx, db, W: int, O: int, flags: int = 0, cache_path: str | None = None, gpu: str = "gpu",
                     repeats: int = 2):
     """Kernel settings for (gpu, W, O, flags): from the JSON cache, else by scrooge_autotune (and stored)."""
-    words = 1 if W <= 32 else (2 if W <= 64 else 4)
+    words = sc.settings_slot(W, flags)
     cache = {}
     if cache_path and os.path.exists(cache_path):
         with open(cache_path) as f:

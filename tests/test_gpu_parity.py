@@ -43,29 +43,58 @@ def test_tiny_windows_full(ctx):
     assert (g["edit_counts"] >= 0).all()
 
 
-@pytest.mark.parametrize("W", [32, 64, 128, 16, 40, 100, 1, 2])
-def test_random_edge_cases_all_lane_configs(ctx, W):
+def _kernels(W):
+    """(settings slot, extra flags, label) of every kernel that serves windows of W bases."""
     words = 1 if W <= 32 else (2 if W <= 64 else 4)
-    lanes_opts = {1: [1, 2, 4], 2: [2, 4, 8], 4: [8, 16]}[words]
+    out = [(words, sc.SCROOGE_NO_BAND if words == 2 else 0, f"full{words}")]
+    if words == 2:
+        out.append((0, 0, "band"))
+    return out
+
+
+@pytest.mark.parametrize("W", [32, 64, 128, 16, 40, 100, 1, 2, 33])
+def test_random_edge_cases_all_lane_configs(ctx, W):
     rng = np.random.default_rng(W)
     b = synth.random_pairs(300, max_text=4 * W + 5, max_pattern=4 * W + 5, seed=100 + W)
-    saved = sc.scrooge_get_kernel_config(ctx, words)
+    for slot, flags, name in _kernels(W):
+        lanes_opts = {1: [1, 2, 4], 2: [2, 4, 8], 4: [8, 16], 0: [2, 4, 8]}[slot]
+        saved = sc.scrooge_get_kernel_config(ctx, slot)
+        try:
+            for lanes in lanes_opts:
+                for rows in (1, 3, 40):
+                    sc.scrooge_set_kernel_config(ctx, slot, lanes, rows, 2)
+                    O = int(rng.integers(0, W))
+                    for k in (W, max(0, W // 8), 16, 15):
+                        if k > W:
+                            continue
+                        g, r = _both(ctx, b, W, O, k, flags)
+                        assert_same(g, r, label=f"{name} W={W} O={O} k={k} lanes={lanes} rows={rows}")
+        finally:
+            sc.scrooge_set_kernel_config(ctx, slot, *saved)
+
+
+@pytest.mark.parametrize("lanes", [2, 4, 8])
+def test_band_fallback_windows(ctx, lanes):
+    """Windows whose edit distance exceeds the band (d_opt > 15) are recomputed at full width."""
+    b = synth.concat([synth.fixed_error(30, 0.25, length=600, seed=61), synth.fixed_error(30, 0.35, length=400, seed=62),
+                      synth.random_pairs(150, 300, 300, seed=63), synth.long_reads(4, seed=64)])
+    pb = sc.PackedBatch(b)
+    saved = sc.scrooge_get_kernel_config(ctx, 0)
     try:
-        for lanes in lanes_opts:
-            for rows in (1, 3, 40):
-                sc.scrooge_set_kernel_config(ctx, words, lanes, rows, 2)
-                O = int(rng.integers(0, W))
-                for k in (W, max(0, W // 8)):
-                    g, r = _both(ctx, b, W, O, k)
-                    assert_same(g, r, label=f"W={W} O={O} k={k} lanes={lanes} rows={rows}")
+        for rows in (1, 5, 16):
+            sc.scrooge_set_kernel_config(ctx, 0, lanes, rows, 2)
+            for O, k in ((24, 64), (24, 16), (24, 17), (33, 40), (24, 15), (0, 64), (63, 64)):
+                g = sc.align_host(ctx, pb, 64, O, k)
+                r = oracle.align_batch(b, 64, O, k, threads=THREADS)
+                assert_same(g, r, label=f"band lanes={lanes} rows={rows} O={O} k={k}")
     finally:
-        sc.scrooge_set_kernel_config(ctx, words, *saved)
+        sc.scrooge_set_kernel_config(ctx, 0, *saved)
 
 
-@pytest.mark.parametrize("flags", list(range(8)))
+@pytest.mark.parametrize("flags", list(range(16)))
 def test_ablation_flags_identical(ctx, flags):
     f = (sc.SCROOGE_NO_SENE if flags & 1 else 0) | (sc.SCROOGE_NO_DENT if flags & 2 else 0) | \
-        (sc.SCROOGE_NO_ET if flags & 4 else 0)
+        (sc.SCROOGE_NO_ET if flags & 4 else 0) | (sc.SCROOGE_NO_BAND if flags & 8 else 0)
     b = synth.concat([synth.tiny_windows(200, seed=5), synth.long_reads(6, seed=9),
                       synth.random_pairs(100, 200, 200, seed=8)])
     for W, O in ((64, 24), (64, 33), (32, 17), (128, 64)):
@@ -78,16 +107,17 @@ def test_kernel_shapes_w64(ctx):
                       synth.fixed_error(4, 0.15, seed=23)])
     r = oracle.align_batch(b, 64, 24, threads=THREADS)
     pb = sc.PackedBatch(b)
-    saved = sc.scrooge_get_kernel_config(ctx, 2)
-    try:
-        for lanes in (2, 4, 8):
-            for rows in (1, 6, 12, 65):
-                for wpb in (1, 2):
-                    sc.scrooge_set_kernel_config(ctx, 2, lanes, rows, wpb)
-                    g = sc.align_host(ctx, pb, 64, 24)
-                    assert_same(g, r, label=f"lanes={lanes} rows={rows} wpb={wpb}")
-    finally:
-        sc.scrooge_set_kernel_config(ctx, 2, *saved)
+    for slot, flags, name in _kernels(64):
+        saved = sc.scrooge_get_kernel_config(ctx, slot)
+        try:
+            for lanes in (2, 4, 8):
+                for rows in (1, 6, 12, 65):
+                    for wpb in (1, 2):
+                        sc.scrooge_set_kernel_config(ctx, slot, lanes, rows, wpb)
+                        g = sc.align_host(ctx, pb, 64, 24, flags=flags)
+                        assert_same(g, r, label=f"{name} lanes={lanes} rows={rows} wpb={wpb}")
+        finally:
+            sc.scrooge_set_kernel_config(ctx, slot, *saved)
 
 
 def test_device_pointers_match_host(ctx):
