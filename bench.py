@@ -122,17 +122,19 @@ def measured_peaks():
         return {}
 
 
-def kernel_traffic(words: int):
-    """DRAM bytes per launch of the alignment kernel from the committed ncu summary,
-    or None when the kernel source changed since the counters were taken."""
-    path = os.path.join(ROOT, "profiles", "align_kernel_traffic.txt")
+def kernel_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch of an alignment kernel on a workload, from the committed ncu summary
+    (profiles/<kernel>_traffic.txt), or None when the kernel source changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_traffic.txt")
     try:
         rec = dict(line.split(": ", 1) for line in open(path).read().splitlines()
                    if line and not line.startswith("#"))
     except (OSError, ValueError):
         return None
-    src = open(os.path.join(ROOT, "paper_2208_09985_gb300", "csrc", "align_kernel.cuh"), "rb").read()
-    if words != 2 or rec.get("source_sha256") != hashlib.sha256(src).hexdigest():
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES[kernel]:
+        h.update(open(os.path.join(ROOT, "paper_2208_09985_gb300", "csrc", name), "rb").read())
+    if rec.get("source_sha256") != h.hexdigest() or rec.get("workload") != workload:
         return None
     return int(rec["dram_bytes_per_launch"])
 
@@ -189,12 +191,18 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-PATHS = ("plain", "persistent", "learned", "learned_graph")
+PATHS = ("plain", "persistent", "learned", "learned_graph", "full_width_persistent")
 
 
 def path_flags(sc, name: str) -> int:
     return {"plain": 0, "persistent": sc.SCROOGE_PERSISTENT, "learned": sc.SCROOGE_LEARNED,
-            "learned_graph": sc.SCROOGE_LEARNED | sc.SCROOGE_GRAPH}[name]
+            "learned_graph": sc.SCROOGE_LEARNED | sc.SCROOGE_GRAPH,
+            "full_width_persistent": sc.SCROOGE_PERSISTENT | sc.SCROOGE_NO_BAND}[name]
+
+
+# sources of each alignment kernel, hashed to tell whether committed ncu counters still apply
+KERNEL_SOURCES = {"align_band_kernel": ("align_band.cu", "align_kernel.cuh"),
+                  "align_kernel": ("align_kernel.cuh",)}
 
 
 def prepare_model(sc, ctx, args):
@@ -349,6 +357,7 @@ def main():
     sm_max = float(peaks.get("sm_max_mhz") or (head_clk or {}).get("sm_max_mhz") or 2070.0)
     peak_ops = props.multi_processor_count * INT_LOGIC_OPS_PER_CLK_PER_SM * sm_max * 1e6
     ops_per_cell = 3 * words - 1
+    kernel = "align_band_kernel" if sc.settings_slot(W, flags) == 0 else "align_kernel"
     achieved = total_cells * ops_per_cell / (kernel_ms / 1e3)
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
@@ -361,7 +370,7 @@ def main():
         "config": {"workload": args.workload, "desc": wl["desc"], "pairs_per_gpu": n_pairs, "W": W, "O": O, "k": k,
                    "path": "learned ordering + persistent work queue + CUDA graph (value); plain, persistent and "
                            "learned without graph in `paths`", "flags": flags,
-                   "kernel_config": list(sc.scrooge_get_kernel_config(ctx, words)),
+                   "kernel": kernel, "kernel_config": list(sc.scrooge_get_kernel_config(ctx, sc.settings_slot(W, flags))),
                    "l2": "inputs larger than L2 (packed inputs %.0f MB)" % (pb.texts.nbytes / 1e6 + pb.patterns.nbytes / 1e6),
                    "parallelism": f"dp{world}" if world > 1 else "single GPU"},
         "gbases_per_s": world * bases / (head_ms / 1e3) / 1e9,
@@ -370,7 +379,7 @@ def main():
         "mean_edits_per_pair": float(ec.mean()), "cigar_runs_per_step": total_runs,
         "dp_cells_per_step": total_cells, "dp_rows_per_step": total_rows,
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
-                     "frac": achieved / peak_ops, "traffic": kernel_traffic(words),
+                     "frac": achieved / peak_ops, "traffic": kernel_traffic(kernel, args.workload),
                      "kernel_ms": kernel_ms,
                      "basis": f"{ops_per_cell} LOP3/SHF ops per DP cell computed up to each window's edit "
                               f"distance; alignment kernel timed alone (events around it, learned order); "
