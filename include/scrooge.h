@@ -168,6 +168,15 @@ int scrooge_set_kernel_config(scrooge_ctx *ctx, int32_t words, int32_t lanes_per
 int scrooge_get_kernel_config(const scrooge_ctx *ctx, int32_t words, int32_t *lanes_per_pair,
                               int32_t *smem_rows, int32_t *warps_per_block);
 
+/* Launch shape of the last scrooge_align_batch call on this context, for
+ * reports: up to 12 int64 into shape[0..n): kernel (0 banded, else the words
+ * of the full-width kernel), lanes per pair, DP rows kept in shared memory,
+ * warps per block, dynamic shared memory per block (bytes), blocks, stored
+ * columns per row, stored words per entry, shared-memory table bytes per
+ * warp, device-scratch row bytes per warp, full-width fallback bytes per
+ * warp, pairs per warp. */
+int scrooge_last_launch_shape(const scrooge_ctx *ctx, int64_t *shape, int32_t n);
+
 /* Autotuner (no counterpart in the paper: it picks implementation
  * parameters only, so results never change). Times every supported
  * (lanes_per_pair, smem_rows, warps_per_block) for the window width of W on
@@ -294,6 +303,28 @@ int scrooge_align_batch_noalloc(const uint32_t *texts, const int64_t *text_offse
                                 uint32_t flags, int32_t *edit_counts, int32_t *text_consumed, uint32_t *cigar,
                                 const int64_t *cigar_offsets, int32_t *cigar_lens, int32_t *status,
                                 void *cuda_stream);
+
+/* ------------------------------------------------- exact edit distances
+ * No counterpart in the paper's hot path. It is the optimal score that the
+ * windowed heuristic is measured against, as in the paper's accuracy study
+ * (Section 5). For every pair it computes
+ *   free_end[p]        = min over t of lev(pattern, text[0:t]): the whole
+ *                        pattern against a text prefix, the problem that
+ *                        scrooge_align_batch solves window by window, so
+ *                        free_end[p] <= edit_counts[p] always;
+ *   global_distance[p] = lev(pattern, text).
+ * Unit costs; Myers' bit-vector algorithm, one warp per pair. Inputs are in
+ * the packed layout of scrooge_align_batch and must be DEVICE pointers
+ * (flags must contain SCROOGE_DEVICE_PTRS; SCROOGE_SYNC is honoured), as
+ * must the two int32 outputs of n_pairs entries.
+ * max_pattern_length bounds the pattern lengths (at most
+ * SCROOGE_EDIT_DISTANCE_MAX_M); a pair above it gets -1 in both outputs.
+ * Asynchronous on the context stream. */
+#define SCROOGE_EDIT_DISTANCE_MAX_M 16384
+int scrooge_edit_distance(scrooge_ctx *ctx, const uint32_t *texts, const int64_t *text_offsets,
+                          const int32_t *text_lengths, const uint32_t *patterns, const int64_t *pattern_offsets,
+                          const int32_t *pattern_lengths, int32_t n_pairs, int32_t max_pattern_length,
+                          uint32_t flags, int32_t *free_end, int32_t *global_distance);
 
 /* Testing hook: make the next `count` device allocations of this context
  * fail with SCROOGE_E_NOMEM (0 switches it off). */

@@ -91,6 +91,8 @@ def load():
                                       P], ctypes.c_int),
                 "scrooge_align_batch_noalloc": ([P, P, P, P, P, P, i32, i32, i32, i32, u32, P, P, P, P, P, P, P],
                                                 ctypes.c_int),
+                "scrooge_edit_distance": ([P, P, P, P, P, P, P, i32, i32, u32, P, P], ctypes.c_int),
+                "scrooge_last_launch_shape": ([P, P, i32], ctypes.c_int),
             }
             for name, (args, res) in sig.items():
                 f = getattr(lib, name)
@@ -238,6 +240,18 @@ def scrooge_set_timing_events(ctx, start=None, stop=None):
     return _check(ctx, load().scrooge_set_timing_events(ctx, h(start), h(stop)))
 
 
+LAUNCH_SHAPE_KEYS = ("kernel", "lanes", "smem_rows", "warps_per_block", "smem_bytes_per_block", "blocks",
+                     "stored_columns", "stored_words", "table_bytes_per_warp", "scratch_bytes_per_warp",
+                     "fallback_bytes_per_warp", "pairs_per_warp")
+
+
+def scrooge_last_launch_shape(ctx) -> dict:
+    """Launch shape of the context's last alignment call (see include/scrooge.h)."""
+    a = np.zeros(len(LAUNCH_SHAPE_KEYS), dtype=np.int64)
+    _check(ctx, load().scrooge_last_launch_shape(ctx, _ptr(a), len(a)))
+    return dict(zip(LAUNCH_SHAPE_KEYS, (int(x) for x in a)))
+
+
 def scrooge_last_kernel_count(ctx) -> int:
     return int(load().scrooge_last_kernel_count(ctx))
 
@@ -292,6 +306,30 @@ def scrooge_learned_order(ctx, texts, text_offsets, text_lengths, patterns, patt
 
 def scrooge_set_stats(ctx, windows=None, rows=None, cells=None, cycles=None):
     return _check(ctx, load().scrooge_set_stats(ctx, _ptr(windows), _ptr(rows), _ptr(cells), _ptr(cycles)))
+
+
+SCROOGE_EDIT_DISTANCE_MAX_M = 16384
+
+
+def scrooge_edit_distance(ctx, texts, text_offsets, text_lengths, patterns, pattern_offsets, pattern_lengths,
+                          n_pairs: int, max_pattern_length: int, flags: int, free_end, global_distance):
+    """Exact free-end and global edit distances (device tensors; flags must include SCROOGE_DEVICE_PTRS)."""
+    return _check(ctx, load().scrooge_edit_distance(ctx, _ptr(texts), _ptr(text_offsets), _ptr(text_lengths),
+                                                    _ptr(patterns), _ptr(pattern_offsets), _ptr(pattern_lengths),
+                                                    int(n_pairs), int(max_pattern_length), int(flags),
+                                                    _ptr(free_end), _ptr(global_distance)))
+
+
+def edit_distance_device(ctx, db: "DeviceBatch", sync: bool = True):
+    """(free_end, global) int32 device tensors of a DeviceBatch: the optimal scores of its pairs."""
+    import torch
+    fe = torch.empty(db.n_pairs, dtype=torch.int32, device=db.texts.device)
+    gl = torch.empty(db.n_pairs, dtype=torch.int32, device=db.texts.device)
+    max_m = int(db.pat_len.max().item()) if db.n_pairs else 0
+    scrooge_edit_distance(ctx, db.texts, db.text_off, db.text_len, db.patterns, db.pat_off, db.pat_len, db.n_pairs,
+                          min(max_m, SCROOGE_EDIT_DISTANCE_MAX_M), SCROOGE_DEVICE_PTRS | (SCROOGE_SYNC if sync else 0),
+                          fe, gl)
+    return fe, gl
 
 
 def scrooge_debug_fail_next_allocs(ctx, count: int):

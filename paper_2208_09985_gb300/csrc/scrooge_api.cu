@@ -24,7 +24,6 @@ bool align_supported(int words, int lanes) {
 }
 }  // namespace scrooge
 
-#include "scrooge_ctx.h"
 
 using namespace scrooge;
 
@@ -172,6 +171,12 @@ int scrooge_get_kernel_config(const scrooge_ctx *c, int32_t words, int32_t *lane
     if (lanes) *lanes = c->kcfg[ix].lanes;
     if (rows) *rows = c->kcfg[ix].rows;
     if (wpb) *wpb = c->kcfg[ix].wpb;
+    return SCROOGE_OK;
+}
+
+int scrooge_last_launch_shape(const scrooge_ctx *c, int64_t *shape, int32_t n) {
+    if (!c || !shape || n < 1) return SCROOGE_E_INVAL;
+    memcpy(shape, c->last_shape, sizeof(int64_t) * (size_t)std::min(n, 12));
     return SCROOGE_OK;
 }
 
@@ -390,6 +395,12 @@ int scrooge_align_batch(scrooge_ctx *c, const uint32_t *texts, const int64_t *te
             (rc = ensure(c, c->l_tmp, (size_t)sort_temp_words(n_pairs) * 8, "sort scratch")))
             return rc;
         p.order = (const int32_t *)c->l_order.p;
+    }
+    {
+        const int64_t shape[12] = {band ? 0 : words, G, rcap, wpb, (int64_t)smem, blocks, p.ncol, ts.swp,
+                                   p.table_words_per_warp * 4LL, p.spill_words_per_pair * 4, p.fb_words_per_warp * 4,
+                                   PPW};
+        memcpy(c->last_shape, shape, sizeof shape);
     }
     p.st_windows = c->st_windows;
     p.st_rows = c->st_rows;

@@ -76,6 +76,25 @@ def free_end_distance(text, pattern) -> int:
     return int(best)
 
 
+def free_end_distance_rows(text, pattern) -> int:
+    """free_end_distance with the insertion chain of a row as a running minimum:
+    cur[y] = y + min(x, min over y' <= y of (best_row[y'-1] - y'))."""
+    n, m = len(text), len(pattern)
+    prev = np.arange(m + 1, dtype=np.int64)
+    best = prev[m]
+    t = np.asarray(text)
+    p = np.asarray(pattern)
+    ys = np.arange(1, m + 1, dtype=np.int64)
+    for x in range(1, n + 1):
+        best_row = np.minimum(prev[:-1] + (p != t[x - 1]), prev[1:] + 1)
+        cur = np.empty(m + 1, dtype=np.int64)
+        cur[0] = x
+        cur[1:] = ys + np.minimum(x, np.minimum.accumulate(best_row - ys))
+        prev = cur
+        best = min(best, prev[m])
+    return int(best)
+
+
 def cigar_ops(runs):
     """uint32 runs -> list of (op, len)."""
     return [(int(r) & 15, int(r) >> 4) for r in runs]

@@ -218,3 +218,13 @@ def test_cigar_overflow_reported(oracle_mod):
         # the alignment itself is unaffected by the capacity
         assert res["edit_counts"][p] == full["edit_count"]
         assert res["text_consumed"][p] == full["text_consumed"]
+
+
+def test_free_end_row_recurrence_matches_its_definition():
+    """The vectorised free-end DP used by the edit-distance tests equals the row-by-row one."""
+    from tests._brute import free_end_distance, free_end_distance_rows
+    rng = np.random.default_rng(17)
+    for _ in range(200):
+        n, m = int(rng.integers(0, 50)), int(rng.integers(0, 50))
+        t, p = rng.integers(0, 4, n), rng.integers(0, 4, m)
+        assert free_end_distance_rows(t, p) == free_end_distance(t, p)
