@@ -65,6 +65,8 @@ def parse():
     ap.add_argument("--flags", type=int, default=0, help="extra SCROOGE_* flags (ablations)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the built-in kernel settings (default: autotune on a separate sample first)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="time budget of the CPU baseline")
     ap.add_argument("--model", default="", help="saved ordering model (JSON); default: train one first")
     ap.add_argument("--train-pairs", type=int, default=50_000)
@@ -241,8 +243,18 @@ def main():
     ctx = sc.scrooge_create(local, stream)
     words = 1 if W <= 32 else (2 if W <= 64 else 4)
     model_info = prepare_model(sc, ctx, args)
-    db = sc.DeviceBatch(pb)
     flags = args.flags
+    tune_info = None
+    if not args.no_autotune:
+        # kernel settings and the heavy load classes, tuned on a same-size sample drawn with another seed
+        t0 = time.perf_counter()
+        sample = wl["make"](n_pairs, wl["seed"] + 7 + 1000 * rank)
+        sdb = sc.DeviceBatch(sc.PackedBatch(sample))
+        table = sc.autotune_device(ctx, sdb, W, O, k, flags=flags | sc.SCROOGE_LEARNED, repeats=3)
+        del sdb, sample
+        tune_info = {"sample_pairs": n_pairs, "sample_seed": wl["seed"] + 7 + 1000 * rank, "configs_timed": len(table),
+                     "heavy_class": sc.scrooge_get_heavy_class(ctx), "seconds": time.perf_counter() - t0}
+    db = sc.DeviceBatch(pb)
 
     # untimed run with per-pair statistics: algorithmic DP cells of the method
     cells = torch.zeros(n_pairs, dtype=torch.int64, device="cuda")
@@ -375,7 +387,7 @@ def main():
                    "parallelism": f"dp{world}" if world > 1 else "single GPU"},
         "gbases_per_s": world * bases / (head_ms / 1e3) / 1e9,
         "paths": paths, "learned_gain_vs_plain": value / plain,
-        "model": model_info,
+        "model": model_info, "autotune": tune_info,
         "mean_edits_per_pair": float(ec.mean()), "cigar_runs_per_step": total_runs,
         "dp_cells_per_step": total_cells, "dp_rows_per_step": total_rows,
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",

@@ -168,6 +168,17 @@ int scrooge_set_kernel_config(scrooge_ctx *ctx, int32_t words, int32_t lanes_per
 int scrooge_get_kernel_config(const scrooge_ctx *ctx, int32_t words, int32_t *lanes_per_pair,
                               int32_t *smem_rows, int32_t *warps_per_block);
 
+/* Kernel per load bucket (no counterpart in the paper; never changes
+ * results). With SCROOGE_LEARNED on windows the banded kernel serves, the
+ * pairs the ordering puts in predicted load classes >= load_class (the 4-bit
+ * class of the bucket key, 0..15) run on the full-width kernel and the rest on
+ * the banded one, the two launches overlapping on two streams. 16 (the
+ * default) sends every pair to the banded kernel, 0 every pair to the
+ * full-width one. scrooge_autotune with SCROOGE_LEARNED also picks this
+ * class. */
+int scrooge_set_heavy_class(scrooge_ctx *ctx, int32_t load_class);
+int32_t scrooge_get_heavy_class(const scrooge_ctx *ctx);
+
 /* Launch shape of the last scrooge_align_batch call on this context, for
  * reports: up to 12 int64 into shape[0..n): kernel (0 banded, else the words
  * of the full-width kernel), lanes per pair, DP rows kept in shared memory,
@@ -185,7 +196,11 @@ int scrooge_last_launch_shape(const scrooge_ctx *ctx, int64_t *shape, int32_t n)
  * `repeats` timed runs per configuration (CUDA events on the context stream,
  * after one untimed run), and installs the fastest configuration in the
  * context. If `results` is not NULL it receives up to max_results rows of 5
- * int32: lanes, rows, warps, microseconds, 1; *n_results gets the row count.
+ * int32: lanes, rows, warps, microseconds, 1; with SCROOGE_LEARNED on windows
+ * the banded kernel serves it then also times the heavy load classes
+ * (scrooge_set_heavy_class) 16, 15, ..., 10, 0 with the chosen settings, as
+ * rows 0, class, 0, microseconds, 2, and installs the fastest class.
+ * *n_results gets the row count.
  * Synchronous. */
 int scrooge_autotune(scrooge_ctx *ctx, const uint32_t *texts, const int64_t *text_offsets,
                      const int32_t *text_lengths, const uint32_t *patterns, const int64_t *pattern_offsets,

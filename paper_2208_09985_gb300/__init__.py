@@ -93,6 +93,8 @@ def load():
                                                 ctypes.c_int),
                 "scrooge_edit_distance": ([P, P, P, P, P, P, P, i32, i32, u32, P, P], ctypes.c_int),
                 "scrooge_last_launch_shape": ([P, P, i32], ctypes.c_int),
+                "scrooge_set_heavy_class": ([P, i32], ctypes.c_int),
+                "scrooge_get_heavy_class": ([P], i32),
             }
             for name, (args, res) in sig.items():
                 f = getattr(lib, name)
@@ -201,7 +203,8 @@ def scrooge_get_kernel_config(ctx, words: int):
 def scrooge_autotune(ctx, texts, text_offsets, text_lengths, patterns, pattern_offsets, pattern_lengths,
                      n_pairs: int, W: int, O: int, k: int, flags: int, edit_counts, text_consumed, cigar,
                      cigar_capacity: int, cigar_offsets, repeats: int = 2, max_results: int = 256):
-    """Time every kernel configuration on a device batch; returns rows (lanes, rows, warps, microseconds)."""
+    """Time every kernel configuration on a device batch; returns rows (lanes, rows, warps, microseconds, kind)
+    with kind 1 for kernel settings and 2 for heavy load classes (lanes 0, rows = the class)."""
     res = np.zeros((max_results, 5), dtype=np.int32)
     nres = ctypes.c_int32(0)
     rc = load().scrooge_autotune(ctx, _ptr(texts), _ptr(text_offsets), _ptr(text_lengths), _ptr(patterns),
@@ -210,7 +213,7 @@ def scrooge_autotune(ctx, texts, text_offsets, text_lengths, patterns, pattern_o
                                  int(cigar_capacity), _ptr(cigar_offsets), int(repeats), _ptr(res), max_results,
                                  ctypes.byref(nres))
     _check(ctx, rc)
-    return [tuple(int(x) for x in r[:4]) for r in res[: nres.value]]
+    return [tuple(int(x) for x in r) for r in res[: nres.value]]
 
 
 def settings_slot(W: int, flags: int = 0) -> int:
@@ -250,6 +253,15 @@ def scrooge_last_launch_shape(ctx) -> dict:
     a = np.zeros(len(LAUNCH_SHAPE_KEYS), dtype=np.int64)
     _check(ctx, load().scrooge_last_launch_shape(ctx, _ptr(a), len(a)))
     return dict(zip(LAUNCH_SHAPE_KEYS, (int(x) for x in a)))
+
+
+def scrooge_set_heavy_class(ctx, load_class: int):
+    """Learned launches: load classes >= load_class run on the full-width kernel (16: none)."""
+    return _check(ctx, load().scrooge_set_heavy_class(ctx, int(load_class)))
+
+
+def scrooge_get_heavy_class(ctx) -> int:
+    return int(load().scrooge_get_heavy_class(ctx))
 
 
 def scrooge_last_kernel_count(ctx) -> int:

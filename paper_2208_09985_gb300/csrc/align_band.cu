@@ -156,6 +156,8 @@ __global__ void __launch_bounds__(64, BandMinBlocks<G>::value) align_band_kernel
 
     Slot s;
     slot_init(s, gw * PPW + g);
+    int64_t q_lo, q_hi;
+    slot_range(p, q_lo, q_hi);
     CigarOut out;
     out.dst = nullptr;
     out.cap = 0;
@@ -163,7 +165,7 @@ __global__ void __launch_bounds__(64, BandMinBlocks<G>::value) align_band_kernel
     out.cur = 0u;
     out.edits = 0;
     for (;;) {
-        slot_fetch<G>(p, s, out, l, g, tbl, nwarps * PPW);
+        slot_fetch<G>(p, s, out, l, g, tbl, nwarps * PPW, q_lo, q_hi);
         if (!__any_sync(kFull, s.active)) break;
         const bool active = s.active;
         const int nw = active ? min(W, s.n - s.ti) : 0;

@@ -173,21 +173,32 @@ __device__ __forceinline__ void slot_init(Slot &s, int64_t first_static) {
 // `order` (persistent launch) or from a fixed stride over the input (plain
 // launch) and shares it with the slot's lanes. Pairs with an empty pattern are
 // finished at fetch time.
+// Slots [lo, hi) of the order this launch serves (persistent launches may split them).
+__device__ __forceinline__ void slot_range(const AlignParams &p, int64_t &lo, int64_t &hi) {
+    lo = 0;
+    hi = p.n_pairs;
+    if (p.queue && p.split_at) {
+        const int64_t sp = *p.split_at;
+        if (p.split_side) lo = sp;
+        else hi = sp;
+    }
+}
+
 template <int G>
 __device__ __forceinline__ void slot_fetch(const AlignParams &p, Slot &s, CigarOut &out, int l, int g, int tbl,
-                                           int64_t stride) {
+                                           int64_t stride, int64_t q_lo, int64_t q_hi) {
     if (s.active || s.exhausted) return;
     int next = -1;
     if (l == G - 1) {
         for (;;) {
             int64_t sl;
             if (p.queue) {
-                sl = atomicAdd(p.queue, 1);
+                sl = q_lo + atomicAdd(p.queue, 1);
             } else {
                 sl = s.next_static;
                 s.next_static += stride;
             }
-            if (sl >= p.n_pairs) break;
+            if (sl >= q_hi) break;
             const int pr = p.order ? p.order[sl] : (int)sl;
             if (p.pat_len[pr] > 0) {
                 next = pr;
@@ -299,6 +310,8 @@ __global__ void __launch_bounds__(64, 6) align_kernel(const AlignParams p) {
     // device work queue over `order` (persistent launch). Pairs with an empty
     // pattern are finished at fetch time.
     int64_t next_static = gw * PPW + g;
+    int64_t q_lo, q_hi;
+    slot_range(p, q_lo, q_hi);
     bool exhausted = false, active = false;
     int pair = 0, n = 0, m = 0;
     const uint2 *tseq = nullptr, *pseq = nullptr;
@@ -321,12 +334,12 @@ __global__ void __launch_bounds__(64, 6) align_kernel(const AlignParams p) {
                 for (;;) {
                     int64_t sl;
                     if (p.queue) {
-                        sl = atomicAdd(p.queue, 1);
+                        sl = q_lo + atomicAdd(p.queue, 1);
                     } else {
                         sl = next_static;
                         next_static += nwarps * PPW;
                     }
-                    if (sl >= p.n_pairs) break;
+                    if (sl >= q_hi) break;
                     const int pr = p.order ? p.order[sl] : (int)sl;
                     if (p.pat_len[pr] > 0) {
                         next = pr;

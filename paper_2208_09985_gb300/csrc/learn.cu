@@ -29,21 +29,76 @@ __device__ __forceinline__ void planes32(const uint2 *seq, int64_t nblk, int64_t
     p1 = __funnelshift_l(c.y, a.y, r);
 }
 
-// One warp per pair. Features (all float32):
+// Eight lanes per pair (kFeatLanes). Features (all float32):
 //   0: log2(m + 1)             1: log2(n + 1)           2: (n - m) / max(m, 1)
 //   3: fraction of sampled pattern 12-mers found in the text within +-64 of
 //      the same position (anchored start)
 //   4: spread (standard deviation / 64) of the offsets text - pattern of the hits
 //   5: fraction of hits within +-16 of the mean offset
+constexpr int kFeatLanes = 8;  // lanes per pair in features_kernel
+
+// Nearest text position of a sampled pattern k-mer, bit-parallel: bit u of
+// the candidate mask (MSB-first, in 32-bit words) says whether the k-mer
+// occurs at text position lo + u; all 12 k-mer bases are tested against 160
+// candidates with shifted words of the text planes. Returns the offset
+// (lo + u) - q of the match nearest to q, the lower one on a tie, or 0x7fff.
+__device__ __forceinline__ int nearest_kmer(const uint2 *ts, int64_t tb, int n, uint32_t a0, uint32_t a1, int q) {
+    const int lo = max(0, q - kBand), hi = min(n - kK, q + kBand);
+    if (hi < lo) return 0x7fff;
+    uint32_t T0[6], T1[6], M[5];
+#pragma unroll
+    for (int w = 0; w < 6; ++w) planes32(ts, tb, (int64_t)lo + 32 * w, T0[w], T1[w]);
+#pragma unroll
+    for (int w = 0; w < 5; ++w) M[w] = 0xffffffffu;
+#pragma unroll
+    for (int c = 0; c < kK; ++c) {
+        const uint32_t k0 = 0u - ((a0 >> (31 - c)) & 1u), k1 = 0u - ((a1 >> (31 - c)) & 1u);
+#pragma unroll
+        for (int w = 0; w < 5; ++w) {
+            const uint32_t x0 = __funnelshift_l(T0[w + 1], T0[w], c);
+            const uint32_t x1 = __funnelshift_l(T1[w + 1], T1[w], c);
+            M[w] &= ~((x0 ^ k0) | (x1 ^ k1));
+        }
+    }
+    const int ncand = hi - lo + 1, u0 = q - lo;
+#pragma unroll
+    for (int w = 0; w < 5; ++w) {
+        const int keep = ncand - 32 * w;
+        M[w] &= keep <= 0 ? 0u : (keep >= 32 ? 0xffffffffu : (0xffffffffu << (32 - keep)));
+    }
+    // first candidate at or after u0, last one before u0
+    const int wf = u0 >> 5, bf = u0 & 31;
+    const int wb = (u0 - 1) >> 5, bb = (u0 - 1) & 31;
+    int uf = 1 << 20, ub = -(1 << 20);
+#pragma unroll
+    for (int w = 4; w >= 0; --w) {
+        const uint32_t v = w > wf ? M[w] : (w == wf ? (M[w] & (0xffffffffu >> bf)) : 0u);
+        if (v) uf = 32 * w + __clz(v);
+    }
+    if (u0 > 0) {
+#pragma unroll
+        for (int w = 0; w < 5; ++w) {
+            const uint32_t v = w < wb ? M[w] : (w == wb ? (M[w] & (0xffffffffu << (31 - bb))) : 0u);
+            if (v) ub = 32 * w + 31 - (__ffs(v) - 1);
+        }
+    }
+    const bool hf = uf < (1 << 20), hb = ub > -(1 << 20);
+    if (!hf && !hb) return 0x7fff;
+    if (hb && (!hf || u0 - ub <= uf - u0)) return ub - u0;
+    return uf - u0;
+}
+
 __global__ void __launch_bounds__(256) features_kernel(const uint32_t *texts, const int64_t *text_off,
                                                        const int32_t *text_len, const uint32_t *patterns,
                                                        const int64_t *pat_off, const int32_t *pat_len, int32_t n_pairs,
                                                        float *feat) {
-    __shared__ int16_t delta_s[8][kSamples];
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t p = warp; p < n_pairs; p += nwarps) {
+    constexpr int GPB = 256 / kFeatLanes;  // pair groups per block
+    __shared__ int16_t delta_s[GPB][kSamples];
+    const int lane = threadIdx.x & (kFeatLanes - 1), gib = threadIdx.x / kFeatLanes;
+    const uint32_t gmask = 0xffu << (kFeatLanes * ((threadIdx.x & 31) / kFeatLanes));
+    const int64_t group = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kFeatLanes;
+    const int64_t ngroups = ((int64_t)gridDim.x * blockDim.x) / kFeatLanes;
+    for (int64_t p = group; p < n_pairs; p += ngroups) {
         const int n = text_len[p], m = pat_len[p];
         const uint2 *ts = reinterpret_cast<const uint2 *>(texts + (text_off[p] >> 4));
         const uint2 *ps = reinterpret_cast<const uint2 *>(patterns + (pat_off[p] >> 4));
@@ -53,25 +108,12 @@ __global__ void __launch_bounds__(256) features_kernel(const uint32_t *texts, co
         const int nsamp = nsamp_max > 0 ? min(kSamples, (nsamp_max + stride - 1) / stride) : 0;
         int hits = 0;
         float sum = 0.f, sum2 = 0.f;
-        for (int s = lane; s < nsamp; s += 32) {
+        for (int s = lane; s < nsamp; s += kFeatLanes) {
             const int q = s * stride;
             uint32_t a0, a1;
             planes32(ps, pb, q, a0, a1);
-            const uint32_t km0 = a0 >> (32 - kK), km1 = a1 >> (32 - kK);
-            // scan text positions q - kBand .. q + kBand for the k-mer, nearest offset first
-            int best = 0x7fff;
-            const int lo = max(0, q - kBand), hi = min(n - kK, q + kBand);
-            for (int t0 = lo; t0 <= hi; t0 += 20) {
-                uint32_t b0, b1;
-                planes32(ts, tb, t0, b0, b1);
-                const int span = min(20, hi - t0 + 1);
-                for (int u = 0; u < span; ++u) {
-                    const uint32_t c0 = (b0 << u) >> (32 - kK), c1 = (b1 << u) >> (32 - kK);
-                    const int off = t0 + u - q;
-                    if (c0 == km0 && c1 == km1 && abs(off) < abs(best)) best = off;
-                }
-            }
-            delta_s[wib][s] = (int16_t)best;
+            const int best = nearest_kmer(ts, tb, n, a0, a1, q);
+            delta_s[gib][s] = (int16_t)best;
             if (best != 0x7fff) {
                 hits += 1;
                 sum += (float)best;
@@ -79,21 +121,21 @@ __global__ void __launch_bounds__(256) features_kernel(const uint32_t *texts, co
             }
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            hits += __shfl_xor_sync(0xffffffffu, hits, o);
-            sum += __shfl_xor_sync(0xffffffffu, sum, o);
-            sum2 += __shfl_xor_sync(0xffffffffu, sum2, o);
+        for (int o = kFeatLanes / 2; o > 0; o >>= 1) {
+            hits += __shfl_xor_sync(gmask, hits, o, kFeatLanes);
+            sum += __shfl_xor_sync(gmask, sum, o, kFeatLanes);
+            sum2 += __shfl_xor_sync(gmask, sum2, o, kFeatLanes);
         }
         const float mean = hits > 0 ? sum / hits : 0.f;
-        __syncwarp();
+        __syncwarp(gmask);
         int near = 0;
-        for (int s = lane; s < nsamp; s += 32) {
-            const int dlt = delta_s[wib][s];
+        for (int s = lane; s < nsamp; s += kFeatLanes) {
+            const int dlt = delta_s[gib][s];
             if (dlt != 0x7fff && fabsf((float)dlt - mean) <= 16.f) near += 1;
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) near += __shfl_xor_sync(0xffffffffu, near, o);
-        __syncwarp();
+        for (int o = kFeatLanes / 2; o > 0; o >>= 1) near += __shfl_xor_sync(gmask, near, o, kFeatLanes);
+        __syncwarp(gmask);
         if (lane == 0) {
             float *f = feat + p * kFeatures;
             f[0] = log2f((float)m + 1.f);
@@ -311,7 +353,7 @@ cudaError_t launch_features(const uint32_t *texts, const int64_t *text_off, cons
                             const uint32_t *patterns, const int64_t *pat_off, const int32_t *pat_len, int32_t n,
                             float *feat, int sm_count, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
-    const int64_t blocks = std::min<int64_t>(((int64_t)n + 7) / 8, (int64_t)sm_count * 16);
+    const int64_t blocks = std::min<int64_t>(((int64_t)n * kFeatLanes + 255) / 256, (int64_t)sm_count * 16);
     features_kernel<<<(unsigned)blocks, 256, 0, s>>>(texts, text_off, text_len, patterns, pat_off, pat_len, n, feat);
     return cudaGetLastError();
 }
@@ -355,6 +397,11 @@ int learned_kernel_count(int32_t n) {
 int64_t sort_temp_words(int32_t n) {
     const int64_t nb = ((int64_t)n + kSortTile - 1) / kSortTile;
     return 256 * nb * 3 + scan_temp_words(256 * nb) + 8;
+}
+
+const int64_t *learned_bucket_start(const int64_t *tmp, int32_t n, int key) {
+    const int64_t nb = ((int64_t)n + kSortTile - 1) / kSortTile;
+    return tmp + 256 * nb + (int64_t)key * nb;  // bucket-major exclusive offsets, tile 0 of the bucket
 }
 
 cudaError_t launch_learned_order(const float *pred, const int32_t *pat_len, int32_t n, uint8_t *key, int32_t *order,

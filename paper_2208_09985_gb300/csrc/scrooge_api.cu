@@ -65,8 +65,11 @@ int scrooge_destroy(scrooge_ctx *c) {
                      &c->in_poff,   &c->in_plen, &c->out_ec,  &c->out_tc,   &c->out_cig,  &c->out_off,
                      &c->scr_runs,  &c->scr_off, &c->scr_len, &c->scr_cap,  &c->scan_tmp, &c->queue,
                      &c->model,     &c->grad,    &c->adam_m1, &c->adam_m2,  &c->loss,     &c->l_feat,
-                     &c->l_pred,    &c->l_key,   &c->l_order, &c->l_tmp,    &c->t_rows,   &c->fallback};
+                     &c->l_pred,    &c->l_key,   &c->l_order, &c->l_tmp,    &c->t_rows,   &c->fallback, &c->spill2};
     if (c->graph) cudaGraphExecDestroy(c->graph);
+    if (c->stream2) cudaStreamDestroy(c->stream2);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     for (DevBuf *b : all) release(*b);
     delete c;
     return SCROOGE_OK;
@@ -174,6 +177,14 @@ int scrooge_get_kernel_config(const scrooge_ctx *c, int32_t words, int32_t *lane
     return SCROOGE_OK;
 }
 
+int scrooge_set_heavy_class(scrooge_ctx *c, int32_t load_class) {
+    if (!c || load_class < 0 || load_class > 16) return SCROOGE_E_INVAL;
+    c->heavy_class = load_class;
+    return SCROOGE_OK;
+}
+
+int32_t scrooge_get_heavy_class(const scrooge_ctx *c) { return c ? c->heavy_class : -1; }
+
 int scrooge_last_launch_shape(const scrooge_ctx *c, int64_t *shape, int32_t n) {
     if (!c || !shape || n < 1) return SCROOGE_E_INVAL;
     memcpy(shape, c->last_shape, sizeof(int64_t) * (size_t)std::min(n, 12));
@@ -204,6 +215,110 @@ int scrooge_set_stats(scrooge_ctx *c, int32_t *windows, int64_t *rows, int64_t *
     c->st_cycles = cycles;
     return SCROOGE_OK;
 }
+
+}  // extern "C"
+
+namespace {
+
+// One alignment-kernel launch: which kernel, its shape and its parameters.
+struct LaunchPlan {
+    bool band = false, sene = true;
+    int words = 0, G = 0, wpb = 1, blocks = 0;
+    size_t smem = 0;
+    TableShape ts{};
+    AlignParams p{};
+};
+
+// Shape of the kernel a call with these flags uses (banded or full width), sized for the device
+// and the context's kernel settings; sizes the row scratch in `spill` (and the banded kernel's
+// fallback area). Queue, order and status are set by the caller.
+int make_plan(scrooge_ctx *c, const AlignParams &base, bool band, uint32_t flags, DevBuf &spill, LaunchPlan &out) {
+    const int W = base.W, O = base.O, k = base.k;
+    const int words = words_for(W);
+    const bool sene = !(flags & SCROOGE_NO_SENE);
+    const bool dent = !(flags & SCROOGE_NO_DENT);
+    const KernelConfig kc = c->kcfg[kcfg_index(band ? 0 : words)];
+    int G = kc.lanes;
+    auto supported = [&](int lanes, int swp) {
+        return words == 1 ? supported_w32(lanes, sene, swp)
+                          : (words == 2 ? supported_w64(lanes, sene, swp) : supported_w128(lanes, sene, swp));
+    };
+    TableShape ts = table_shape(W, O, words, G, dent, sene);
+    if (band) ts.swp = 1;  // one 32-bit band word per stored entry
+    if (!band && !supported(G, ts.swp)) {  // the edge-storing ablation exists for the default lane count only
+        G = words == 1 ? 2 : (words == 2 ? 4 : 8);
+        ts = table_shape(W, O, words, G, dent, sene);
+        if (!supported(G, ts.swp)) return fail(c, SCROOGE_E_INVAL, "no kernel for this W/O/flags combination");
+    }
+    AlignParams p = base;
+    const int PPW = 32 / G, chunk = 32 * words / G;
+    p.et = (flags & SCROOGE_NO_ET) ? 0 : 1;
+    p.sene = sene ? 1 : 0;
+    p.ncol = ts.ncol;
+    p.sw = ts.swp;
+    p.rstride = row_stride_cells(ts, PPW, chunk);
+    const int rows_needed = band ? std::min(k, kBandRows - 1) + 1 : k + 1;  // rows the kernel may store
+    int rcap = std::min(kc.rows, rows_needed);
+    const int stage = stage_words_per_warp(words, PPW);
+    int wpb = kc.wpb;
+    // keep the block's shared memory within the opt-in limit
+    while (rcap > 1 && (size_t)wpb * (table_words_per_warp(rcap, ts, PPW, chunk) + stage) * 4 > c->smem_optin) --rcap;
+    while (wpb > 1 && (size_t)wpb * (table_words_per_warp(rcap, ts, PPW, chunk) + stage) * 4 > c->smem_optin) --wpb;
+    p.rcap = rcap;
+    p.table_words_per_warp = (int32_t)table_words_per_warp(rcap, ts, PPW, chunk);
+    p.smem_words_per_warp = p.table_words_per_warp + stage;
+    const size_t smem = (size_t)wpb * p.smem_words_per_warp * 4;
+    int per_sm = 0;
+    cudaError_t e = band ? occupancy_band(G, wpb, smem, &per_sm)
+                         : (words == 1 ? occupancy_w32(G, sene, ts.swp, wpb, smem, &per_sm)
+                                       : (words == 2 ? occupancy_w64(G, sene, ts.swp, wpb, smem, &per_sm)
+                                                     : occupancy_w128(G, sene, ts.swp, wpb, smem, &per_sm)));
+    if (e != cudaSuccess) return cuda_fail(c, e, "occupancy query");
+    if (per_sm < 1) return fail(c, SCROOGE_E_INVAL, "kernel config does not fit on an SM (smem %zu B)", smem);
+    const int64_t groups = ((int64_t)p.n_pairs + PPW - 1) / PPW;
+    const int64_t want_blocks = (groups + wpb - 1) / wpb;
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(want_blocks, (int64_t)per_sm * c->sm_count));
+    const int spill_rows = std::max(0, rows_needed - rcap);
+    p.spill_words_per_pair = table_words_per_warp(spill_rows, ts, PPW, chunk);  // per warp
+    const size_t spill_bytes = (size_t)blocks * wpb * (size_t)std::max<int64_t>(p.spill_words_per_pair, 4) * 4;
+    int rc;
+    if ((rc = ensure(c, spill, spill_bytes, "DP row scratch"))) return rc;
+    p.spill = (uint32_t *)spill.p;
+    p.fb = nullptr;
+    p.fb_words_per_warp = 0;
+    if (band) {
+        p.fb_words_per_warp = band_fallback_words(k, ts.ncol, PPW);
+        if (p.fb_words_per_warp > 0) {
+            if ((rc = ensure(c, c->fallback, (size_t)blocks * wpb * (size_t)p.fb_words_per_warp * 4,
+                             "full-width fallback scratch")))
+                return rc;
+            p.fb = (uint32_t *)c->fallback.p;
+        }
+    }
+    out.band = band;
+    out.sene = sene;
+    out.words = words;
+    out.G = G;
+    out.wpb = wpb;
+    out.blocks = blocks;
+    out.smem = smem;
+    out.ts = ts;
+    out.p = p;
+    return SCROOGE_OK;
+}
+
+cudaError_t launch_plan(const LaunchPlan &lp, cudaStream_t st) {
+    if (lp.band) return launch_align_band(lp.p, lp.G, lp.wpb, lp.blocks, lp.smem, st);
+    switch (lp.words) {
+        case 1: return launch_align_w32(lp.p, lp.G, lp.sene, lp.ts.swp, lp.wpb, lp.blocks, lp.smem, st);
+        case 2: return launch_align_w64(lp.p, lp.G, lp.sene, lp.ts.swp, lp.wpb, lp.blocks, lp.smem, st);
+        default: return launch_align_w128(lp.p, lp.G, lp.sene, lp.ts.swp, lp.wpb, lp.blocks, lp.smem, st);
+    }
+}
+
+}  // namespace
+
+extern "C" {
 
 int scrooge_align_batch(scrooge_ctx *c, const uint32_t *texts, const int64_t *text_offsets,
                         const int32_t *text_lengths, const uint32_t *patterns, const int64_t *pattern_offsets,
@@ -320,71 +435,25 @@ int scrooge_align_batch(scrooge_ctx *c, const uint32_t *texts, const int64_t *te
     p.cigar_off = (const int64_t *)c->scr_off.p;
     p.cigar_lens = (int32_t *)c->scr_len.p;
 
-    // kernel shape
-    const int words = words_for(W);
-    const bool sene = !(flags & SCROOGE_NO_SENE);
-    const bool dent = !(flags & SCROOGE_NO_DENT);
+    p.st_windows = c->st_windows;
+    p.st_rows = c->st_rows;
+    p.st_cells = c->st_cells;
+    p.st_cycles = c->st_cycles;
+    // kernel shape(s): the kernel the call uses, and with SCROOGE_LEARNED on band-sized windows
+    // the full-width kernel for the pairs the ordering puts in the heavy load classes
     const bool band = use_band(W, flags);
-    const KernelConfig kc = c->kcfg[kcfg_index(band ? 0 : words)];
-    int G = kc.lanes;
-    auto supported = [&](int lanes, int swp) {
-        return words == 1 ? supported_w32(lanes, sene, swp)
-                          : (words == 2 ? supported_w64(lanes, sene, swp) : supported_w128(lanes, sene, swp));
-    };
-    TableShape ts = table_shape(W, O, words, G, dent, sene);
-    if (band) ts.swp = 1;  // one 32-bit band word per stored entry
-    if (!band && !supported(G, ts.swp)) {  // the edge-storing ablation exists for the default lane count only
-        G = words == 1 ? 2 : (words == 2 ? 4 : 8);
-        ts = table_shape(W, O, words, G, dent, sene);
-        if (!supported(G, ts.swp)) return fail(c, SCROOGE_E_INVAL, "no kernel for this W/O/flags combination");
-    }
-    const int PPW = 32 / G;
-    p.et = (flags & SCROOGE_NO_ET) ? 0 : 1;
-    p.sene = sene ? 1 : 0;
-    p.ncol = ts.ncol;
-    p.sw = ts.swp;
-    p.rstride = row_stride_cells(ts, PPW, 32 * words / G);
-    const int rows_needed = band ? std::min(k, kBandRows - 1) + 1 : k + 1;  // rows the kernel may store
-    int rcap = std::min(kc.rows, rows_needed);
-    const int stage = stage_words_per_warp(words, PPW);
-    int wpb = kc.wpb;
-    // keep the block's shared memory within the opt-in limit
-    while (rcap > 1 && (size_t)wpb * (table_words_per_warp(rcap, ts, PPW, 32 * words / G) + stage) * 4 > c->smem_optin) --rcap;
-    while (wpb > 1 && (size_t)wpb * (table_words_per_warp(rcap, ts, PPW, 32 * words / G) + stage) * 4 > c->smem_optin) --wpb;
-    p.rcap = rcap;
-    p.table_words_per_warp = (int32_t)table_words_per_warp(rcap, ts, PPW, 32 * words / G);
-    p.smem_words_per_warp = p.table_words_per_warp + stage;
-    const size_t smem = (size_t)wpb * p.smem_words_per_warp * 4;
-    int per_sm = 0;
-    e = band ? occupancy_band(G, wpb, smem, &per_sm)
-             : (words == 1 ? occupancy_w32(G, sene, ts.swp, wpb, smem, &per_sm)
-                           : (words == 2 ? occupancy_w64(G, sene, ts.swp, wpb, smem, &per_sm)
-                                         : occupancy_w128(G, sene, ts.swp, wpb, smem, &per_sm)));
-    if (e != cudaSuccess) return cuda_fail(c, e, "occupancy query");
-    if (per_sm < 1) return fail(c, SCROOGE_E_INVAL, "kernel config does not fit on an SM (smem %zu B)", smem);
-    const int64_t groups = ((int64_t)n_pairs + PPW - 1) / PPW;
-    const int64_t want_blocks = (groups + wpb - 1) / wpb;
-    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(want_blocks, (int64_t)per_sm * c->sm_count));
-    const int spill_rows = std::max(0, rows_needed - rcap);
-    p.spill_words_per_pair = table_words_per_warp(spill_rows, ts, PPW, 32 * words / G);  // per warp
-    const size_t spill_bytes = (size_t)blocks * wpb * (size_t)std::max<int64_t>(p.spill_words_per_pair, 4) * 4;
-    if ((rc = ensure(c, c->spill, spill_bytes, "DP row scratch")) || (rc = ensure(c, c->status, 64, "status")))
-        return rc;
-    p.spill = (uint32_t *)c->spill.p;
-    if (band) {
-        p.fb_words_per_warp = band_fallback_words(k, ts.ncol, PPW);
-        if (p.fb_words_per_warp > 0) {
-            if ((rc = ensure(c, c->fallback, (size_t)blocks * wpb * (size_t)p.fb_words_per_warp * 4,
-                             "full-width fallback scratch")))
-                return rc;
-            p.fb = (uint32_t *)c->fallback.p;
+    const bool split = band && (flags & SCROOGE_LEARNED) && c->heavy_class < 16;
+    LaunchPlan plan, heavy;
+    if ((rc = make_plan(c, p, band, flags, c->spill, plan))) return rc;
+    if (split && (rc = make_plan(c, p, false, flags | SCROOGE_NO_BAND, c->spill2, heavy))) return rc;
+    if ((rc = ensure(c, c->status, 64, "status"))) return rc;
+    if ((flags & SCROOGE_PERSISTENT) && (rc = ensure(c, c->queue, 128, "work queues"))) return rc;
+    for (LaunchPlan *lp : {&plan, &heavy}) {
+        lp->p.status = (int32_t *)c->status.p;
+        if (flags & SCROOGE_PERSISTENT) {
+            lp->p.queue = (int32_t *)c->queue.p + (lp == &heavy ? 16 : 0);
+            lp->p.order = (c->order && c->order_n == n_pairs) ? c->order : nullptr;
         }
-    }
-    p.status = (int32_t *)c->status.p;
-    if (flags & SCROOGE_PERSISTENT) {
-        if ((rc = ensure(c, c->queue, 64, "work queue"))) return rc;
-        p.queue = (int32_t *)c->queue.p;
-        p.order = (c->order && c->order_n == n_pairs) ? c->order : nullptr;
     }
     if (flags & SCROOGE_LEARNED) {
         // buffers of the ordering pipeline must exist before any capture
@@ -394,25 +463,40 @@ int scrooge_align_batch(scrooge_ctx *c, const uint32_t *texts, const int64_t *te
             (rc = ensure(c, c->l_order, npp * 4, "pair order")) ||
             (rc = ensure(c, c->l_tmp, (size_t)sort_temp_words(n_pairs) * 8, "sort scratch")))
             return rc;
-        p.order = (const int32_t *)c->l_order.p;
+        plan.p.order = heavy.p.order = (const int32_t *)c->l_order.p;
+    }
+    if (split) {
+        // the ordering puts load classes >= heavy_class first; they end where bucket key (16 - class) << 4 starts
+        const int64_t *at = learned_bucket_start((int64_t *)c->l_tmp.p, n_pairs, (16 - c->heavy_class) << 4);
+        heavy.p.split_at = plan.p.split_at = at;
+        heavy.p.split_side = 0;
+        plan.p.split_side = 1;
+        // the banded kernel's stream gets the lowest priority, so the block scheduler dispatches the heavy
+        // kernel's blocks first whatever order the two launches (or graph nodes) reach it in
+        int prio_least = 0, prio_greatest = 0;
+        cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
+        if (!c->stream2 && ((e = cudaStreamCreateWithPriority(&c->stream2, cudaStreamNonBlocking, prio_least)) !=
+                                cudaSuccess ||
+                            (e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming)) != cudaSuccess ||
+                            (e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming)) != cudaSuccess))
+            return cuda_fail(c, e, "second stream");
     }
     {
-        const int64_t shape[12] = {band ? 0 : words, G, rcap, wpb, (int64_t)smem, blocks, p.ncol, ts.swp,
-                                   p.table_words_per_warp * 4LL, p.spill_words_per_pair * 4, p.fb_words_per_warp * 4,
-                                   PPW};
+        const TableShape &ts = plan.ts;
+        const int64_t shape[12] = {plan.band ? 0 : plan.words, plan.G, plan.p.rcap, plan.wpb, (int64_t)plan.smem,
+                                   plan.blocks, plan.p.ncol, ts.swp, plan.p.table_words_per_warp * 4LL,
+                                   plan.p.spill_words_per_pair * 4, plan.p.fb_words_per_warp * 4, 32 / plan.G};
         memcpy(c->last_shape, shape, sizeof shape);
     }
-    p.st_windows = c->st_windows;
-    p.st_rows = c->st_rows;
-    p.st_cells = c->st_cells;
-    p.st_cycles = c->st_cycles;
     int64_t *dense_off = dev ? cigar_offsets : (int64_t *)c->out_off.p;
     c->last_kernels = 1 + scan_kernel_count(n_pairs) + 1;  // alignment, CIGAR offsets, gather
+    if (split) c->last_kernels += 1;
     if (flags & SCROOGE_LEARNED) c->last_kernels += learned_kernel_count(n_pairs);
     // everything from the status reset to the CIGAR offsets, on `st`
     auto enqueue = [&]() -> int {
-        if ((e = cudaMemsetAsync(p.status, 0, 4, st)) != cudaSuccess) return cuda_fail(c, e, "status reset");
-        if (p.queue && (e = cudaMemsetAsync(p.queue, 0, 4, st)) != cudaSuccess) return cuda_fail(c, e, "queue reset");
+        if ((e = cudaMemsetAsync(plan.p.status, 0, 4, st)) != cudaSuccess) return cuda_fail(c, e, "status reset");
+        if (plan.p.queue && (e = cudaMemsetAsync(c->queue.p, 0, 128, st)) != cudaSuccess)
+            return cuda_fail(c, e, "queue reset");
         if (flags & SCROOGE_LEARNED) {
             const int lrc = learned_order(c, p.texts, p.text_off, p.text_len, p.patterns, p.pat_off, p.pat_len,
                                           n_pairs);
@@ -420,11 +504,20 @@ int scrooge_align_batch(scrooge_ctx *c, const uint32_t *texts, const int64_t *te
         }
         const bool timed = c->t_start && c->t_stop && !(flags & SCROOGE_GRAPH);
         if (timed) cudaEventRecord(c->t_start, st);
-        e = band ? launch_align_band(p, G, wpb, blocks, smem, st)
-                 : (words == 1 ? launch_align_w32(p, G, sene, ts.swp, wpb, blocks, smem, st)
-                               : (words == 2 ? launch_align_w64(p, G, sene, ts.swp, wpb, blocks, smem, st)
-                                             : launch_align_w128(p, G, sene, ts.swp, wpb, blocks, smem, st)));
-        if (e != cudaSuccess) return cuda_fail(c, e, "alignment kernel launch");
+        if (split) {
+            // heavy pairs on the full-width kernel first; the banded kernel on a second stream takes
+            // over the SMs as the heavy blocks retire
+            if ((e = cudaEventRecord(c->ev_fork, st)) != cudaSuccess ||
+                (e = cudaStreamWaitEvent(c->stream2, c->ev_fork, 0)) != cudaSuccess)
+                return cuda_fail(c, e, "stream fork");
+            if ((e = launch_plan(heavy, st)) != cudaSuccess) return cuda_fail(c, e, "alignment kernel launch");
+            if ((e = launch_plan(plan, c->stream2)) != cudaSuccess) return cuda_fail(c, e, "alignment kernel launch");
+            if ((e = cudaEventRecord(c->ev_join, c->stream2)) != cudaSuccess ||
+                (e = cudaStreamWaitEvent(st, c->ev_join, 0)) != cudaSuccess)
+                return cuda_fail(c, e, "stream join");
+        } else if ((e = launch_plan(plan, st)) != cudaSuccess) {
+            return cuda_fail(c, e, "alignment kernel launch");
+        }
         if (timed) cudaEventRecord(c->t_stop, st);
         // dense CIGAR: prefix sums of the run counts (the gather follows)
         if ((e = exclusive_scan(p.cigar_lens, 0, n_pairs, dense_off, (int64_t *)c->scan_tmp.p, st)) != cudaSuccess)
@@ -436,7 +529,7 @@ int scrooge_align_batch(scrooge_ctx *c, const uint32_t *texts, const int64_t *te
     };
     if (flags & SCROOGE_GRAPH) {
         // one captured graph per distinct call; replayed while the call repeats
-        const unsigned long long key[26] = {(unsigned long long)(uintptr_t)p.texts, (unsigned long long)(uintptr_t)p.text_off,
+        const unsigned long long key[28] = {(unsigned long long)(uintptr_t)p.texts, (unsigned long long)(uintptr_t)p.text_off,
             (unsigned long long)(uintptr_t)p.text_len, (unsigned long long)(uintptr_t)p.patterns,
             (unsigned long long)(uintptr_t)p.pat_off, (unsigned long long)(uintptr_t)p.pat_len,
             (unsigned long long)(uintptr_t)p.edit_counts, (unsigned long long)(uintptr_t)p.text_consumed,
@@ -444,11 +537,17 @@ int scrooge_align_batch(scrooge_ctx *c, const uint32_t *texts, const int64_t *te
             (unsigned long long)(uintptr_t)dense_off, (unsigned long long)(uintptr_t)(dev ? cigar : nullptr),
             (unsigned long long)cigar_capacity, (unsigned long long)n_pairs,
             ((unsigned long long)W << 32) | ((unsigned long long)O << 16) | (unsigned long long)k,
-            (unsigned long long)flags, (unsigned long long)(uintptr_t)p.spill, (unsigned long long)(uintptr_t)p.order,
-            (unsigned long long)(uintptr_t)st, ((unsigned long long)G << 32) | (unsigned long long)rcap,
-            ((unsigned long long)wpb << 32) | (unsigned long long)blocks, (unsigned long long)(uintptr_t)c->st_rows,
-            (unsigned long long)(uintptr_t)c->st_cells, (unsigned long long)(uintptr_t)c->st_windows,
-            (unsigned long long)(uintptr_t)p.fb, (unsigned long long)band};
+            (unsigned long long)flags, (unsigned long long)(uintptr_t)plan.p.spill,
+            (unsigned long long)(uintptr_t)plan.p.order, (unsigned long long)(uintptr_t)st,
+            ((unsigned long long)plan.G << 32) | (unsigned long long)plan.p.rcap,
+            ((unsigned long long)plan.wpb << 32) | (unsigned long long)plan.blocks,
+            (unsigned long long)(uintptr_t)c->st_rows, (unsigned long long)(uintptr_t)c->st_cells,
+            (unsigned long long)(uintptr_t)c->st_windows, (unsigned long long)(uintptr_t)plan.p.fb,
+            (unsigned long long)band,
+            split ? (((unsigned long long)heavy.G << 48) | ((unsigned long long)heavy.p.rcap << 32) |
+                     ((unsigned long long)heavy.wpb << 24) | (unsigned long long)heavy.blocks)
+                  : 0ull,
+            split ? (((unsigned long long)(uintptr_t)heavy.p.spill) ^ ((unsigned long long)c->heavy_class << 56)) : 0ull};
         if (!c->graph || memcmp(key, c->graph_key, sizeof key) != 0) {
             if (c->graph) {
                 cudaGraphExecDestroy(c->graph);
@@ -480,7 +579,7 @@ int scrooge_align_batch(scrooge_ctx *c, const uint32_t *texts, const int64_t *te
     if (dev) {
         if (!(flags & SCROOGE_SYNC)) return SCROOGE_OK;
         int64_t total = 0;
-        if ((e = cudaMemcpyAsync(&status_h, p.status, 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        if ((e = cudaMemcpyAsync(&status_h, plan.p.status, 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
             (e = cudaMemcpyAsync(&total, dense_off + n_pairs, 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
             (e = cudaStreamSynchronize(st)) != cudaSuccess)
             return cuda_fail(c, e, "stream synchronise");
@@ -492,7 +591,7 @@ int scrooge_align_batch(scrooge_ctx *c, const uint32_t *texts, const int64_t *te
     }
     // host pointers: learn the total, gather into a device buffer, copy back
     if ((e = cudaMemcpyAsync(cigar_offsets, dense_off, (np + 1) * 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(&status_h, p.status, 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(&status_h, plan.p.status, 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
         (e = cudaStreamSynchronize(st)) != cudaSuccess)
         return cuda_fail(c, e, "CIGAR offsets copy");
     if (status_h != 0) return fail(c, SCROOGE_E_INTERNAL, "kernel status %d", status_h);
@@ -579,9 +678,49 @@ int scrooge_autotune(scrooge_ctx *c, const uint32_t *texts, const int64_t *text_
             if (rc != SCROOGE_OK) break;
         }
     }
+    c->kcfg[ix] = rc == SCROOGE_OK ? best_cfg : saved;
+    // learned launches on band-sized windows: which load classes go to the full-width kernel
+    if (rc == SCROOGE_OK && (flags & SCROOGE_LEARNED) && use_band(W, flags)) {
+        const int32_t saved_class = c->heavy_class;
+        const int classes[] = {16, 15, 14, 13, 12, 11, 10, 0};
+        float best_t = -1.f;
+        int best_class = saved_class;
+        for (int hc : classes) {
+            c->heavy_class = hc;
+            rc = scrooge_align_batch(c, texts, text_offsets, text_lengths, patterns, pattern_offsets,
+                                     pattern_lengths, n_pairs, W, O, k, fl, edit_counts, text_consumed, cigar,
+                                     cigar_capacity, cigar_offsets);
+            float tmin = -1.f;
+            for (int r = 0; r < repeats && rc == SCROOGE_OK; ++r) {
+                cudaEventRecord(e0, c->stream);
+                rc = scrooge_align_batch(c, texts, text_offsets, text_lengths, patterns, pattern_offsets,
+                                         pattern_lengths, n_pairs, W, O, k, fl, edit_counts, text_consumed, cigar,
+                                         cigar_capacity, cigar_offsets);
+                cudaEventRecord(e1, c->stream);
+                if (cudaEventSynchronize(e1) != cudaSuccess) rc = fail(c, SCROOGE_E_CUDA, "event sync failed");
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (tmin < 0.f || ms < tmin) tmin = ms;
+            }
+            if (rc != SCROOGE_OK) break;
+            if (results && nres < max_results) {
+                int32_t *r = results + 5 * nres;
+                r[0] = 0;
+                r[1] = hc;
+                r[2] = 0;
+                r[3] = (int32_t)(tmin * 1000.f);
+                r[4] = 2;
+            }
+            ++nres;
+            if (best_t < 0.f || tmin < best_t) {
+                best_t = tmin;
+                best_class = hc;
+            }
+        }
+        c->heavy_class = rc == SCROOGE_OK ? best_class : saved_class;
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    c->kcfg[ix] = rc == SCROOGE_OK ? best_cfg : saved;
     if (n_results) *n_results = std::min(nres, max_results);
     return rc;
 }

@@ -33,7 +33,12 @@ struct scrooge_ctx {
     // full-width kernels of 1, 2, 4 words, then the banded kernel (autotuned on GB300)
     scrooge::KernelConfig kcfg[4] = {{2, 8, 2}, {4, 4, 2}, {8, 8, 2}, {4, 8, 2}};
     int fail_allocs = 0;  // testing hook: fail the next N device allocations
-    scrooge::DevBuf spill, status, fallback;
+    scrooge::DevBuf spill, status, fallback, spill2;
+    // pairs the learned ordering puts in load classes >= heavy_class run on the full-width kernel
+    // (16: none); the banded kernel then runs the rest on stream2
+    int32_t heavy_class = 16;
+    cudaStream_t stream2 = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     scrooge::DevBuf in_text, in_pat, in_toff, in_tlen, in_poff, in_plen;
     scrooge::DevBuf out_ec, out_tc, out_cig, out_off;
     scrooge::DevBuf scr_runs, scr_off, scr_len, scr_cap, scan_tmp;
@@ -52,7 +57,7 @@ struct scrooge_ctx {
     int64_t last_shape[12] = {0};  // launch shape of the last alignment call (scrooge_last_launch_shape)
     // CUDA graph of the learned pipeline, keyed by the call it was captured for
     cudaGraphExec_t graph = nullptr;
-    unsigned long long graph_key[26] = {0};
+    unsigned long long graph_key[28] = {0};
 };
 
 namespace scrooge {

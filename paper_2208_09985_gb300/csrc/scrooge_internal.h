@@ -41,6 +41,8 @@ struct AlignParams {
     int32_t table_words_per_warp;
     const int32_t *order;   // optional pair order (slot -> pair id)
     int32_t *queue;         // persistent mode: next slot to hand out (nullptr: static)
+    const int64_t *split_at;  // persistent mode: slots [0, *split_at) or [*split_at, n_pairs) only (nullptr: all)
+    int32_t split_side;       // 0: the slots below *split_at, 1: the slots from it
     int32_t *status;        // bit 0: traceback found no edge (impossible by Theorem 1)
     int32_t *st_windows;
     int64_t *st_rows;
@@ -147,6 +149,9 @@ cudaError_t launch_adam(float *model, const float *grad, float *m1, float *m2, f
 cudaError_t launch_feature_stats(const float *feat, int32_t n, float *model, cudaStream_t s);
 int64_t sort_temp_words(int32_t n);
 int learned_kernel_count(int32_t n);
+// Device address of the first position of bucket `key` in the order that launch_learned_order
+// wrote with scratch `tmp` (the number of pairs with a smaller key).
+const int64_t *learned_bucket_start(const int64_t *tmp, int32_t n, int key);
 cudaError_t launch_learned_order(const float *pred, const int32_t *pat_len, int32_t n, uint8_t *key, int32_t *order,
                                  int64_t *tmp, cudaStream_t s);
 

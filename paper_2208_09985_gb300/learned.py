@@ -99,10 +99,13 @@ def autotune_cached(ctx, db, W: int, O: int, flags: int = 0, cache_path: str | N
     if key in cache:
         lanes, rows, wpb = cache[key]["config"]
         sc.scrooge_set_kernel_config(ctx, words, lanes, rows, wpb)
+        if "heavy_class" in cache[key]:
+            sc.scrooge_set_heavy_class(ctx, cache[key]["heavy_class"])
         return cache[key]
     table = sc.autotune_device(ctx, db, W, O, flags=flags, repeats=repeats)
     cfg = sc.scrooge_get_kernel_config(ctx, words)
-    entry = {"config": list(cfg), "table": [list(r) for r in table], "pairs": db.n_pairs}
+    entry = {"config": list(cfg), "table": [list(r) for r in table], "pairs": db.n_pairs,
+             "heavy_class": sc.scrooge_get_heavy_class(ctx)}
     if cache_path:
         cache[key] = entry
         tmp = cache_path + ".tmp"

@@ -261,3 +261,46 @@ def test_learned_order_is_stable_bucket_sort(ctx):
     assert (np.diff(k) >= 0).all(), "not sorted by key"
     for kv in np.unique(k):  # stable: input order inside a key
         assert (np.diff(got[k == kv]) > 0).all()
+
+
+def test_heavy_buckets_on_the_full_width_kernel_identical(ctx):
+    """Learned launches that send heavy load classes to the full-width kernel change nothing."""
+    import torch
+    h, s = ctx
+    b = synth.concat([synth.uneven_reads(200, seed=21), synth.fixed_error(40, 0.15, length=3000, seed=22),
+                      synth.short_reads(300, seed=23)])
+    db = sc.DeviceBatch(sc.PackedBatch(b))
+    plain = _run(ctx, db, 0)
+    assert_same(plain, oracle.align_batch(b, 64, 24), label="plain")
+    with torch.cuda.stream(s):
+        learned.train(h, db, epochs=5, batch=256)
+    saved = sc.scrooge_get_heavy_class(h)
+    try:
+        for hc in (0, 6, 10, 13, 16):
+            sc.scrooge_set_heavy_class(h, hc)
+            assert sc.scrooge_get_heavy_class(h) == hc
+            for flags in (sc.SCROOGE_LEARNED, sc.SCROOGE_LEARNED | sc.SCROOGE_GRAPH):
+                for rep in range(2):
+                    _same_device(_run(ctx, db, flags), plain, f"heavy class {hc} flags {flags} run {rep}")
+            ref33 = _run(ctx, db, 0, O=33)
+            _same_device(_run(ctx, db, sc.SCROOGE_LEARNED, O=33), ref33, f"heavy class {hc} O=33")
+    finally:
+        sc.scrooge_set_heavy_class(h, saved)
+    with pytest.raises(sc.ScroogeError):
+        sc.scrooge_set_heavy_class(h, 17)
+
+
+def test_autotune_picks_a_heavy_class(ctx):
+    h, s = ctx
+    b = synth.concat([synth.uneven_reads(150, seed=31), synth.fixed_error(30, 0.15, length=2000, seed=32)])
+    db = sc.DeviceBatch(sc.PackedBatch(b))
+    import torch
+    with torch.cuda.stream(s):
+        learned.train(h, db, epochs=3, batch=256)
+        table = sc.autotune_device(h, db, 64, 24, flags=sc.SCROOGE_LEARNED, repeats=1)
+    s.synchronize()
+    kinds = [r[4] for r in table]
+    assert 1 in kinds and 2 in kinds
+    assert sc.scrooge_get_heavy_class(h) in [r[1] for r in table if r[4] == 2]
+    got = _run(ctx, db, sc.SCROOGE_LEARNED)
+    assert_same(got, oracle.align_batch(b, 64, 24), label="after autotune")
