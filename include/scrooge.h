@@ -196,10 +196,11 @@ int scrooge_last_launch_shape(const scrooge_ctx *ctx, int64_t *shape, int32_t n)
  * `repeats` timed runs per configuration (CUDA events on the context stream,
  * after one untimed run), and installs the fastest configuration in the
  * context. If `results` is not NULL it receives up to max_results rows of 5
- * int32: lanes, rows, warps, microseconds, 1; with SCROOGE_LEARNED on windows
- * the banded kernel serves it then also times the heavy load classes
- * (scrooge_set_heavy_class) 16, 15, ..., 10, 0 with the chosen settings, as
- * rows 0, class, 0, microseconds, 2, and installs the fastest class.
+ * int32: lanes, rows, warps, microseconds, 1. With SCROOGE_LEARNED on windows
+ * the banded kernel serves, it also times the heavy load classes
+ * (scrooge_set_heavy_class) 16, 15, ..., 10, 0 before and again after the
+ * settings sweep (at least 3 timed runs each), as rows 0, class, 0,
+ * microseconds, 2, and installs the fastest class of the second pass.
  * *n_results gets the row count.
  * Synchronous. */
 int scrooge_autotune(scrooge_ctx *ctx, const uint32_t *texts, const int64_t *text_offsets,

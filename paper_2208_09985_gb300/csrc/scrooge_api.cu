@@ -627,51 +627,80 @@ int scrooge_autotune(scrooge_ctx *c, const uint32_t *texts, const int64_t *text_
     const int words = words_for(W);
     const int ix = kcfg_index(use_band(W, flags) ? 0 : words);
     const KernelConfig saved = c->kcfg[ix];
+    const int32_t saved_class = c->heavy_class;
     const int lanes_opts[4][3] = {{1, 2, 4}, {2, 4, 8}, {8, 16, 0}, {2, 4, 8}};
     const int rows_opts[] = {1, 2, 3, 4, 6, 8, 10, 12, 16, 20};
     const int wpb_opts[] = {1, 2};
+    const int classes[] = {16, 15, 14, 13, 12, 11, 10, 0};
+    const bool tune_classes = (flags & SCROOGE_LEARNED) && use_band(W, flags);
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         return fail(c, SCROOGE_E_CUDA, "cudaEventCreate failed");
-    float best = -1.f;
-    KernelConfig best_cfg = saved;
     int nres = 0, rc = SCROOGE_OK;
     const uint32_t fl = (flags | SCROOGE_DEVICE_PTRS) & ~(uint32_t)SCROOGE_SYNC;
+    auto call = [&]() {
+        return scrooge_align_batch(c, texts, text_offsets, text_lengths, patterns, pattern_offsets, pattern_lengths,
+                                   n_pairs, W, O, k, fl, edit_counts, text_consumed, cigar, cigar_capacity,
+                                   cigar_offsets);
+    };
+    // one untimed run, then the fastest of `reps` timed runs (CUDA events on the context stream)
+    auto time_it = [&](int reps, float &tmin) -> int {
+        tmin = -1.f;
+        int r = call();
+        for (int i = 0; i < reps && r == SCROOGE_OK; ++i) {
+            cudaEventRecord(e0, c->stream);
+            r = call();
+            cudaEventRecord(e1, c->stream);
+            if (cudaEventSynchronize(e1) != cudaSuccess) return fail(c, SCROOGE_E_CUDA, "event sync failed");
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (tmin < 0.f || ms < tmin) tmin = ms;
+        }
+        return r;
+    };
+    auto record = [&](int a, int b, int w, float ms, int kind) {
+        if (results && nres < max_results) {
+            int32_t *r = results + 5 * nres;
+            r[0] = a;
+            r[1] = b;
+            r[2] = w;
+            r[3] = (int32_t)(ms * 1000.f);
+            r[4] = kind;
+        }
+        ++nres;
+    };
+    // learned launches on band-sized windows: which load classes go to the full-width kernel
+    auto sweep_classes = [&]() -> int {
+        float best_t = -1.f;
+        int best_class = c->heavy_class;
+        for (int hc : classes) {
+            c->heavy_class = hc;
+            float t;
+            const int r = time_it(std::max(repeats, 3), t);
+            if (r != SCROOGE_OK) return r;
+            record(0, hc, 0, t, 2);
+            if (best_t < 0.f || t < best_t) {
+                best_t = t;
+                best_class = hc;
+            }
+        }
+        c->heavy_class = best_class;
+        return SCROOGE_OK;
+    };
+    if (tune_classes) rc = sweep_classes();
+    float best = -1.f;
+    KernelConfig best_cfg = saved;
     for (int li = 0; li < 3 && rc == SCROOGE_OK; ++li) {
         const int lanes = lanes_opts[ix][li];
         if (!lanes) continue;
         for (int rows : rows_opts) {
             for (int wpb : wpb_opts) {
                 c->kcfg[ix] = {lanes, rows, wpb};
-                // one untimed run, then `repeats` timed runs; keep the fastest
-                rc = scrooge_align_batch(c, texts, text_offsets, text_lengths, patterns, pattern_offsets,
-                                         pattern_lengths, n_pairs, W, O, k, fl, edit_counts, text_consumed, cigar,
-                                         cigar_capacity, cigar_offsets);
-                if (rc != SCROOGE_OK) break;
-                float tmin = -1.f;
-                for (int r = 0; r < repeats && rc == SCROOGE_OK; ++r) {
-                    cudaEventRecord(e0, c->stream);
-                    rc = scrooge_align_batch(c, texts, text_offsets, text_lengths, patterns, pattern_offsets,
-                                             pattern_lengths, n_pairs, W, O, k, fl, edit_counts, text_consumed,
-                                             cigar, cigar_capacity, cigar_offsets);
-                    cudaEventRecord(e1, c->stream);
-                    if (cudaEventSynchronize(e1) != cudaSuccess) rc = fail(c, SCROOGE_E_CUDA, "event sync failed");
-                    float ms = 0.f;
-                    cudaEventElapsedTime(&ms, e0, e1);
-                    if (tmin < 0.f || ms < tmin) tmin = ms;
-                }
-                if (rc != SCROOGE_OK) break;
-                if (results && nres < max_results) {
-                    int32_t *r = results + 5 * nres;
-                    r[0] = lanes;
-                    r[1] = rows;
-                    r[2] = wpb;
-                    r[3] = (int32_t)(tmin * 1000.f);
-                    r[4] = 1;
-                }
-                ++nres;
-                if (best < 0.f || tmin < best) {
-                    best = tmin;
+                float t;
+                if ((rc = time_it(repeats, t)) != SCROOGE_OK) break;
+                record(lanes, rows, wpb, t, 1);
+                if (best < 0.f || t < best) {
+                    best = t;
                     best_cfg = c->kcfg[ix];
                 }
             }
@@ -679,46 +708,8 @@ int scrooge_autotune(scrooge_ctx *c, const uint32_t *texts, const int64_t *text_
         }
     }
     c->kcfg[ix] = rc == SCROOGE_OK ? best_cfg : saved;
-    // learned launches on band-sized windows: which load classes go to the full-width kernel
-    if (rc == SCROOGE_OK && (flags & SCROOGE_LEARNED) && use_band(W, flags)) {
-        const int32_t saved_class = c->heavy_class;
-        const int classes[] = {16, 15, 14, 13, 12, 11, 10, 0};
-        float best_t = -1.f;
-        int best_class = saved_class;
-        for (int hc : classes) {
-            c->heavy_class = hc;
-            rc = scrooge_align_batch(c, texts, text_offsets, text_lengths, patterns, pattern_offsets,
-                                     pattern_lengths, n_pairs, W, O, k, fl, edit_counts, text_consumed, cigar,
-                                     cigar_capacity, cigar_offsets);
-            float tmin = -1.f;
-            for (int r = 0; r < repeats && rc == SCROOGE_OK; ++r) {
-                cudaEventRecord(e0, c->stream);
-                rc = scrooge_align_batch(c, texts, text_offsets, text_lengths, patterns, pattern_offsets,
-                                         pattern_lengths, n_pairs, W, O, k, fl, edit_counts, text_consumed, cigar,
-                                         cigar_capacity, cigar_offsets);
-                cudaEventRecord(e1, c->stream);
-                if (cudaEventSynchronize(e1) != cudaSuccess) rc = fail(c, SCROOGE_E_CUDA, "event sync failed");
-                float ms = 0.f;
-                cudaEventElapsedTime(&ms, e0, e1);
-                if (tmin < 0.f || ms < tmin) tmin = ms;
-            }
-            if (rc != SCROOGE_OK) break;
-            if (results && nres < max_results) {
-                int32_t *r = results + 5 * nres;
-                r[0] = 0;
-                r[1] = hc;
-                r[2] = 0;
-                r[3] = (int32_t)(tmin * 1000.f);
-                r[4] = 2;
-            }
-            ++nres;
-            if (best_t < 0.f || tmin < best_t) {
-                best_t = tmin;
-                best_class = hc;
-            }
-        }
-        c->heavy_class = rc == SCROOGE_OK ? best_class : saved_class;
-    }
+    if (rc == SCROOGE_OK && tune_classes) rc = sweep_classes();  // again, with the chosen settings
+    if (rc != SCROOGE_OK) c->heavy_class = saved_class;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (n_results) *n_results = std::min(nres, max_results);
