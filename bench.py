@@ -253,7 +253,11 @@ def main():
         table = sc.autotune_device(ctx, sdb, W, O, k, flags=flags | sc.SCROOGE_LEARNED, repeats=3)
         del sdb, sample
         tune_info = {"sample_pairs": n_pairs, "sample_seed": wl["seed"] + 7 + 1000 * rank, "configs_timed": len(table),
-                     "heavy_class": sc.scrooge_get_heavy_class(ctx), "seconds": time.perf_counter() - t0}
+                     "class_ms": [[r[1], r[3] / 1e3] for r in table if r[4] == 2],
+                     "best_settings_ms": sorted([[r[0], r[1], r[2], r[3] / 1e3] for r in table if r[4] == 1],
+                                                key=lambda r: r[3])[:3],
+                     "heavy_class": sc.scrooge_get_heavy_class(ctx), "long_class": sc.scrooge_get_long_class(ctx),
+                     "seconds": time.perf_counter() - t0}
     db = sc.DeviceBatch(pb)
 
     # untimed run with per-pair statistics: algorithmic DP cells of the method

@@ -170,14 +170,27 @@ int scrooge_get_kernel_config(const scrooge_ctx *ctx, int32_t words, int32_t *la
 
 /* Kernel per load bucket (no counterpart in the paper; never changes
  * results). With SCROOGE_LEARNED on windows the banded kernel serves, the
- * pairs the ordering puts in predicted load classes >= load_class (the 4-bit
- * class of the bucket key, 0..15) run on the full-width kernel and the rest on
- * the banded one, the two launches overlapping on two streams. 16 (the
+ * pairs whose predicted load class (see "learned pair ordering") is at least
+ * load_class come first in the order and run on the full-width kernel; the
+ * rest run on the banded one, and the two launches overlap on two streams. 16 (the
  * default) sends every pair to the banded kernel, 0 every pair to the
  * full-width one. scrooge_autotune with SCROOGE_LEARNED also picks this
  * class. */
 int scrooge_set_heavy_class(scrooge_ctx *ctx, int32_t load_class);
 int32_t scrooge_get_heavy_class(const scrooge_ctx *ctx);
+
+/* Long pairs (no counterpart in the paper; never changes results). The
+ * windows of a pair are sequential, so a batch can take no less time than
+ * its longest pair. With SCROOGE_LEARNED on windows the banded kernel
+ * serves, the pairs whose predicted work class (see "learned pair ordering")
+ * is at least work_class come first in the order. A first launch on a
+ * high-priority stream gives each of them a warp of its own (one pair per
+ * warp, three one-warp blocks per SM), so each of their windows costs only
+ * its own rows and traceback steps, not the worst of a warp's pairs.
+ * 16 (the default) turns this off; 13 selects pattern length x rows per
+ * window of at least 2^19. */
+int scrooge_set_long_class(scrooge_ctx *ctx, int32_t work_class);
+int32_t scrooge_get_long_class(const scrooge_ctx *ctx);
 
 /* Launch shape of the last scrooge_align_batch call on this context, for
  * reports: up to 12 int64 into shape[0..n): kernel (0 banded, else the words
@@ -219,10 +232,19 @@ int scrooge_set_order(scrooge_ctx *ctx, const int32_t *order, int32_t n_pairs);
 
 /* ------------------------------------------------- learned pair ordering
  * No counterpart in the paper: a small MLP predicts each pair's per-window
- * load from cheap features; SCROOGE_LEARNED launches hand pairs to the
- * persistent kernel heaviest-per-window first (bucketed by predicted load,
- * then by length class, longest first), so pairs sharing a warp do similar
- * early-termination work. The order never changes results.
+ * load from cheap features, and SCROOGE_LEARNED launches hand pairs to the
+ * persistent kernel in the order of an 8-bit bucket key, stable within a
+ * bucket. From the most significant bit down the key holds:
+ *   - the long pairs first (work class >= scrooge_set_long_class);
+ *   - then the heavy pairs (load class >= scrooge_set_heavy_class);
+ *   - then the largest predicted total work first (work class halved), so
+ *     that the longest pairs do not finish last;
+ *   - then the heaviest per-window load first (load class halved).
+ * Here rows is the predicted mean DP rows per window, the load class is
+ * floor(4 log2(rows + 1)) and the work class is
+ * floor(log2((m + 1)(rows + 1))) - 6, both clipped to 0..15. Pairs sharing
+ * a warp do similar early-termination work. The order never changes
+ * results.
  *
  * Features (float32, 6 per pair, row-major): log2(m+1), log2(n+1),
  * (n-m)/max(m,1), the fraction of sampled pattern 12-mers found in the text

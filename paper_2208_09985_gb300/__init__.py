@@ -95,6 +95,8 @@ def load():
                 "scrooge_last_launch_shape": ([P, P, i32], ctypes.c_int),
                 "scrooge_set_heavy_class": ([P, i32], ctypes.c_int),
                 "scrooge_get_heavy_class": ([P], i32),
+                "scrooge_set_long_class": ([P, i32], ctypes.c_int),
+                "scrooge_get_long_class": ([P], i32),
             }
             for name, (args, res) in sig.items():
                 f = getattr(lib, name)
@@ -262,6 +264,15 @@ def scrooge_set_heavy_class(ctx, load_class: int):
 
 def scrooge_get_heavy_class(ctx) -> int:
     return int(load().scrooge_get_heavy_class(ctx))
+
+
+def scrooge_set_long_class(ctx, work_class: int):
+    """Learned launches: pairs in work classes >= work_class get a warp each (16: off)."""
+    return _check(ctx, load().scrooge_set_long_class(ctx, int(work_class)))
+
+
+def scrooge_get_long_class(ctx) -> int:
+    return int(load().scrooge_get_long_class(ctx))
 
 
 def scrooge_last_kernel_count(ctx) -> int:

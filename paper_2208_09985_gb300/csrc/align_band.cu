@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(64, BandMinBlocks<G>::value) align_band_kernel
     };
 
     Slot s;
-    slot_init(s, gw * PPW + g);
+    slot_init(s, gw * PPW + g, p.slots_per_warp > 0 && g >= p.slots_per_warp);
     int64_t q_lo, q_hi;
     slot_range(p, q_lo, q_hi);
     CigarOut out;
@@ -347,9 +347,17 @@ cudaError_t launch_g(const AlignParams &p, int wpb, int blocks, size_t smem, cud
     return cudaGetLastError();
 }
 
+// The dynamic shared-memory limit of a kernel is only ever raised: one call may launch the same
+// instantiation with two shapes (the long-pair launch and the main one).
 template <int G>
 cudaError_t occupancy_g(int wpb, size_t smem, int *per_sm) {
-    cudaFuncSetAttribute(align_band_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, align_band_kernel<G>);
+    if (e != cudaSuccess) return e;
+    if ((size_t)a.maxDynamicSharedSizeBytes < smem &&
+        (e = cudaFuncSetAttribute(align_band_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+            cudaSuccess)
+        return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, align_band_kernel<G>, 32 * wpb, smem);
 }
 

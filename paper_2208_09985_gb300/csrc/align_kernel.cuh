@@ -158,12 +158,13 @@ struct Slot {
     long long t_start;
 };
 
-__device__ __forceinline__ void slot_init(Slot &s, int64_t first_static) {
+__device__ __forceinline__ void slot_init(Slot &s, int64_t first_static, bool idle) {
     s.pair = s.n = s.m = s.ti = s.pj = 0;
     s.tseq = s.pseq = nullptr;
     s.tblk = s.pblk = 0;
     s.next_static = first_static;
-    s.active = s.exhausted = s.failed = false;
+    s.active = s.failed = false;
+    s.exhausted = idle;  // a slot beyond slots_per_warp never takes a pair
     s.st_rows = s.st_cells = 0;
     s.st_windows = 0;
     s.t_start = 0;
@@ -175,13 +176,8 @@ __device__ __forceinline__ void slot_init(Slot &s, int64_t first_static) {
 // finished at fetch time.
 // Slots [lo, hi) of the order this launch serves (persistent launches may split them).
 __device__ __forceinline__ void slot_range(const AlignParams &p, int64_t &lo, int64_t &hi) {
-    lo = 0;
-    hi = p.n_pairs;
-    if (p.queue && p.split_at) {
-        const int64_t sp = *p.split_at;
-        if (p.split_side) lo = sp;
-        else hi = sp;
-    }
+    lo = (p.queue && p.range_lo) ? *p.range_lo : 0;
+    hi = (p.queue && p.range_hi) ? *p.range_hi : p.n_pairs;
 }
 
 template <int G>
@@ -312,7 +308,7 @@ __global__ void __launch_bounds__(64, 6) align_kernel(const AlignParams p) {
     int64_t next_static = gw * PPW + g;
     int64_t q_lo, q_hi;
     slot_range(p, q_lo, q_hi);
-    bool exhausted = false, active = false;
+    bool exhausted = p.slots_per_warp > 0 && g >= p.slots_per_warp, active = false;
     int pair = 0, n = 0, m = 0;
     const uint2 *tseq = nullptr, *pseq = nullptr;
     int64_t tblk = 0, pblk = 0;

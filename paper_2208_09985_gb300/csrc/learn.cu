@@ -300,15 +300,25 @@ __global__ void adam_kernel(float *model, const float *grad, float *m1, float *m
 // Bucket key of each pair from the predicted per-window load (log1p of the
 // mean DP rows per window) and the pattern length: ascending keys put heavy
 // windows first and, inside a load class, long pairs first.
-__global__ void bucket_key_kernel(const float *pred, const int32_t *pat_len, int32_t n, uint8_t *key) {
+// 8-bit bucket key, sorted ascending:
+//   bit 7     0 for the long pairs (work class >= long_class): they go first;
+//   bit 6     0 for the heavy pairs (load class >= heavy_class);
+//   bits 3-5  7 - work class / 2: predicted total work, pattern length x rows per window, largest first;
+//   bits 0-2  7 - load class / 2: heavier per-window load first within a work class.
+// rows = predicted mean DP rows per window, load class = floor(4 log2(rows + 1)) in 0..15,
+// work class = floor(log2((m + 1)(rows + 1))) - 6 in 0..15.
+__global__ void bucket_key_kernel(const float *pred, const int32_t *pat_len, int32_t n, int heavy_class,
+                                  int long_class, uint8_t *key) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
     const float rows = fmaxf(expm1f(pred[p]), 0.f);
     int load = (int)floorf(log2f(rows + 1.f) * 4.f);
     load = max(0, min(15, load));
-    int len = (int)floorf(log2f((float)pat_len[p] + 1.f));
-    len = max(0, min(15, len));
-    key[p] = (uint8_t)(((15 - load) << 4) | (15 - len));
+    int work = (int)floorf(log2f(((float)pat_len[p] + 1.f) * (rows + 1.f))) - 6;
+    work = max(0, min(15, work));
+    const int shortp = work >= long_class ? 0 : 1;
+    const int light = load >= heavy_class ? 0 : 1;
+    key[p] = (uint8_t)((shortp << 7) | (light << 6) | ((7 - (work >> 1)) << 3) | (7 - (load >> 1)));
 }
 
 constexpr int kSortTile = 2048;  // elements per block of the counting sort
@@ -404,14 +414,14 @@ const int64_t *learned_bucket_start(const int64_t *tmp, int32_t n, int key) {
     return tmp + 256 * nb + (int64_t)key * nb;  // bucket-major exclusive offsets, tile 0 of the bucket
 }
 
-cudaError_t launch_learned_order(const float *pred, const int32_t *pat_len, int32_t n, uint8_t *key, int32_t *order,
-                                 int64_t *tmp, cudaStream_t s) {
+cudaError_t launch_learned_order(const float *pred, const int32_t *pat_len, int32_t n, int heavy_class, int long_class,
+                                 uint8_t *key, int32_t *order, int64_t *tmp, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     const int nb = (int)(((int64_t)n + kSortTile - 1) / kSortTile);
     int32_t *counts = reinterpret_cast<int32_t *>(tmp);       // 256 * nb int32
     int64_t *offsets = tmp + 256 * (int64_t)nb;               // 256 * nb + 1 int64
     int64_t *scan_tmp = offsets + 256 * (int64_t)nb + 8;
-    bucket_key_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pred, pat_len, n, key);
+    bucket_key_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pred, pat_len, n, heavy_class, long_class, key);
     key_hist_kernel<<<nb, 256, 0, s>>>(key, n, counts, nb);
     cudaError_t e = exclusive_scan(counts, 0, 256 * (int64_t)nb, offsets, scan_tmp, s);
     if (e != cudaSuccess) return e;

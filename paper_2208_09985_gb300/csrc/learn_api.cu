@@ -55,7 +55,8 @@ int learned_order(scrooge_ctx *c, const uint32_t *texts, const int64_t *text_off
                              c->sm_count, c->stream)) != cudaSuccess ||
         (e = launch_mlp_forward((const float *)c->model.p, (const float *)c->l_feat.p, n, (float *)c->l_pred.p,
                                 c->stream)) != cudaSuccess ||
-        (e = launch_learned_order((const float *)c->l_pred.p, pat_len, n, (uint8_t *)c->l_key.p,
+        (e = launch_learned_order((const float *)c->l_pred.p, pat_len, n, c->heavy_class, c->long_class,
+                                  (uint8_t *)c->l_key.p,
                                   (int32_t *)c->l_order.p, (int64_t *)c->l_tmp.p, c->stream)) != cudaSuccess)
         return cuda_fail(c, e, "learned ordering");
     return SCROOGE_OK;

@@ -65,11 +65,14 @@ int scrooge_destroy(scrooge_ctx *c) {
                      &c->in_poff,   &c->in_plen, &c->out_ec,  &c->out_tc,   &c->out_cig,  &c->out_off,
                      &c->scr_runs,  &c->scr_off, &c->scr_len, &c->scr_cap,  &c->scan_tmp, &c->queue,
                      &c->model,     &c->grad,    &c->adam_m1, &c->adam_m2,  &c->loss,     &c->l_feat,
-                     &c->l_pred,    &c->l_key,   &c->l_order, &c->l_tmp,    &c->t_rows,   &c->fallback, &c->spill2};
+                     &c->l_pred,    &c->l_key,   &c->l_order, &c->l_tmp,    &c->t_rows,   &c->fallback, &c->spill2,
+                     &c->spill3,    &c->fallback2};
     if (c->graph) cudaGraphExecDestroy(c->graph);
     if (c->stream2) cudaStreamDestroy(c->stream2);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->ev_join3) cudaEventDestroy(c->ev_join3);
+    if (c->stream3) cudaStreamDestroy(c->stream3);
     for (DevBuf *b : all) release(*b);
     delete c;
     return SCROOGE_OK;
@@ -185,6 +188,14 @@ int scrooge_set_heavy_class(scrooge_ctx *c, int32_t load_class) {
 
 int32_t scrooge_get_heavy_class(const scrooge_ctx *c) { return c ? c->heavy_class : -1; }
 
+int scrooge_set_long_class(scrooge_ctx *c, int32_t work_class) {
+    if (!c || work_class < 0 || work_class > 16) return SCROOGE_E_INVAL;
+    c->long_class = work_class;
+    return SCROOGE_OK;
+}
+
+int32_t scrooge_get_long_class(const scrooge_ctx *c) { return c ? c->long_class : -1; }
+
 int scrooge_last_launch_shape(const scrooge_ctx *c, int64_t *shape, int32_t n) {
     if (!c || !shape || n < 1) return SCROOGE_E_INVAL;
     memcpy(shape, c->last_shape, sizeof(int64_t) * (size_t)std::min(n, 12));
@@ -232,7 +243,9 @@ struct LaunchPlan {
 // Shape of the kernel a call with these flags uses (banded or full width), sized for the device
 // and the context's kernel settings; sizes the row scratch in `spill` (and the banded kernel's
 // fallback area). Queue, order and status are set by the caller.
-int make_plan(scrooge_ctx *c, const AlignParams &base, bool band, uint32_t flags, DevBuf &spill, LaunchPlan &out) {
+// slots > 0: a launch with that many pair slots per warp, one warp per block and three blocks per SM.
+int make_plan(scrooge_ctx *c, const AlignParams &base, bool band, uint32_t flags, DevBuf &spill, DevBuf &fallback,
+              int slots, LaunchPlan &out) {
     const int W = base.W, O = base.O, k = base.k;
     const int words = words_for(W);
     const bool sene = !(flags & SCROOGE_NO_SENE);
@@ -260,7 +273,7 @@ int make_plan(scrooge_ctx *c, const AlignParams &base, bool band, uint32_t flags
     const int rows_needed = band ? std::min(k, kBandRows - 1) + 1 : k + 1;  // rows the kernel may store
     int rcap = std::min(kc.rows, rows_needed);
     const int stage = stage_words_per_warp(words, PPW);
-    int wpb = kc.wpb;
+    int wpb = slots > 0 ? 1 : kc.wpb;
     // keep the block's shared memory within the opt-in limit
     while (rcap > 1 && (size_t)wpb * (table_words_per_warp(rcap, ts, PPW, chunk) + stage) * 4 > c->smem_optin) --rcap;
     while (wpb > 1 && (size_t)wpb * (table_words_per_warp(rcap, ts, PPW, chunk) + stage) * 4 > c->smem_optin) --wpb;
@@ -277,7 +290,9 @@ int make_plan(scrooge_ctx *c, const AlignParams &base, bool band, uint32_t flags
     if (per_sm < 1) return fail(c, SCROOGE_E_INVAL, "kernel config does not fit on an SM (smem %zu B)", smem);
     const int64_t groups = ((int64_t)p.n_pairs + PPW - 1) / PPW;
     const int64_t want_blocks = (groups + wpb - 1) / wpb;
-    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(want_blocks, (int64_t)per_sm * c->sm_count));
+    int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(want_blocks, (int64_t)per_sm * c->sm_count));
+    if (slots > 0) blocks = (int)std::min<int64_t>((int64_t)per_sm * c->sm_count, 3LL * c->sm_count);
+    p.slots_per_warp = slots;
     const int spill_rows = std::max(0, rows_needed - rcap);
     p.spill_words_per_pair = table_words_per_warp(spill_rows, ts, PPW, chunk);  // per warp
     const size_t spill_bytes = (size_t)blocks * wpb * (size_t)std::max<int64_t>(p.spill_words_per_pair, 4) * 4;
@@ -289,10 +304,10 @@ int make_plan(scrooge_ctx *c, const AlignParams &base, bool band, uint32_t flags
     if (band) {
         p.fb_words_per_warp = band_fallback_words(k, ts.ncol, PPW);
         if (p.fb_words_per_warp > 0) {
-            if ((rc = ensure(c, c->fallback, (size_t)blocks * wpb * (size_t)p.fb_words_per_warp * 4,
+            if ((rc = ensure(c, fallback, (size_t)blocks * wpb * (size_t)p.fb_words_per_warp * 4,
                              "full-width fallback scratch")))
                 return rc;
-            p.fb = (uint32_t *)c->fallback.p;
+            p.fb = (uint32_t *)fallback.p;
         }
     }
     out.band = band;
@@ -442,16 +457,24 @@ int scrooge_align_batch(scrooge_ctx *c, const uint32_t *texts, const int64_t *te
     // kernel shape(s): the kernel the call uses, and with SCROOGE_LEARNED on band-sized windows
     // the full-width kernel for the pairs the ordering puts in the heavy load classes
     const bool band = use_band(W, flags);
-    const bool split = band && (flags & SCROOGE_LEARNED) && c->heavy_class < 16;
-    LaunchPlan plan, heavy;
-    if ((rc = make_plan(c, p, band, flags, c->spill, plan))) return rc;
-    if (split && (rc = make_plan(c, p, false, flags | SCROOGE_NO_BAND, c->spill2, heavy))) return rc;
+    // Learned launches on band-sized windows split the order (see the bucket key in learn.cu):
+    //   [0, start of key 128)    long pairs, one pair per warp, banded kernel, high-priority stream;
+    //   [.., start of key 192)   heavy pairs, full-width kernel, the context stream;
+    //   [.., n_pairs)            the rest, banded kernel, low-priority stream.
+    const bool learned_split = band && (flags & SCROOGE_LEARNED) && (c->heavy_class < 16 || c->long_class < 16);
+    const bool use_heavy = learned_split && c->heavy_class < 16;
+    const bool use_long = learned_split && c->long_class < 16;
+    LaunchPlan plan, heavy, lng;
+    if ((rc = make_plan(c, p, band, flags, c->spill, c->fallback, 0, plan))) return rc;
+    if (use_heavy && (rc = make_plan(c, p, false, flags | SCROOGE_NO_BAND, c->spill2, c->fallback, 0, heavy)))
+        return rc;
+    if (use_long && (rc = make_plan(c, p, true, flags, c->spill3, c->fallback2, 1, lng))) return rc;
     if ((rc = ensure(c, c->status, 64, "status"))) return rc;
-    if ((flags & SCROOGE_PERSISTENT) && (rc = ensure(c, c->queue, 128, "work queues"))) return rc;
-    for (LaunchPlan *lp : {&plan, &heavy}) {
+    if ((flags & SCROOGE_PERSISTENT) && (rc = ensure(c, c->queue, 256, "work queues"))) return rc;
+    for (LaunchPlan *lp : {&plan, &heavy, &lng}) {
         lp->p.status = (int32_t *)c->status.p;
         if (flags & SCROOGE_PERSISTENT) {
-            lp->p.queue = (int32_t *)c->queue.p + (lp == &heavy ? 16 : 0);
+            lp->p.queue = (int32_t *)c->queue.p + (lp == &heavy ? 16 : (lp == &lng ? 32 : 0));
             lp->p.order = (c->order && c->order_n == n_pairs) ? c->order : nullptr;
         }
     }
@@ -463,22 +486,26 @@ int scrooge_align_batch(scrooge_ctx *c, const uint32_t *texts, const int64_t *te
             (rc = ensure(c, c->l_order, npp * 4, "pair order")) ||
             (rc = ensure(c, c->l_tmp, (size_t)sort_temp_words(n_pairs) * 8, "sort scratch")))
             return rc;
-        plan.p.order = heavy.p.order = (const int32_t *)c->l_order.p;
+        plan.p.order = heavy.p.order = lng.p.order = (const int32_t *)c->l_order.p;
     }
-    if (split) {
-        // the ordering puts load classes >= heavy_class first; they end where bucket key (16 - class) << 4 starts
-        const int64_t *at = learned_bucket_start((int64_t *)c->l_tmp.p, n_pairs, (16 - c->heavy_class) << 4);
-        heavy.p.split_at = plan.p.split_at = at;
-        heavy.p.split_side = 0;
-        plan.p.split_side = 1;
-        // the banded kernel's stream gets the lowest priority, so the block scheduler dispatches the heavy
-        // kernel's blocks first whatever order the two launches (or graph nodes) reach it in
+    if (learned_split) {
+        const int64_t *k128 = learned_bucket_start((int64_t *)c->l_tmp.p, n_pairs, 128);
+        const int64_t *k192 = learned_bucket_start((int64_t *)c->l_tmp.p, n_pairs, 192);
+        lng.p.range_hi = k128;
+        heavy.p.range_lo = k128;
+        heavy.p.range_hi = k192;
+        plan.p.range_lo = k192;
+        // stream priorities order the block scheduler: long pairs first, then the heavy kernel, then the
+        // banded one, whatever order the launches (or graph nodes) reach it in
         int prio_least = 0, prio_greatest = 0;
         cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
         if (!c->stream2 && ((e = cudaStreamCreateWithPriority(&c->stream2, cudaStreamNonBlocking, prio_least)) !=
                                 cudaSuccess ||
+                            (e = cudaStreamCreateWithPriority(&c->stream3, cudaStreamNonBlocking, prio_greatest)) !=
+                                cudaSuccess ||
                             (e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming)) != cudaSuccess ||
-                            (e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming)) != cudaSuccess))
+                            (e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming)) != cudaSuccess ||
+                            (e = cudaEventCreateWithFlags(&c->ev_join3, cudaEventDisableTiming)) != cudaSuccess))
             return cuda_fail(c, e, "second stream");
     }
     {
@@ -490,12 +517,12 @@ int scrooge_align_batch(scrooge_ctx *c, const uint32_t *texts, const int64_t *te
     }
     int64_t *dense_off = dev ? cigar_offsets : (int64_t *)c->out_off.p;
     c->last_kernels = 1 + scan_kernel_count(n_pairs) + 1;  // alignment, CIGAR offsets, gather
-    if (split) c->last_kernels += 1;
+    if (learned_split) c->last_kernels += 2;
     if (flags & SCROOGE_LEARNED) c->last_kernels += learned_kernel_count(n_pairs);
     // everything from the status reset to the CIGAR offsets, on `st`
     auto enqueue = [&]() -> int {
         if ((e = cudaMemsetAsync(plan.p.status, 0, 4, st)) != cudaSuccess) return cuda_fail(c, e, "status reset");
-        if (plan.p.queue && (e = cudaMemsetAsync(c->queue.p, 0, 128, st)) != cudaSuccess)
+        if (plan.p.queue && (e = cudaMemsetAsync(c->queue.p, 0, 256, st)) != cudaSuccess)
             return cuda_fail(c, e, "queue reset");
         if (flags & SCROOGE_LEARNED) {
             const int lrc = learned_order(c, p.texts, p.text_off, p.text_len, p.patterns, p.pat_off, p.pat_len,
@@ -504,16 +531,21 @@ int scrooge_align_batch(scrooge_ctx *c, const uint32_t *texts, const int64_t *te
         }
         const bool timed = c->t_start && c->t_stop && !(flags & SCROOGE_GRAPH);
         if (timed) cudaEventRecord(c->t_start, st);
-        if (split) {
-            // heavy pairs on the full-width kernel first; the banded kernel on a second stream takes
-            // over the SMs as the heavy blocks retire
+        if (learned_split) {
+            // three launches over disjoint ranges of the order; an empty range costs one short launch
             if ((e = cudaEventRecord(c->ev_fork, st)) != cudaSuccess ||
-                (e = cudaStreamWaitEvent(c->stream2, c->ev_fork, 0)) != cudaSuccess)
+                (e = cudaStreamWaitEvent(c->stream2, c->ev_fork, 0)) != cudaSuccess ||
+                (e = cudaStreamWaitEvent(c->stream3, c->ev_fork, 0)) != cudaSuccess)
                 return cuda_fail(c, e, "stream fork");
-            if ((e = launch_plan(heavy, st)) != cudaSuccess) return cuda_fail(c, e, "alignment kernel launch");
+            if (use_long && (e = launch_plan(lng, c->stream3)) != cudaSuccess)
+                return cuda_fail(c, e, "alignment kernel launch");
+            if (use_heavy && (e = launch_plan(heavy, st)) != cudaSuccess)
+                return cuda_fail(c, e, "alignment kernel launch");
             if ((e = launch_plan(plan, c->stream2)) != cudaSuccess) return cuda_fail(c, e, "alignment kernel launch");
             if ((e = cudaEventRecord(c->ev_join, c->stream2)) != cudaSuccess ||
-                (e = cudaStreamWaitEvent(st, c->ev_join, 0)) != cudaSuccess)
+                (e = cudaEventRecord(c->ev_join3, c->stream3)) != cudaSuccess ||
+                (e = cudaStreamWaitEvent(st, c->ev_join, 0)) != cudaSuccess ||
+                (e = cudaStreamWaitEvent(st, c->ev_join3, 0)) != cudaSuccess)
                 return cuda_fail(c, e, "stream join");
         } else if ((e = launch_plan(plan, st)) != cudaSuccess) {
             return cuda_fail(c, e, "alignment kernel launch");
@@ -544,10 +576,12 @@ int scrooge_align_batch(scrooge_ctx *c, const uint32_t *texts, const int64_t *te
             (unsigned long long)(uintptr_t)c->st_rows, (unsigned long long)(uintptr_t)c->st_cells,
             (unsigned long long)(uintptr_t)c->st_windows, (unsigned long long)(uintptr_t)plan.p.fb,
             (unsigned long long)band,
-            split ? (((unsigned long long)heavy.G << 48) | ((unsigned long long)heavy.p.rcap << 32) |
-                     ((unsigned long long)heavy.wpb << 24) | (unsigned long long)heavy.blocks)
-                  : 0ull,
-            split ? (((unsigned long long)(uintptr_t)heavy.p.spill) ^ ((unsigned long long)c->heavy_class << 56)) : 0ull};
+            use_heavy ? (((unsigned long long)heavy.G << 48) | ((unsigned long long)heavy.p.rcap << 32) |
+                         ((unsigned long long)heavy.wpb << 24) | (unsigned long long)heavy.blocks)
+                      : 0ull,
+            learned_split ? (((unsigned long long)(uintptr_t)heavy.p.spill) ^ ((unsigned long long)c->heavy_class << 56) ^
+                             ((unsigned long long)c->long_class << 48) ^ ((unsigned long long)(uintptr_t)lng.p.spill))
+                          : 0ull};
         if (!c->graph || memcmp(key, c->graph_key, sizeof key) != 0) {
             if (c->graph) {
                 cudaGraphExecDestroy(c->graph);

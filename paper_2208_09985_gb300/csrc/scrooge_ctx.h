@@ -33,12 +33,13 @@ struct scrooge_ctx {
     // full-width kernels of 1, 2, 4 words, then the banded kernel (autotuned on GB300)
     scrooge::KernelConfig kcfg[4] = {{2, 8, 2}, {4, 4, 2}, {8, 8, 2}, {4, 8, 2}};
     int fail_allocs = 0;  // testing hook: fail the next N device allocations
-    scrooge::DevBuf spill, status, fallback, spill2;
-    // pairs the learned ordering puts in load classes >= heavy_class run on the full-width kernel
-    // (16: none); the banded kernel then runs the rest on stream2
-    int32_t heavy_class = 16;
-    cudaStream_t stream2 = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    scrooge::DevBuf spill, status, fallback, spill2, spill3, fallback2;
+    // learned launches: pairs in load classes >= heavy_class run on the full-width kernel, pairs in
+    // work classes >= long_class one per warp on stream3 (16: none); the banded kernel runs the rest
+    // on stream2
+    int32_t heavy_class = 16, long_class = 16;
+    cudaStream_t stream2 = nullptr, stream3 = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join3 = nullptr;
     scrooge::DevBuf in_text, in_pat, in_toff, in_tlen, in_poff, in_plen;
     scrooge::DevBuf out_ec, out_tc, out_cig, out_off;
     scrooge::DevBuf scr_runs, scr_off, scr_len, scr_cap, scan_tmp;

@@ -41,8 +41,9 @@ struct AlignParams {
     int32_t table_words_per_warp;
     const int32_t *order;   // optional pair order (slot -> pair id)
     int32_t *queue;         // persistent mode: next slot to hand out (nullptr: static)
-    const int64_t *split_at;  // persistent mode: slots [0, *split_at) or [*split_at, n_pairs) only (nullptr: all)
-    int32_t split_side;       // 0: the slots below *split_at, 1: the slots from it
+    const int64_t *range_lo;  // persistent mode: only slots [*range_lo, *range_hi) of the order
+    const int64_t *range_hi;  // (nullptr: 0 and n_pairs)
+    int32_t slots_per_warp;   // pair slots of a warp that take pairs (0: all 32/G)
     int32_t *status;        // bit 0: traceback found no edge (impossible by Theorem 1)
     int32_t *st_windows;
     int64_t *st_rows;
@@ -152,7 +153,7 @@ int learned_kernel_count(int32_t n);
 // Device address of the first position of bucket `key` in the order that launch_learned_order
 // wrote with scratch `tmp` (the number of pairs with a smaller key).
 const int64_t *learned_bucket_start(const int64_t *tmp, int32_t n, int key);
-cudaError_t launch_learned_order(const float *pred, const int32_t *pat_len, int32_t n, uint8_t *key, int32_t *order,
-                                 int64_t *tmp, cudaStream_t s);
+cudaError_t launch_learned_order(const float *pred, const int32_t *pat_len, int32_t n, int heavy_class, int long_class,
+                                 uint8_t *key, int32_t *order, int64_t *tmp, cudaStream_t s);
 
 }  // namespace scrooge
