@@ -239,7 +239,9 @@ int scrooge_set_order(scrooge_ctx *ctx, const int32_t *order, int32_t n_pairs);
  *   - then the heavy pairs (load class >= scrooge_set_heavy_class);
  *   - then the largest predicted total work first (work class halved), so
  *     that the longest pairs do not finish last;
- *   - then the heaviest per-window load first (load class halved).
+ *   - then the lightest per-window load first (load class halved): at
+ *     equal work the lighter pair has more windows, and this measured
+ *     faster than heavier-first on long and on uneven reads.
  * Here rows is the predicted mean DP rows per window, the load class is
  * floor(4 log2(rows + 1)) and the work class is
  * floor(log2((m + 1)(rows + 1))) - 6, both clipped to 0..15. Pairs sharing

@@ -304,7 +304,8 @@ __global__ void adam_kernel(float *model, const float *grad, float *m1, float *m
 //   bit 7     0 for the long pairs (work class >= long_class): they go first;
 //   bit 6     0 for the heavy pairs (load class >= heavy_class);
 //   bits 3-5  7 - work class / 2: predicted total work, pattern length x rows per window, largest first;
-//   bits 0-2  7 - load class / 2: heavier per-window load first within a work class.
+//   bits 0-2  load class / 2: lighter per-window load (hence more windows) first within a work class,
+//             which measured faster than heavier-first on both the long and the uneven reads.
 // rows = predicted mean DP rows per window, load class = floor(4 log2(rows + 1)) in 0..15,
 // work class = floor(log2((m + 1)(rows + 1))) - 6 in 0..15.
 __global__ void bucket_key_kernel(const float *pred, const int32_t *pat_len, int32_t n, int heavy_class,
@@ -318,7 +319,7 @@ __global__ void bucket_key_kernel(const float *pred, const int32_t *pat_len, int
     work = max(0, min(15, work));
     const int shortp = work >= long_class ? 0 : 1;
     const int light = load >= heavy_class ? 0 : 1;
-    key[p] = (uint8_t)((shortp << 7) | (light << 6) | ((7 - (work >> 1)) << 3) | (7 - (load >> 1)));
+    key[p] = (uint8_t)((shortp << 7) | (light << 6) | ((7 - (work >> 1)) << 3) | (load >> 1));
 }
 
 constexpr int kSortTile = 2048;  // elements per block of the counting sort

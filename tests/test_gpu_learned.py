@@ -258,7 +258,7 @@ def test_learned_order_is_stable_bucket_sort(ctx):
     heavy = load >= sc.scrooge_get_heavy_class(h)
     longp = work >= sc.scrooge_get_long_class(h)
     key = (np.where(longp, 0, 128) | np.where(heavy, 0, 64) | ((7 - (work >> 1)) << 3) |
-           (7 - (load >> 1))).astype(np.int64)
+           (load >> 1)).astype(np.int64)
     # pairs whose class values sit within rounding of an integer may land in either bucket:
     # check the order on the others (a subsequence of a sorted, stable order is sorted and stable)
     # (an exact integer, e.g. log2(1) for rows = 0, is not ambiguous)
