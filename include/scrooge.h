@@ -69,6 +69,11 @@ typedef struct scrooge_ctx scrooge_ctx; /* opaque, owned by the library */
  * with SENE and ET use the banded kernel unless this flag asks for the
  * full-width one (see "kernel settings"). */
 #define SCROOGE_NO_BAND (1u << 8)
+/* Implementation choice, never a change of results: persistent launches of
+ * the banded kernel run as blocks of four DC warps and one traceback warp,
+ * which hand windows over through shared-memory barriers (4 lanes per pair,
+ * the banded kernel settings' shared-memory rows). */
+#define SCROOGE_WARP_SPECIALIZED (1u << 9)
 
 /* CIGAR run encoding: (length << 4) | op, op in SAM codes. */
 #define SCROOGE_OP_I 1  /* base only in the pattern (read): insertion */

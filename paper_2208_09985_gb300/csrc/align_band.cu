@@ -116,14 +116,226 @@ __device__ __noinline__ void full_width_dc(const uint2 *pseq, int64_t pblk, int 
     }
 }
 
+// One window of one pair slot of a banded launch, as the DC and traceback routines see it.
+struct BandWindow {
+    const uint2 *tseq, *pseq;
+    int64_t tblk, pblk;  // 0 for an idle slot
+    int ti, pj, nw, mw;
+    bool active;
+};
+
+// GenASM-DC of one window for the 32/G pairs of a warp (all 32 lanes take part). Band rows go to
+// `tab` (rows < rcap, shared memory) and `spill` (deeper rows); the traceback lane of each pair
+// stages its 64 bases of text and pattern at `stage` (12 words per pair); windows beyond the band
+// are recomputed at full width into `fb`. On the traceback lane, d_opt gets the window's edit
+// distance (-1: none <= k) and full whether the full-width rows hold it.
 template <int G>
-__global__ void __launch_bounds__(64, BandMinBlocks<G>::value) align_band_kernel(const AlignParams p) {
+__device__ __forceinline__ void band_window_dc(const AlignParams &p, const BandWindow &bw, int l, int g, int tbl,
+                                               uint32_t tbl_all, uint32_t *tab, uint32_t *spill, uint32_t *fb,
+                                               uint32_t *stage, int &d_opt_out, bool &full_out) {
     constexpr int WMAX = 64;
     constexpr int C = WMAX / G;
     constexpr int PPW = 32 / G;
     constexpr int COLW = PPW;  // words between two columns of one stored band row
     constexpr int B0 = kBandDiag;
-    static_assert(C * G == WMAX && C <= 32 && 32 % G == 0, "unsupported shape");
+    const int k = p.k, ncolp = p.ncol, rcap = p.rcap, rstride = p.rstride;
+    const int dmax = min(k, kBandRows - 1);  // deepest row the band computes
+    const int colbase = (G - 1 - l) * C;
+    const bool lane_stores = colbase < ncolp;
+    const bool active = bw.active;
+    const int nw = bw.nw, mw = bw.mw;
+    auto band_row = [&](int row) -> uint32_t * {
+        return row < rcap ? tab + row * rstride + g : spill + (row - rcap) * rstride + g;
+    };
+
+    // ---- window set-up: band pattern masks and row-0 masks of this lane's columns
+    uint32_t XA[C];   // X of the next row (row 0: bits with j >= m_w cleared)
+    uint32_t PMC[C];  // PMrel[text[i]]
+    {
+        // pattern planes from pj + colbase - 16: column colbase + c starts c + 1 bits in
+        uint32_t Pa0, Pa1, Pb0, Pb1, T0, T1;
+        load32(bw.pseq, bw.pblk, (int64_t)bw.pj + colbase - 16, Pa0, Pa1);
+        load32(bw.pseq, bw.pblk, (int64_t)bw.pj + colbase + 16, Pb0, Pb1);
+        load32(bw.tseq, bw.tblk, (int64_t)bw.ti + colbase, T0, T1);
+        const int real_cols = nw - colbase;
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+            const uint32_t m0 = 0u - ((T0 >> (31 - c)) & 1u);
+            const uint32_t m1 = 0u - ((T1 >> (31 - c)) & 1u);
+            const uint32_t w0 = __funnelshift_lc(Pb0, Pa0, c + 1);
+            const uint32_t w1 = __funnelshift_lc(Pb1, Pa1, c + 1);
+            PMC[c] = c < real_cols ? ((w0 ^ m0) | (w1 ^ m1)) : kFull;
+            XA[c] = prefix_mask(mw - (colbase + c) + B0);
+        }
+        if (active && l == G - 1) {
+#pragma unroll
+            for (int w = 0; w <= 2; ++w) {
+                uint32_t a, b;
+                load32(bw.tseq, bw.tblk, (int64_t)bw.ti + 32 * w, a, b);
+                stage[w] = a;
+                stage[3 + w] = b;
+                load32(bw.pseq, bw.pblk, (int64_t)bw.pj + 32 * w, a, b);
+                stage[6 + w] = a;
+                stage[9 + w] = b;
+            }
+        }
+    }
+
+    // ---- GenASM-DC in the band, rows in a pipeline over the lanes of each pair
+    uint32_t done_mask = __ballot_sync(kFull, l == G - 1 && !active);
+    int d_opt = -1;
+    uint32_t bottom = 0u;
+    for (int st = 0; done_mask != tbl_all; ++st) {
+        const int d = st - l;
+        const bool dc_done = (done_mask >> tbl) & 1u;
+        const uint32_t v = __shfl_up_sync(kFull, bottom, 1);
+        // lane 0 starts from column 64, whose bits j < m_w - d are 1
+        uint32_t pR = (l == 0) ? prefix_mask(mw - d - WMAX + B0) : v;
+        bool found = false;
+        if (!dc_done && d >= 0 && d <= dmax) {
+            uint32_t *rowp = band_row(d) + colbase * COLW;
+#pragma unroll
+            for (int c = C - 1; c >= 0; --c) {
+                const uint32_t R = XA[c] & (pR | PMC[c]);
+                if (lane_stores) rowp[c * COLW] = R;
+                // next row: S = V[i+1][d], D = V[i+1][d] >> 1, I = V[i][d] << 1 (1s shifted in)
+                XA[c] = pR & __funnelshift_r(pR, kFull, 1) & __funnelshift_l(kFull, R, 1);
+                pR = R;
+            }
+            bottom = pR;
+            found = (l == G - 1) && (((pR >> (31 - B0)) & 1u) == 0u);
+        }
+        const uint32_t fmask = __ballot_sync(kFull, found);
+        const int dl = st - (G - 1);  // row finished by the traceback lane
+        if (!dc_done && ((fmask >> tbl) & 1u) && d_opt < 0) d_opt = dl;
+        done_mask |= fmask;
+        if (dl >= dmax) done_mask = tbl_all;
+    }
+
+    // ---- windows beyond the band: full-width DC (Algorithm 1 on two words)
+    const uint32_t full_mask = __ballot_sync(kFull, l == G - 1 && active && d_opt < 0 && k >= kBandRows);
+    const bool full = (full_mask >> tbl) & 1u;
+    if (full_mask)
+        full_width_dc<G>(bw.pseq, bw.pblk, bw.pj, bw.tseq, bw.tblk, bw.ti, nw, mw, k, l, tbl, tbl_all, full_mask,
+                         lane_stores, fb + ((int64_t)colbase * PPW + g) * 2, ncolp * PPW * 2, d_opt);
+    d_opt_out = d_opt;
+    full_out = full;
+}
+
+// GenASM-TB of one window, one lane per pair; every lane of `mask` calls it (the loop is warp
+// uniform over those lanes). The pair's band rows are column-interleaved with the other pairs of
+// a warp of G-lane pairs (pair index g) in `tab` / `spill`, its full-width rows in `fb`, its
+// staged bases at `stage`. Emits the window's CIGAR runs, counts the window in the statistics and
+// advances the cursors by what it consumed.
+template <int G>
+__device__ __forceinline__ void band_window_tb(const AlignParams &p, uint32_t mask, bool active, int d_opt,
+                                               bool full, int nw, int mw, const uint32_t *stage,
+                                               const uint32_t *tab, const uint32_t *spill, const uint32_t *fb,
+                                               int g, CigarOut &out, int &ti, int &pj, bool &failed,
+                                               int64_t &st_rows, int64_t &st_cells, int32_t &st_windows) {
+    constexpr int PPW = 32 / G;
+    constexpr int COLW = PPW;
+    constexpr int B0 = kBandDiag;
+    const int L = p.W - p.O, rcap = p.rcap, rstride = p.rstride;
+    const int fb_row = p.ncol * PPW * 2;
+    auto band_row = [&](int row) -> const uint32_t * {
+        return row < rcap ? tab + row * rstride + g : spill + (row - rcap) * rstride + g;
+    };
+    const bool tb_live = active && d_opt >= 0;
+    if (active) st_windows += 1;
+    if (active && d_opt < 0) failed = true;
+    if (tb_live) {
+        st_rows += d_opt + 1;
+        st_cells += (int64_t)(d_opt + 1) * nw;
+    }
+    const uint64_t qT0 = ((uint64_t)stage[0] << 32) | stage[1];
+    const uint64_t qT1 = ((uint64_t)stage[3] << 32) | stage[4];
+    const uint64_t qP0 = ((uint64_t)stage[6] << 32) | stage[7];
+    const uint64_t qP1 = ((uint64_t)stage[9] << 32) | stage[10];
+    int i = 0, j = 0, d = d_opt;
+    bool going = tb_live && (j < mw && i < L && j < L);
+    while (__any_sync(mask, going)) {
+        if (going) {
+            const int lim = min(min(nw - i, mw - j), min(L - i, L - j));
+            // a match run never reaches past the window: the zeros shifted in are never compared
+            const uint32_t x = (uint32_t)(((qT0 << i) ^ (qP0 << j)) >> 32) |
+                               (uint32_t)(((qT1 << i) ^ (qP1 << j)) >> 32);
+            const int z = __clz(x);
+            const int run = min(z, lim);
+            out.emit_maybe(kOpEq, run);
+            i += run;
+            j += run;
+            const bool cont = j < mw && i < L && j < L;
+            const bool edit = cont && !(z == 32 && run < lim);
+            if (edit && d <= 0) {  // no edge can leave row 0 here (Theorem 1)
+                atomicOr(p.status, 1);
+                failed = true;
+                going = false;
+            } else if (edit) {
+                const bool tx = i < nw;
+                const bool j1 = j + 1 < mw;
+                const int lim_r = mw - (d - 1);  // bits < lim_r of the right column R[n][d-1] are 1
+                const int r = d - 1;
+                const bool ld1 = tx && i + 1 < nw;
+                // entries (i+1, d-1) and (i, d-1) as 64-bit words; t1 = bits j, j+1 of the
+                // first, r0b = bit j+1 of the second
+                uint64_t q1, q0;
+                int s1, s0;
+                if (!full) {
+                    const uint32_t *rp = band_row(r) + i * COLW;
+                    const uint32_t v1 = ld1 ? rp[COLW] : 0u;
+                    const uint32_t v0 = tx ? rp[0] : 0u;
+                    const int kk = j - i + B0;  // band bit of (i, j); 0..30 on the path
+                    q1 = (1ull << 63) | ((uint64_t)v1 << 31);  // band bit kk-1 at position kk
+                    q0 = (uint64_t)v0 << 32;
+                    s1 = kk;
+                    s0 = kk + 1;
+                } else {
+                    const uint2 *fp = reinterpret_cast<const uint2 *>(fb + (int64_t)r * fb_row) + (i * PPW + g);
+                    const uint2 a = ld1 ? fp[PPW] : make_uint2(0u, 0u);
+                    const uint2 b = tx ? fp[0] : make_uint2(0u, 0u);
+                    q1 = ((uint64_t)a.x << 32) | a.y;
+                    q0 = ((uint64_t)b.x << 32) | b.y;
+                    s1 = j;
+                    s0 = j + 1;
+                }
+                const uint32_t t1 = (uint32_t)((q1 << s1) >> 62);
+                const uint32_t r0b = (uint32_t)((q0 << (s0 & 63)) >> 63);  // s0 == 64 only when !j1
+                const uint32_t r1j = ld1 ? (t1 >> 1) : (j < lim_r ? 1u : 0u);
+                const uint32_t r1j1 = !j1 ? 0u : (ld1 ? (t1 & 1u) : (j + 1 < lim_r ? 1u : 0u));
+                const uint32_t r0j1 = !j1 ? 0u : (tx ? r0b : (j + 1 < lim_r ? 1u : 0u));
+                const uint32_t bS = tx ? r1j1 : 1u;
+                const uint32_t bI = r0j1;
+                const uint32_t bD = tx ? r1j : 1u;
+                const bool tS = tx && bS == 0u;
+                const bool tI = !tS && bI == 0u;
+                const bool tD = !tS && !tI && tx && bD == 0u;
+                if (!(tS || tI || tD)) {
+                    atomicOr(p.status, 1);
+                    failed = true;
+                    going = false;
+                } else {
+                    out.emit(tS ? kOpX : (tI ? kOpI : kOpD), 1);
+                    i += (tS || tD) ? 1 : 0;
+                    j += (tS || tI) ? 1 : 0;
+                    d -= 1;
+                    going = j < mw && i < L && j < L;
+                }
+            } else {
+                going = cont;
+            }
+        }
+    }
+    if (tb_live) {
+        ti += i;
+        pj += j;
+    }
+}
+
+template <int G>
+__global__ void __launch_bounds__(64, BandMinBlocks<G>::value) align_band_kernel(const AlignParams p) {
+    constexpr int PPW = 32 / G;
+    static_assert((64 / G) * G == 64 && 64 / G <= 32 && 32 % G == 0, "unsupported shape");
 
     extern __shared__ __align__(16) uint32_t smem[];
     const int lane = threadIdx.x & 31;
@@ -131,11 +343,7 @@ __global__ void __launch_bounds__(64, BandMinBlocks<G>::value) align_band_kernel
     const int g = lane / G;
     const int l = lane - g * G;
     const int tbl = g * G + G - 1;  // traceback lane of this pair (owns column 0)
-    const int W = p.W, L = p.W - p.O, k = p.k;
-    const int ncolp = p.ncol, rcap = p.rcap, rstride = p.rstride;
-    const int dmax = min(k, kBandRows - 1);  // deepest row the band computes
-    const int colbase = (G - 1 - l) * C;
-    const bool lane_stores = colbase < ncolp;
+    const int W = p.W;
     uint32_t tbl_all = 0;
 #pragma unroll
     for (int q = 0; q < PPW; ++q) tbl_all |= 1u << (q * G + G - 1);
@@ -147,12 +355,6 @@ __global__ void __launch_bounds__(64, BandMinBlocks<G>::value) align_band_kernel
     uint32_t *spill = p.spill + gw * p.spill_words_per_pair;
     // full-width fallback rows: [row][column][pair][2 words]
     uint32_t *fb = p.fb ? p.fb + gw * p.fb_words_per_warp : nullptr;
-    const int fb_row = ncolp * PPW * 2;
-
-    // word of (row, column 0) of this pair's band rows (shared memory or scratch)
-    auto band_row = [&](int row) -> uint32_t * {
-        return row < rcap ? tab + row * rstride + g : spill + (row - rcap) * rstride + g;
-    };
 
     Slot s;
     slot_init(s, gw * PPW + g, p.slots_per_warp > 0 && g >= p.slots_per_warp);
@@ -167,178 +369,308 @@ __global__ void __launch_bounds__(64, BandMinBlocks<G>::value) align_band_kernel
     for (;;) {
         slot_fetch<G>(p, s, out, l, g, tbl, nwarps * PPW, q_lo, q_hi);
         if (!__any_sync(kFull, s.active)) break;
-        const bool active = s.active;
-        const int nw = active ? min(W, s.n - s.ti) : 0;
-        const int mw = active ? min(W, s.m - s.pj) : 0;
-        const int64_t tblk = active ? s.tblk : 0, pblk = active ? s.pblk : 0;
-
-        // ---- window set-up: band pattern masks and row-0 masks of this lane's columns
-        uint32_t XA[C];   // X of the next row (row 0: bits with j >= m_w cleared)
-        uint32_t PMC[C];  // PMrel[text[i]]
-        {
-            // pattern planes from pj + colbase - 16: column colbase + c starts c + 1 bits in
-            uint32_t Pa0, Pa1, Pb0, Pb1, T0, T1;
-            load32(s.pseq, pblk, (int64_t)s.pj + colbase - 16, Pa0, Pa1);
-            load32(s.pseq, pblk, (int64_t)s.pj + colbase + 16, Pb0, Pb1);
-            load32(s.tseq, tblk, (int64_t)s.ti + colbase, T0, T1);
-            const int real_cols = nw - colbase;
-#pragma unroll
-            for (int c = 0; c < C; ++c) {
-                const uint32_t m0 = 0u - ((T0 >> (31 - c)) & 1u);
-                const uint32_t m1 = 0u - ((T1 >> (31 - c)) & 1u);
-                const uint32_t w0 = __funnelshift_lc(Pb0, Pa0, c + 1);
-                const uint32_t w1 = __funnelshift_lc(Pb1, Pa1, c + 1);
-                PMC[c] = c < real_cols ? ((w0 ^ m0) | (w1 ^ m1)) : kFull;
-                XA[c] = prefix_mask(mw - (colbase + c) + B0);
-            }
-            if (active && l == G - 1) {
-#pragma unroll
-                for (int w = 0; w <= 2; ++w) {
-                    uint32_t a, b;
-                    load32(s.tseq, s.tblk, (int64_t)s.ti + 32 * w, a, b);
-                    stage[w] = a;
-                    stage[3 + w] = b;
-                    load32(s.pseq, s.pblk, (int64_t)s.pj + 32 * w, a, b);
-                    stage[6 + w] = a;
-                    stage[9 + w] = b;
-                }
-            }
-        }
-
-        // ---- GenASM-DC in the band, rows in a pipeline over the lanes of each pair
-        uint32_t done_mask = __ballot_sync(kFull, l == G - 1 && !active);
-        int d_opt = -1;
-        uint32_t bottom = 0u;
-        for (int st = 0; done_mask != tbl_all; ++st) {
-            const int d = st - l;
-            const bool dc_done = (done_mask >> tbl) & 1u;
-            const uint32_t v = __shfl_up_sync(kFull, bottom, 1);
-            // lane 0 starts from column 64, whose bits j < m_w - d are 1
-            uint32_t pR = (l == 0) ? prefix_mask(mw - d - WMAX + B0) : v;
-            bool found = false;
-            if (!dc_done && d >= 0 && d <= dmax) {
-                uint32_t *rowp = band_row(d) + colbase * COLW;
-#pragma unroll
-                for (int c = C - 1; c >= 0; --c) {
-                    const uint32_t R = XA[c] & (pR | PMC[c]);
-                    if (lane_stores) rowp[c * COLW] = R;
-                    // next row: S = V[i+1][d], D = V[i+1][d] >> 1, I = V[i][d] << 1 (1s shifted in)
-                    XA[c] = pR & __funnelshift_r(pR, kFull, 1) & __funnelshift_l(kFull, R, 1);
-                    pR = R;
-                }
-                bottom = pR;
-                found = (l == G - 1) && (((pR >> (31 - B0)) & 1u) == 0u);
-            }
-            const uint32_t fmask = __ballot_sync(kFull, found);
-            const int dl = st - (G - 1);  // row finished by the traceback lane
-            if (!dc_done && ((fmask >> tbl) & 1u) && d_opt < 0) d_opt = dl;
-            done_mask |= fmask;
-            if (dl >= dmax) done_mask = tbl_all;
-        }
-
-        // ---- windows beyond the band: full-width DC (Algorithm 1 on two words)
-        const uint32_t full_mask = __ballot_sync(kFull, l == G - 1 && active && d_opt < 0 && k >= kBandRows);
-        const bool full = (full_mask >> tbl) & 1u;
-        if (full_mask)
-            full_width_dc<G>(s.pseq, pblk, s.pj, s.tseq, tblk, s.ti, nw, mw, k, l, tbl, tbl_all, full_mask,
-                             lane_stores, fb + ((int64_t)colbase * PPW + g) * 2, fb_row, d_opt);
-
+        BandWindow bw;
+        bw.active = s.active;
+        bw.nw = bw.active ? min(W, s.n - s.ti) : 0;
+        bw.mw = bw.active ? min(W, s.m - s.pj) : 0;
+        bw.tblk = bw.active ? s.tblk : 0;
+        bw.pblk = bw.active ? s.pblk : 0;
+        bw.tseq = s.tseq;
+        bw.pseq = s.pseq;
+        bw.ti = s.ti;
+        bw.pj = s.pj;
+        int d_opt;
+        bool full;
+        band_window_dc<G>(p, bw, l, g, tbl, tbl_all, tab, spill, fb, stage, d_opt, full);
         __syncwarp();  // entries written by every lane are visible to the traceback lane
-
-        // ---- GenASM-TB (branch-free over the warp's traceback lanes, as in the full-width kernel)
-        if (l == G - 1) {
-            const bool tb_live = active && d_opt >= 0;
-            if (active) s.st_windows += 1;
-            if (active && d_opt < 0) s.failed = true;
-            if (tb_live) {
-                s.st_rows += d_opt + 1;
-                s.st_cells += (int64_t)(d_opt + 1) * nw;
-            }
-            const uint64_t qT0 = ((uint64_t)stage[0] << 32) | stage[1];
-            const uint64_t qT1 = ((uint64_t)stage[3] << 32) | stage[4];
-            const uint64_t qP0 = ((uint64_t)stage[6] << 32) | stage[7];
-            const uint64_t qP1 = ((uint64_t)stage[9] << 32) | stage[10];
-            int i = 0, j = 0, d = d_opt;
-            bool going = tb_live && (j < mw && i < L && j < L);
-            while (__any_sync(tbl_all, going)) {
-                if (going) {
-                    const int lim = min(min(nw - i, mw - j), min(L - i, L - j));
-                    // a match run never reaches past the window: the zeros shifted in are never compared
-                    const uint32_t x = (uint32_t)(((qT0 << i) ^ (qP0 << j)) >> 32) |
-                                       (uint32_t)(((qT1 << i) ^ (qP1 << j)) >> 32);
-                    const int z = __clz(x);
-                    const int run = min(z, lim);
-                    out.emit_maybe(kOpEq, run);
-                    i += run;
-                    j += run;
-                    const bool cont = j < mw && i < L && j < L;
-                    const bool edit = cont && !(z == 32 && run < lim);
-                    if (edit && d <= 0) {  // no edge can leave row 0 here (Theorem 1)
-                        atomicOr(p.status, 1);
-                        s.failed = true;
-                        going = false;
-                    } else if (edit) {
-                        const bool tx = i < nw;
-                        const bool j1 = j + 1 < mw;
-                        const int lim_r = mw - (d - 1);  // bits < lim_r of the right column R[n][d-1] are 1
-                        const int r = d - 1;
-                        const bool ld1 = tx && i + 1 < nw;
-                        // entries (i+1, d-1) and (i, d-1) as 64-bit words; t1 = bits j, j+1 of the
-                        // first, r0b = bit j+1 of the second
-                        uint64_t q1, q0;
-                        int s1, s0;
-                        if (!full) {
-                            const uint32_t *rp = band_row(r) + i * COLW;
-                            const uint32_t v1 = ld1 ? rp[COLW] : 0u;
-                            const uint32_t v0 = tx ? rp[0] : 0u;
-                            const int kk = j - i + B0;  // band bit of (i, j); 0..30 on the path
-                            q1 = (1ull << 63) | ((uint64_t)v1 << 31);  // band bit kk-1 at position kk
-                            q0 = (uint64_t)v0 << 32;
-                            s1 = kk;
-                            s0 = kk + 1;
-                        } else {
-                            const uint2 *fp = reinterpret_cast<const uint2 *>(fb + (int64_t)r * fb_row) + (i * PPW + g);
-                            const uint2 a = ld1 ? fp[PPW] : make_uint2(0u, 0u);
-                            const uint2 b = tx ? fp[0] : make_uint2(0u, 0u);
-                            q1 = ((uint64_t)a.x << 32) | a.y;
-                            q0 = ((uint64_t)b.x << 32) | b.y;
-                            s1 = j;
-                            s0 = j + 1;
-                        }
-                        const uint32_t t1 = (uint32_t)((q1 << s1) >> 62);
-                        const uint32_t r0b = (uint32_t)((q0 << (s0 & 63)) >> 63);  // s0 == 64 only when !j1
-                        const uint32_t r1j = ld1 ? (t1 >> 1) : (j < lim_r ? 1u : 0u);
-                        const uint32_t r1j1 = !j1 ? 0u : (ld1 ? (t1 & 1u) : (j + 1 < lim_r ? 1u : 0u));
-                        const uint32_t r0j1 = !j1 ? 0u : (tx ? r0b : (j + 1 < lim_r ? 1u : 0u));
-                        const uint32_t bS = tx ? r1j1 : 1u;
-                        const uint32_t bI = r0j1;
-                        const uint32_t bD = tx ? r1j : 1u;
-                        const bool tS = tx && bS == 0u;
-                        const bool tI = !tS && bI == 0u;
-                        const bool tD = !tS && !tI && tx && bD == 0u;
-                        if (!(tS || tI || tD)) {
-                            atomicOr(p.status, 1);
-                            s.failed = true;
-                            going = false;
-                        } else {
-                            out.emit(tS ? kOpX : (tI ? kOpI : kOpD), 1);
-                            i += (tS || tD) ? 1 : 0;
-                            j += (tS || tI) ? 1 : 0;
-                            d -= 1;
-                            going = j < mw && i < L && j < L;
-                        }
-                    } else {
-                        going = cont;
-                    }
-                }
-            }
-            if (tb_live) {
-                s.ti += i;
-                s.pj += j;
-            }
-        }
+        if (l == G - 1)
+            band_window_tb<G>(p, tbl_all, bw.active, d_opt, full, bw.nw, bw.mw, stage, tab, spill, fb, g, out, s.ti,
+                              s.pj, s.failed, s.st_rows, s.st_cells, s.st_windows);
         slot_window_done<G>(p, s, out, l, tbl);
     }
+}
+
+// ---------------------------------------------------------------- warp-specialised banded kernel
+//
+// A block holds kWsDcWarps DC warps and one traceback warp. Each DC warp owns two sets of eight
+// pair slots (4 lanes per pair) and alternates between them: while the traceback warp traces set
+// A of every DC warp (32 pairs, one lane each), the DC warps compute the next window of set B.
+// The hand-offs are mbarriers in shared memory: full[w][x] (the 32 lanes of DC warp w arrive when
+// set x's rows and d_opt are written) and empty[w][x] (the traceback warp's 8 lanes for warp w
+// arrive when set x is traced and its cursors advanced). Every wait is bounded; on a time-out the
+// warp sets status bit 3 and returns as a whole.
+
+constexpr int kWsDcWarps = 4;
+constexpr int kWsSlotFree = 0, kWsSlotActive = 1, kWsSlotFresh = 2, kWsSlotDone = 3;
+
+// One pair slot of a set, in shared memory: the DC warp refills it, the traceback warp advances it.
+struct WsSlot {
+    int64_t toff, poff;         // sequence offsets (bases)
+    int64_t cig_base, cig_cap;  // the pair's CIGAR scratch
+    int64_t st_rows, st_cells;
+    long long t_start;
+    int32_t pair, state, n, m, ti, pj, d_opt, full;
+    int32_t cig_n, edits, st_windows, failed;
+    uint32_t cig_cur, pad;
+};
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_addr(bar))
+                 : "memory");
+}
+
+// Wait for the completion of the phase of parity `parity`; false after about 2^24 tries.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
+    const uint32_t a = smem_addr(bar);
+    for (int it = 0; it < (1 << 24); ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+__global__ void __launch_bounds__(32 * (kWsDcWarps + 1), 3) align_ws_kernel(const AlignParams p) {
+    constexpr int G = 4, PPW = 8;
+    extern __shared__ __align__(16) uint32_t smem[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int set_words = p.smem_words_per_warp;  // rows + stage of one set
+    WsSlot *slots = reinterpret_cast<WsSlot *>(smem + (int64_t)2 * kWsDcWarps * set_words);  // [w][x][g]
+    int32_t *set_done = reinterpret_cast<int32_t *>(slots + 2 * kWsDcWarps * PPW);           // [w][x]
+    uint64_t *bars = reinterpret_cast<uint64_t *>(set_done + 2 * kWsDcWarps);                // full[w][x], empty[w][x]
+    uint64_t *full_bar = bars, *empty_bar = bars + 2 * kWsDcWarps;
+    const int W = p.W;
+    int64_t q_lo, q_hi;
+    slot_range(p, q_lo, q_hi);
+
+    if (threadIdx.x == 0) {
+        for (int b = 0; b < 2 * kWsDcWarps; ++b) {
+            mbar_init(full_bar + b, 32);
+            mbar_init(empty_bar + b, PPW);
+            set_done[b] = 0;
+        }
+    }
+    for (int t = threadIdx.x; t < 2 * kWsDcWarps * PPW; t += blockDim.x) {
+        slots[t].state = kWsSlotFree;
+        slots[t].pair = -1;
+        slots[t].toff = slots[t].poff = 0;
+        slots[t].n = slots[t].m = slots[t].ti = slots[t].pj = 0;
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    __syncthreads();
+
+    auto set_tab = [&](int w, int x) { return smem + (int64_t)(w * 2 + x) * set_words; };
+    auto set_scratch = [&](uint32_t *base, int64_t words, int w, int x) -> uint32_t * {
+        return base ? base + (((int64_t)blockIdx.x * kWsDcWarps + w) * 2 + x) * words : nullptr;
+    };
+
+    if (wib < kWsDcWarps) {
+        // ------------------------------------------------------------ DC warp
+        const int w = wib;
+        const int g = lane / G, l = lane - g * G, tbl = g * G + G - 1;
+        uint32_t tbl_all = 0;
+#pragma unroll
+        for (int q = 0; q < PPW; ++q) tbl_all |= 1u << (q * G + G - 1);
+        int rounds[2] = {0, 0};
+        bool fin[2] = {false, false};
+        for (int r = 0; !(fin[0] && fin[1]); ++r) {
+            const int x = r & 1;
+            if (fin[x]) continue;
+            const bool timed_out = rounds[x] > 0 && !mbar_wait(empty_bar + w * 2 + x, (rounds[x] - 1) & 1);
+            if (__any_sync(kFull, timed_out)) {  // the whole warp leaves together
+                if (lane == 0) atomicOr(p.status, 8);
+                return;
+            }
+            WsSlot &sl = slots[(w * 2 + x) * PPW + g];
+            // refill: the pair's traceback lane takes the next pair from the queue
+            if (l == G - 1 && sl.state == kWsSlotFree) {
+                int next = -1;
+                for (;;) {
+                    const int64_t q = q_lo + atomicAdd(p.queue, 1);
+                    if (q >= q_hi) break;
+                    const int pr = p.order ? p.order[q] : (int)q;
+                    if (p.pat_len[pr] > 0) {
+                        next = pr;
+                        break;
+                    }
+                    p.edit_counts[pr] = 0;
+                    p.text_consumed[pr] = 0;
+                    p.cigar_lens[pr] = 0;
+                    if (p.st_windows) p.st_windows[pr] = 0;
+                    if (p.st_rows) p.st_rows[pr] = 0;
+                    if (p.st_cells) p.st_cells[pr] = 0;
+                    if (p.st_cycles) p.st_cycles[pr] = 0;
+                }
+                if (next < 0) {
+                    sl.state = kWsSlotDone;
+                } else {
+                    sl.pair = next;
+                    sl.n = p.text_len[next];
+                    sl.m = p.pat_len[next];
+                    sl.toff = p.text_off[next];
+                    sl.poff = p.pat_off[next];
+                    sl.ti = 0;
+                    sl.pj = 0;
+                    sl.t_start = clock64();
+                    sl.state = kWsSlotFresh;
+                }
+            }
+            __syncwarp();
+            const int state = sl.state;
+            const bool active = state == kWsSlotActive || state == kWsSlotFresh;
+            if (!__any_sync(kFull, active)) {
+                if (lane == 0) set_done[w * 2 + x] = 1;
+                __syncwarp();
+                mbar_arrive(full_bar + w * 2 + x);
+                fin[x] = true;
+                ++rounds[x];
+                continue;
+            }
+            BandWindow bw;
+            bw.active = active;
+            bw.tseq = reinterpret_cast<const uint2 *>(p.texts + (sl.toff >> 4));
+            bw.pseq = reinterpret_cast<const uint2 *>(p.patterns + (sl.poff >> 4));
+            bw.ti = sl.ti;
+            bw.pj = sl.pj;
+            bw.nw = active ? min(W, sl.n - sl.ti) : 0;
+            bw.mw = active ? min(W, sl.m - sl.pj) : 0;
+            bw.tblk = active ? (sl.n + 31) >> 5 : 0;
+            bw.pblk = active ? (sl.m + 31) >> 5 : 0;
+            uint32_t *tab = set_tab(w, x);
+            uint32_t *stage = tab + p.table_words_per_warp + g * (4 * 3);
+            int d_opt;
+            bool full;
+            band_window_dc<G>(p, bw, l, g, tbl, tbl_all, tab, set_scratch(p.spill, p.spill_words_per_pair, w, x),
+                              set_scratch(p.fb, p.fb_words_per_warp, w, x), stage, d_opt, full);
+            if (l == G - 1) {
+                sl.d_opt = d_opt;
+                sl.full = full ? 1 : 0;
+            }
+            __syncwarp();
+            mbar_arrive(full_bar + w * 2 + x);  // every lane: its rows, stage and slot writes are released
+            ++rounds[x];
+        }
+    } else {
+        // ------------------------------------------------------------ traceback warp
+        const int w = lane / PPW, g = lane % PPW;
+        int rounds[2] = {0, 0};
+        bool fin[2] = {false, false};
+        for (int r = 0; !__all_sync(kFull, fin[0] && fin[1]); ++r) {
+            const int x = r & 1;
+            const bool waited = !fin[x];
+            const bool timed_out = waited && !mbar_wait(full_bar + w * 2 + x, rounds[x] & 1);
+            if (__any_sync(kFull, timed_out)) {  // the whole warp leaves together
+                if (lane == 0) atomicOr(p.status, 8);
+                return;
+            }
+            const bool set_fin = waited && set_done[w * 2 + x] != 0;
+            WsSlot &sl = slots[(w * 2 + x) * PPW + g];
+            const int state = waited ? sl.state : kWsSlotDone;
+            const bool active = !set_fin && (state == kWsSlotActive || state == kWsSlotFresh);
+            CigarOut out;
+            int ti = 0, pj = 0, nw = 0, mw = 0, d_opt = -1;
+            bool full = false, failed = false;
+            int64_t st_rows = 0, st_cells = 0;
+            int32_t st_windows = 0;
+            if (active) {
+                if (state == kWsSlotFresh) {
+                    const int64_t c0 = p.cigar_off[sl.pair];
+                    sl.cig_base = c0;
+                    sl.cig_cap = p.cigar_off[sl.pair + 1] - c0;
+                    sl.cig_n = 0;
+                    sl.cig_cur = 0u;
+                    sl.edits = 0;
+                    sl.failed = 0;
+                    sl.st_rows = 0;
+                    sl.st_cells = 0;
+                    sl.st_windows = 0;
+                }
+                out.dst = p.cigar + sl.cig_base;
+                out.cap = sl.cig_cap;
+                out.n = sl.cig_n;
+                out.cur = sl.cig_cur;
+                out.edits = sl.edits;
+                ti = sl.ti;
+                pj = sl.pj;
+                nw = min(W, sl.n - ti);
+                mw = min(W, sl.m - pj);
+                d_opt = sl.d_opt;
+                full = sl.full != 0;
+                failed = sl.failed != 0;
+                st_rows = sl.st_rows;
+                st_cells = sl.st_cells;
+                st_windows = sl.st_windows;
+            } else {
+                out.dst = nullptr;
+                out.cap = 0;
+                out.n = 0;
+                out.cur = 0u;
+                out.edits = 0;
+            }
+            const uint32_t *tab = set_tab(w, x);
+            band_window_tb<G>(p, kFull, active, d_opt, full, nw, mw, tab + p.table_words_per_warp + g * (4 * 3), tab,
+                              set_scratch(p.spill, p.spill_words_per_pair, w, x),
+                              set_scratch(p.fb, p.fb_words_per_warp, w, x), g, out, ti, pj, failed, st_rows, st_cells,
+                              st_windows);
+            if (active) {
+                if (failed || pj >= sl.m) {
+                    out.flush();
+                    const int pair = sl.pair;
+                    p.edit_counts[pair] = failed ? -1 : out.edits;
+                    p.text_consumed[pair] = failed ? 0 : ti;
+                    if (out.n > out.cap) atomicOr(p.status, 2);
+                    p.cigar_lens[pair] = failed ? 0 : min(out.n, (int32_t)out.cap);
+                    if (p.st_windows) p.st_windows[pair] = st_windows;
+                    if (p.st_rows) p.st_rows[pair] = st_rows;
+                    if (p.st_cells) p.st_cells[pair] = st_cells;
+                    if (p.st_cycles) p.st_cycles[pair] = clock64() - sl.t_start;
+                    sl.state = kWsSlotFree;
+                } else {
+                    sl.ti = ti;
+                    sl.pj = pj;
+                    sl.cig_n = out.n;
+                    sl.cig_cur = out.cur;
+                    sl.edits = out.edits;
+                    sl.failed = 0;
+                    sl.st_rows = st_rows;
+                    sl.st_cells = st_cells;
+                    sl.st_windows = st_windows;
+                    sl.state = kWsSlotActive;
+                }
+            }
+            __syncwarp();
+            if (waited && !set_fin) mbar_arrive(empty_bar + w * 2 + x);
+            if (set_fin) fin[x] = true;
+            if (waited) ++rounds[x];
+        }
+    }
+}
+
+cudaError_t launch_ws_kernel(const AlignParams &p, int blocks, size_t smem, cudaStream_t st) {
+    align_ws_kernel<<<blocks, 32 * (kWsDcWarps + 1), smem, st>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t occupancy_ws_kernel(size_t smem, int *per_sm) {
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, align_ws_kernel);
+    if (e != cudaSuccess) return e;
+    if ((size_t)a.maxDynamicSharedSizeBytes < smem &&
+        (e = cudaFuncSetAttribute(align_ws_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+            cudaSuccess)
+        return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, align_ws_kernel, 32 * (kWsDcWarps + 1), smem);
 }
 
 template <int G>
@@ -382,5 +714,16 @@ cudaError_t occupancy_band(int lanes, int wpb, size_t smem, int *per_sm) {
 }
 
 bool supported_band(int lanes) { return lanes == 2 || lanes == 4 || lanes == 8; }
+
+cudaError_t launch_align_ws(const AlignParams &p, int blocks, size_t smem, cudaStream_t st) {
+    return kern::launch_ws_kernel(p, blocks, smem, st);
+}
+
+cudaError_t occupancy_ws(size_t smem, int *per_sm) { return kern::occupancy_ws_kernel(smem, per_sm); }
+
+size_t ws_meta_bytes() {
+    return sizeof(kern::WsSlot) * 2 * kern::kWsDcWarps * 8 + sizeof(int32_t) * 2 * kern::kWsDcWarps +
+           sizeof(uint64_t) * 4 * kern::kWsDcWarps + 16;
+}
 
 }  // namespace scrooge

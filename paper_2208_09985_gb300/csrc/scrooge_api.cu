@@ -233,7 +233,7 @@ namespace {
 
 // One alignment-kernel launch: which kernel, its shape and its parameters.
 struct LaunchPlan {
-    bool band = false, sene = true;
+    bool band = false, sene = true, ws = false;
     int words = 0, G = 0, wpb = 1, blocks = 0;
     size_t smem = 0;
     TableShape ts{};
@@ -251,7 +251,9 @@ int make_plan(scrooge_ctx *c, const AlignParams &base, bool band, uint32_t flags
     const bool sene = !(flags & SCROOGE_NO_SENE);
     const bool dent = !(flags & SCROOGE_NO_DENT);
     const KernelConfig kc = c->kcfg[kcfg_index(band ? 0 : words)];
-    int G = kc.lanes;
+    // warp-specialised blocks: banded, persistent, four lanes per pair, not the long-pair launch
+    const bool ws = band && slots == 0 && (flags & SCROOGE_WARP_SPECIALIZED) && (flags & SCROOGE_PERSISTENT);
+    int G = ws ? 4 : kc.lanes;
     auto supported = [&](int lanes, int swp) {
         return words == 1 ? supported_w32(lanes, sene, swp)
                           : (words == 2 ? supported_w64(lanes, sene, swp) : supported_w128(lanes, sene, swp));
@@ -274,28 +276,33 @@ int make_plan(scrooge_ctx *c, const AlignParams &base, bool band, uint32_t flags
     int rcap = std::min(kc.rows, rows_needed);
     const int stage = stage_words_per_warp(words, PPW);
     int wpb = slots > 0 ? 1 : kc.wpb;
-    // keep the block's shared memory within the opt-in limit
-    while (rcap > 1 && (size_t)wpb * (table_words_per_warp(rcap, ts, PPW, chunk) + stage) * 4 > c->smem_optin) --rcap;
-    while (wpb > 1 && (size_t)wpb * (table_words_per_warp(rcap, ts, PPW, chunk) + stage) * 4 > c->smem_optin) --wpb;
+    // keep the block's shared memory within the opt-in limit (a warp-specialised block holds 8 sets)
+    const int sets = ws ? kWsSets : wpb;
+    const size_t meta = ws ? ws_meta_bytes() : 0;
+    while (rcap > 1 && (size_t)sets * (table_words_per_warp(rcap, ts, PPW, chunk) + stage) * 4 + meta > c->smem_optin)
+        --rcap;
+    while (!ws && wpb > 1 && (size_t)wpb * (table_words_per_warp(rcap, ts, PPW, chunk) + stage) * 4 > c->smem_optin)
+        --wpb;
     p.rcap = rcap;
     p.table_words_per_warp = (int32_t)table_words_per_warp(rcap, ts, PPW, chunk);
     p.smem_words_per_warp = p.table_words_per_warp + stage;
-    const size_t smem = (size_t)wpb * p.smem_words_per_warp * 4;
+    const size_t smem = (size_t)(ws ? kWsSets : wpb) * p.smem_words_per_warp * 4 + meta;
     int per_sm = 0;
-    cudaError_t e = band ? occupancy_band(G, wpb, smem, &per_sm)
+    cudaError_t e = ws ? occupancy_ws(smem, &per_sm)
+                  : band ? occupancy_band(G, wpb, smem, &per_sm)
                          : (words == 1 ? occupancy_w32(G, sene, ts.swp, wpb, smem, &per_sm)
                                        : (words == 2 ? occupancy_w64(G, sene, ts.swp, wpb, smem, &per_sm)
                                                      : occupancy_w128(G, sene, ts.swp, wpb, smem, &per_sm)));
     if (e != cudaSuccess) return cuda_fail(c, e, "occupancy query");
     if (per_sm < 1) return fail(c, SCROOGE_E_INVAL, "kernel config does not fit on an SM (smem %zu B)", smem);
     const int64_t groups = ((int64_t)p.n_pairs + PPW - 1) / PPW;
-    const int64_t want_blocks = (groups + wpb - 1) / wpb;
+    const int64_t want_blocks = ws ? (groups + kWsSets - 1) / kWsSets : (groups + wpb - 1) / wpb;
     int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(want_blocks, (int64_t)per_sm * c->sm_count));
     if (slots > 0) blocks = (int)std::min<int64_t>((int64_t)per_sm * c->sm_count, 3LL * c->sm_count);
     p.slots_per_warp = slots;
     const int spill_rows = std::max(0, rows_needed - rcap);
     p.spill_words_per_pair = table_words_per_warp(spill_rows, ts, PPW, chunk);  // per warp
-    const size_t spill_bytes = (size_t)blocks * wpb * (size_t)std::max<int64_t>(p.spill_words_per_pair, 4) * 4;
+    const size_t spill_bytes = (size_t)blocks * sets * (size_t)std::max<int64_t>(p.spill_words_per_pair, 4) * 4;
     int rc;
     if ((rc = ensure(c, spill, spill_bytes, "DP row scratch"))) return rc;
     p.spill = (uint32_t *)spill.p;
@@ -304,13 +311,14 @@ int make_plan(scrooge_ctx *c, const AlignParams &base, bool band, uint32_t flags
     if (band) {
         p.fb_words_per_warp = band_fallback_words(k, ts.ncol, PPW);
         if (p.fb_words_per_warp > 0) {
-            if ((rc = ensure(c, fallback, (size_t)blocks * wpb * (size_t)p.fb_words_per_warp * 4,
+            if ((rc = ensure(c, fallback, (size_t)blocks * sets * (size_t)p.fb_words_per_warp * 4,
                              "full-width fallback scratch")))
                 return rc;
             p.fb = (uint32_t *)fallback.p;
         }
     }
     out.band = band;
+    out.ws = ws;
     out.sene = sene;
     out.words = words;
     out.G = G;
@@ -323,6 +331,7 @@ int make_plan(scrooge_ctx *c, const AlignParams &base, bool band, uint32_t flags
 }
 
 cudaError_t launch_plan(const LaunchPlan &lp, cudaStream_t st) {
+    if (lp.ws) return launch_align_ws(lp.p, lp.blocks, lp.smem, st);
     if (lp.band) return launch_align_band(lp.p, lp.G, lp.wpb, lp.blocks, lp.smem, st);
     switch (lp.words) {
         case 1: return launch_align_w32(lp.p, lp.G, lp.sene, lp.ts.swp, lp.wpb, lp.blocks, lp.smem, st);

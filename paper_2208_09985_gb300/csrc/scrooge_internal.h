@@ -116,6 +116,13 @@ constexpr int kBandRows = 16;  // rows d = 0..15 are exact inside the 32-bit ban
 cudaError_t launch_align_band(const AlignParams &, int lanes, int wpb, int blocks, size_t smem, cudaStream_t);
 cudaError_t occupancy_band(int lanes, int wpb, size_t smem, int *blocks_per_sm);
 bool supported_band(int lanes);
+// Warp-specialised banded kernel (align_band.cu): blocks of 4 DC warps (4 lanes per pair, two
+// sets of 8 pairs each) and one traceback warp; persistent launches only. Shared memory per block:
+// 8 sets x smem_words_per_warp words, then ws_meta_bytes().
+constexpr int kWsSets = 8;
+cudaError_t launch_align_ws(const AlignParams &, int blocks, size_t smem, cudaStream_t);
+cudaError_t occupancy_ws(size_t smem, int *blocks_per_sm);
+size_t ws_meta_bytes();
 // words of the full-width fallback region of one warp of the banded kernel
 inline int64_t band_fallback_words(int k, int ncol, int ppw) {
     return k >= kBandRows ? (int64_t)(k + 1) * ncol * ppw * 2 : 0;

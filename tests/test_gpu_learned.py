@@ -319,3 +319,23 @@ def test_autotune_picks_a_heavy_class(ctx):
     assert sc.scrooge_get_heavy_class(h) in [r[1] for r in table if r[4] == 2]
     got = _run(ctx, db, sc.SCROOGE_LEARNED)
     assert_same(got, oracle.align_batch(b, 64, 24), label="after autotune")
+
+
+def test_warp_specialized_learned_and_graph(ctx):
+    h, s = ctx
+    b = synth.concat([synth.uneven_reads(150, seed=91), synth.short_reads(400, seed=92)])
+    db = sc.DeviceBatch(sc.PackedBatch(b))
+    plain = _run(ctx, db, 0)
+    import torch
+    with torch.cuda.stream(s):
+        learned.train(h, db, epochs=3, batch=256)
+    saved = sc.scrooge_get_heavy_class(h)
+    try:
+        for hc in (16, 12):
+            sc.scrooge_set_heavy_class(h, hc)
+            for flags in (sc.SCROOGE_LEARNED, sc.SCROOGE_LEARNED | sc.SCROOGE_GRAPH, sc.SCROOGE_PERSISTENT):
+                for rep in range(2):
+                    _same_device(_run(ctx, db, flags | sc.SCROOGE_WARP_SPECIALIZED), plain,
+                                 f"warp-specialised heavy {hc} flags {flags} run {rep}")
+    finally:
+        sc.scrooge_set_heavy_class(h, saved)

@@ -263,3 +263,30 @@ def test_full_size_short_reads_sampled(ctx):
     sample = np.random.default_rng(7).choice(b.n_pairs, 5000, replace=False)
     r = oracle.align_batch(b.subset(sample), 64, 24, threads=THREADS)
     assert_same(g, r, pairs=sample, label="short_reads full size (sample)")
+
+
+@pytest.mark.parametrize("rows", [1, 4, 8])
+def test_warp_specialized_blocks(ctx, rows):
+    """Persistent banded launches as DC + traceback warps give the oracle's results."""
+    b = synth.concat([synth.long_reads(6, seed=71), synth.short_reads(600, seed=72),
+                      synth.fixed_error(20, 0.2, length=1500, seed=73), synth.random_pairs(300, 300, 300, seed=74),
+                      synth.tiny_windows(50, seed=75)])
+    pb = sc.PackedBatch(b)
+    saved = sc.scrooge_get_kernel_config(ctx, 0)
+    try:
+        sc.scrooge_set_kernel_config(ctx, 0, 4, rows, 2)
+        for O, k in ((24, 64), (33, 64), (24, 12), (40, 20), (0, 64)):
+            r = oracle.align_batch(b, 64, O, k, threads=THREADS)
+            g = sc.align_host(ctx, pb, 64, O, k, sc.SCROOGE_PERSISTENT | sc.SCROOGE_WARP_SPECIALIZED)
+            assert_same(g, r, label=f"warp-specialised rows={rows} O={O} k={k}")
+    finally:
+        sc.scrooge_set_kernel_config(ctx, 0, *saved)
+
+
+def test_warp_specialized_few_pairs(ctx):
+    """Fewer pairs than slots, a single pair, and empty patterns."""
+    for b in (synth.tiny_windows(1, seed=81), synth.tiny_windows(7, seed=82), synth.short_reads(65, seed=83),
+              synth.from_lists(["ACGT" * 30, "", "ACG"], ["", "ACGT", "ACGTT"])):
+        r = oracle.align_batch(b, 64, 24, threads=THREADS)
+        g = sc.align_host(ctx, sc.PackedBatch(b), 64, 24, None, sc.SCROOGE_PERSISTENT | sc.SCROOGE_WARP_SPECIALIZED)
+        assert_same(g, r, label=f"warp-specialised {b.n_pairs} pairs")
