@@ -218,7 +218,8 @@ int scrooge_last_launch_shape(const scrooge_ctx *ctx, int64_t *shape, int32_t n)
  * the banded kernel serves, it also times the heavy load classes
  * (scrooge_set_heavy_class) 16, 15, ..., 10, 0 before and again after the
  * settings sweep (at least 3 timed runs each), as rows 0, class, 0,
- * microseconds, 2, and installs the fastest class of the second pass.
+ * microseconds, 2, and installs the fastest class of the second pass if it
+ * beats class 16 (no split) by at least 10%, else 16.
  * *n_results gets the row count.
  * Synchronous. */
 int scrooge_autotune(scrooge_ctx *ctx, const uint32_t *texts, const int64_t *text_offsets,

@@ -713,8 +713,10 @@ int scrooge_autotune(scrooge_ctx *c, const uint32_t *texts, const int64_t *text_
         ++nres;
     };
     // learned launches on band-sized windows: which load classes go to the full-width kernel
+    // A split must beat "no split" (class 16) by 10% to be chosen: the class times of one sample
+    // vary with its hardest pairs, and a marginal split can cost more on the next batch.
     auto sweep_classes = [&]() -> int {
-        float best_t = -1.f;
+        float best_t = -1.f, t_none = -1.f;
         int best_class = c->heavy_class;
         for (int hc : classes) {
             c->heavy_class = hc;
@@ -722,11 +724,13 @@ int scrooge_autotune(scrooge_ctx *c, const uint32_t *texts, const int64_t *text_
             const int r = time_it(std::max(repeats, 3), t);
             if (r != SCROOGE_OK) return r;
             record(0, hc, 0, t, 2);
+            if (hc == 16) t_none = t;
             if (best_t < 0.f || t < best_t) {
                 best_t = t;
                 best_class = hc;
             }
         }
+        if (best_class != 16 && t_none > 0.f && best_t > 0.9f * t_none) best_class = 16;
         c->heavy_class = best_class;
         return SCROOGE_OK;
     };

@@ -316,7 +316,11 @@ def test_autotune_picks_a_heavy_class(ctx):
     s.synchronize()
     kinds = [r[4] for r in table]
     assert 1 in kinds and 2 in kinds
-    assert sc.scrooge_get_heavy_class(h) in [r[1] for r in table if r[4] == 2]
+    classes = {r[1]: r[3] for r in table if r[4] == 2}  # the second pass overwrites the first
+    chosen = sc.scrooge_get_heavy_class(h)
+    assert chosen in classes
+    if chosen != 16:
+        assert classes[chosen] <= 0.9 * classes[16]
     got = _run(ctx, db, sc.SCROOGE_LEARNED)
     assert_same(got, oracle.align_batch(b, 64, 24), label="after autotune")
 
