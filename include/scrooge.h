@@ -65,9 +65,9 @@ typedef struct scrooge_ctx scrooge_ctx; /* opaque, owned by the library */
  * (pointers, sizes, W/O/k, flags, kernel settings) repeats. Needs a stream
  * other than the legacy default stream. */
 #define SCROOGE_GRAPH (1u << 7)
-/* Implementation choice, never a change of results: windows of 33..64 bases
- * with SENE and ET use the banded kernel unless this flag asks for the
- * full-width one (see "kernel settings"). */
+/* Implementation choice, never a change of results: windows of 33..128 bases
+ * with SENE and ET use the banded kernels unless this flag asks for the
+ * full-width ones (see "kernel settings"). */
 #define SCROOGE_NO_BAND (1u << 8)
 /* Implementation choice, never a change of results: persistent launches of
  * the banded kernel run as blocks of four DC warps and one traceback warp,
@@ -156,12 +156,14 @@ int scrooge_align_batch(scrooge_ctx *ctx, const uint32_t *texts, const int64_t *
 /* ------------------------------------------------------- kernel settings
  * Implementation parameters of the alignment kernels. They never change
  * results. words = 1, 2 or 4 selects the full-width kernel for windows of up
- * to 32 * words bases; words = 0 selects the banded kernel, which serves
- * windows of 33..64 bases when SENE and ET are on (and SCROOGE_NO_BAND is
- * not given): it keeps the 32 diagonals j - i = -15..16 of each DP entry in
- * one word, which is exact for every window whose edit distance is at most
- * 15, and recomputes the other windows at full width (lanes_per_pair 2, 4 or
- * 8).
+ * to 32 * words bases. The banded kernels serve windows of 33..128 bases when
+ * SENE and ET are on (and SCROOGE_NO_BAND is not given):
+ *   - words = 0 selects the one for 33..64-base windows (lanes_per_pair 2, 4
+ *     or 8). It keeps the 32 diagonals j - i = -15..16 of each DP entry in one
+ *     word, which is exact for every window whose edit distance is at most 15.
+ *   - words = 3 selects the one for 65..128-base windows (lanes_per_pair 8 or
+ *     16). It keeps the 64 diagonals -31..32 in two words, exact up to 31.
+ * Both recompute the other windows at full width.
  *   lanes_per_pair   threads that share one pair's window (words=1: 1,2,4;
  *                    words=2: 2,4,8; words=4: 8,16)
  *   smem_rows        DP rows of each pair kept in shared memory (>= 1); rows

@@ -221,8 +221,8 @@ def scrooge_autotune(ctx, texts, text_offsets, text_lengths, patterns, pattern_o
 
 def settings_slot(W: int, flags: int = 0) -> int:
     """The kernel-settings slot (``words`` of scrooge_set_kernel_config) a call with W and flags uses."""
-    if 32 < W <= 64 and not flags & (SCROOGE_NO_SENE | SCROOGE_NO_ET | SCROOGE_NO_BAND):
-        return 0
+    if 32 < W <= 128 and not flags & (SCROOGE_NO_SENE | SCROOGE_NO_ET | SCROOGE_NO_BAND):
+        return 0 if W <= 64 else 3
     return 1 if W <= 32 else (2 if W <= 64 else 4)
 
 

@@ -32,6 +32,10 @@
 // edits) is recomputed at full width (two words per cell, rows in a per-warp
 // device area) by the lanes of its pair before the traceback.
 //
+// Windows of 65..128 bases use a band of 64 diagonals (j - i = -31..32) in two
+// words per entry, exact for d_opt <= 31, with the same recurrence on 64-bit
+// words and a four-word full-width fallback.
+//
 // The rest -- lanes per pair, the row pipeline over the lanes, rows below
 // `rcap` in shared memory and deeper ones in device scratch, DENT columns,
 // the traceback by runs of matches, the pair queue -- is as in the full-width
@@ -41,72 +45,115 @@
 namespace scrooge {
 namespace kern {
 
+// Band of 32 * BW diagonals in one (BW = 1) or two (BW = 2) 32-bit words per entry.
+template <int BW>
+struct BandT;
+template <>
+struct BandT<1> {
+    using T = uint32_t;
+};
+template <>
+struct BandT<2> {
+    using T = uint64_t;
+};
+template <int BW>
+constexpr int band_diag() { return 16 * BW - 1; }  // band bit of the main diagonal j == i
+template <int BW>
+constexpr int band_rows() { return 16 * BW; }      // rows d = 0..band_rows()-1 are exact
+
+// First `bits` bits (MSB-first) of a band word set.
+__device__ __forceinline__ uint32_t band_prefix(uint32_t, int bits) { return prefix_mask(bits); }
+__device__ __forceinline__ uint64_t band_prefix(uint64_t, int bits) {
+    return bits <= 0 ? 0ull : (bits >= 64 ? ~0ull : (~0ull << (64 - bits)));
+}
+// v >> 1 and v << 1 in band order with a 1 shifted in (no path beyond the band edge).
+__device__ __forceinline__ uint32_t shr1_fill(uint32_t v) { return __funnelshift_r(v, kFull, 1); }
+__device__ __forceinline__ uint64_t shr1_fill(uint64_t v) { return (v >> 1) | (1ull << 63); }
+__device__ __forceinline__ uint32_t shl1_fill(uint32_t v) { return __funnelshift_l(kFull, v, 1); }
+__device__ __forceinline__ uint64_t shl1_fill(uint64_t v) { return (v << 1) | 1ull; }
+__device__ __forceinline__ void store_band(uint32_t *p, uint32_t v) { *p = v; }
+__device__ __forceinline__ void store_band(uint32_t *p, uint64_t v) {
+    *reinterpret_cast<uint2 *>(p) = make_uint2((uint32_t)(v >> 32), (uint32_t)v);
+}
+__device__ __forceinline__ uint64_t load_band64(const uint32_t *p) {
+    const uint2 v = *reinterpret_cast<const uint2 *>(p);
+    return ((uint64_t)v.x << 32) | v.y;
+}
+
 // resident blocks of two warps the register budget is sized for
-template <int G>
+template <int G, int BW>
 struct BandMinBlocks {
-    static constexpr int value = G == 8 ? 12 : (G == 4 ? 8 : 6);
+    static constexpr int value = BW == 2 ? 6 : (G == 8 ? 12 : (G == 4 ? 8 : 6));
 };
 
-// Full-width DC of the windows in `full_mask` (Algorithm 1 on two words per
+// Full-width DC of the windows in `full_mask` (Algorithm 1 on NW words per
 // entry, as in the full-width kernel), rows stored to `rows` (this lane's first
-// column of row 0; [row][column][pair][2 words]); d_opt of those windows is set
+// column of row 0; [row][column][pair][NW words]); d_opt of those windows is set
 // on their traceback lanes. Kept out of line: it is rare, and its registers
 // must not count against the banded loop.
-template <int G>
+template <int G, int NW>
 __device__ __noinline__ void full_width_dc(const uint2 *pseq, int64_t pblk, int pj, const uint2 *tseq, int64_t tblk,
                                            int ti, int nw, int mw, int k, int l, int tbl, uint32_t tbl_all,
                                            uint32_t full_mask, bool lane_stores, uint32_t *rows, int row_words,
                                            int &d_opt) {
-    constexpr int C = 64 / G;
+    constexpr int C = 32 * NW / G;
     constexpr int PPW = 32 / G;
     const bool full = (full_mask >> tbl) & 1u;
     const int colbase = (G - 1 - l) * C;
-    uint32_t P0[2], P1[2], T0, T1;
-    load32(pseq, pblk, (int64_t)pj, P0[0], P1[0]);
-    load32(pseq, pblk, (int64_t)pj + 32, P0[1], P1[1]);
+    uint32_t P0[NW], P1[NW], mm[NW], T0, T1;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+        load32(pseq, pblk, (int64_t)pj + 32 * w, P0[w], P1[w]);
+        mm[w] = prefix_mask(mw - 32 * w);
+    }
     load32(tseq, tblk, (int64_t)ti + colbase, T0, T1);
     const int real_cols = nw - colbase;
-    uint32_t FX0[C], FX1[C];  // X of the next row, words 0 and 1
-    const uint32_t mm0 = prefix_mask(mw), mm1 = prefix_mask(mw - 32);
+    uint32_t FX[C][NW];  // X of the next row
 #pragma unroll
-    for (int c = 0; c < C; ++c) {
-        FX0[c] = mm0;
-        FX1[c] = mm1;
-    }
+    for (int c = 0; c < C; ++c)
+#pragma unroll
+        for (int w = 0; w < NW; ++w) FX[c][w] = mm[w];
     uint32_t fdone = tbl_all & ~full_mask;
-    uint32_t bot0 = 0u, bot1 = 0u;
+    uint32_t bot[NW];
+#pragma unroll
+    for (int w = 0; w < NW; ++w) bot[w] = 0u;
     for (int st = 0; fdone != tbl_all; ++st) {
         const int d = st - l;
         const bool ddone = (fdone >> tbl) & 1u;
-        const uint32_t v0 = __shfl_up_sync(kFull, bot0, 1);
-        const uint32_t v1 = __shfl_up_sync(kFull, bot1, 1);
-        uint32_t pR0 = (l == 0) ? prefix_mask(mw - d) : v0;
-        uint32_t pR1 = (l == 0) ? prefix_mask(mw - d - 32) : v1;
+        uint32_t pR[NW], pS[NW];
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+            const uint32_t v = __shfl_up_sync(kFull, bot[w], 1);
+            pR[w] = (l == 0) ? prefix_mask(mw - d - 32 * w) : v;
+        }
         bool found = false;
         if (!ddone && d >= 0 && d <= k) {
-            uint32_t pS0 = __funnelshift_l(pR1, pR0, 1), pS1 = pR1 << 1;
+            shl1<NW>(pR, pS);
             uint32_t *rowp = rows + (int64_t)d * row_words;
 #pragma unroll
             for (int c = C - 1; c >= 0; --c) {
-                // PM[text[i]] of both words from the pattern planes
+                // PM[text[i]] from the pattern planes
                 const uint32_t m0 = 0u - ((T0 >> (31 - c)) & 1u);
                 const uint32_t m1 = 0u - ((T1 >> (31 - c)) & 1u);
                 const bool real = c < real_cols;
-                const uint32_t pm0 = real ? ((P0[0] ^ m0) | (P1[0] ^ m1)) : kFull;
-                const uint32_t pm1 = real ? ((P0[1] ^ m0) | (P1[1] ^ m1)) : kFull;
-                const uint32_t R0 = FX0[c] & (pS0 | pm0), R1 = FX1[c] & (pS1 | pm1);
-                const uint32_t S0 = __funnelshift_l(R1, R0, 1), S1 = R1 << 1;
-                if (lane_stores) *reinterpret_cast<uint2 *>(rowp + c * 2 * PPW) = make_uint2(R0, R1);
-                FX0[c] = S0 & pR0 & pS0;
-                FX1[c] = S1 & pR1 & pS1;
-                pR0 = R0;
-                pR1 = R1;
-                pS0 = S0;
-                pS1 = S1;
+                uint32_t R[NW], S[NW];
+#pragma unroll
+                for (int w = 0; w < NW; ++w) {
+                    const uint32_t pm = real ? ((P0[w] ^ m0) | (P1[w] ^ m1)) : kFull;
+                    R[w] = FX[c][w] & (pS[w] | pm);
+                }
+                shl1<NW>(R, S);
+                if (lane_stores) store_vec<NW, NW>(rowp + c * NW * PPW, R);
+#pragma unroll
+                for (int w = 0; w < NW; ++w) {
+                    FX[c][w] = S[w] & pR[w] & pS[w];
+                    pR[w] = R[w];
+                    pS[w] = S[w];
+                }
             }
-            bot0 = pR0;
-            bot1 = pR1;
-            found = (l == G - 1) && ((pR0 >> 31) == 0u);
+#pragma unroll
+            for (int w = 0; w < NW; ++w) bot[w] = pR[w];
+            found = (l == G - 1) && ((pR[0] >> 31) == 0u);
         }
         const uint32_t fm = __ballot_sync(kFull, found);
         const int dl = st - (G - 1);
@@ -126,57 +173,77 @@ struct BandWindow {
 
 // GenASM-DC of one window for the 32/G pairs of a warp (all 32 lanes take part). Band rows go to
 // `tab` (rows < rcap, shared memory) and `spill` (deeper rows); the traceback lane of each pair
-// stages its 64 bases of text and pattern at `stage` (12 words per pair); windows beyond the band
-// are recomputed at full width into `fb`. On the traceback lane, d_opt gets the window's edit
-// distance (-1: none <= k) and full whether the full-width rows hold it.
-template <int G>
+// stages its text and pattern at `stage` (4 planes x (2 BW + 1) words per pair); windows beyond
+// the band are recomputed at full width into `fb`. On the traceback lane, d_opt gets the
+// window's edit distance (-1: none <= k) and full whether the full-width rows hold it.
+template <int G, int BW>
 __device__ __forceinline__ void band_window_dc(const AlignParams &p, const BandWindow &bw, int l, int g, int tbl,
                                                uint32_t tbl_all, uint32_t *tab, uint32_t *spill, uint32_t *fb,
                                                uint32_t *stage, int &d_opt_out, bool &full_out) {
-    constexpr int WMAX = 64;
+    using T = typename BandT<BW>::T;
+    constexpr int BITS = 32 * BW;
+    constexpr int NW = 2 * BW;  // words of a full-width entry
+    constexpr int WMAX = 64 * BW;
     constexpr int C = WMAX / G;
     constexpr int PPW = 32 / G;
-    constexpr int COLW = PPW;  // words between two columns of one stored band row
-    constexpr int B0 = kBandDiag;
+    constexpr int COLW = PPW * BW;  // words between two columns of one stored band row
+    constexpr int B0 = band_diag<BW>();
     const int k = p.k, ncolp = p.ncol, rcap = p.rcap, rstride = p.rstride;
-    const int dmax = min(k, kBandRows - 1);  // deepest row the band computes
+    const int dmax = min(k, band_rows<BW>() - 1);  // deepest row the band computes
     const int colbase = (G - 1 - l) * C;
     const bool lane_stores = colbase < ncolp;
     const bool active = bw.active;
     const int nw = bw.nw, mw = bw.mw;
     auto band_row = [&](int row) -> uint32_t * {
-        return row < rcap ? tab + row * rstride + g : spill + (row - rcap) * rstride + g;
+        return row < rcap ? tab + (row * rstride + g) * BW : spill + ((row - rcap) * rstride + g) * BW;
     };
 
     // ---- window set-up: band pattern masks and row-0 masks of this lane's columns
-    uint32_t XA[C];   // X of the next row (row 0: bits with j >= m_w cleared)
-    uint32_t PMC[C];  // PMrel[text[i]]
+    T XA[C];   // X of the next row (row 0: bits with j >= m_w cleared)
+    T PMC[C];  // PMrel[text[i]]
     {
-        // pattern planes from pj + colbase - 16: column colbase + c starts c + 1 bits in
-        uint32_t Pa0, Pa1, Pb0, Pb1, T0, T1;
-        load32(bw.pseq, bw.pblk, (int64_t)bw.pj + colbase - 16, Pa0, Pa1);
-        load32(bw.pseq, bw.pblk, (int64_t)bw.pj + colbase + 16, Pb0, Pb1);
+        uint32_t T0, T1;
         load32(bw.tseq, bw.tblk, (int64_t)bw.ti + colbase, T0, T1);
         const int real_cols = nw - colbase;
+        if (BW == 1) {
+            // pattern planes from pj + colbase - 16: column colbase + c starts c + 1 bits in
+            uint32_t Pa0, Pa1, Pb0, Pb1;
+            load32(bw.pseq, bw.pblk, (int64_t)bw.pj + colbase - 16, Pa0, Pa1);
+            load32(bw.pseq, bw.pblk, (int64_t)bw.pj + colbase + 16, Pb0, Pb1);
 #pragma unroll
-        for (int c = 0; c < C; ++c) {
-            const uint32_t m0 = 0u - ((T0 >> (31 - c)) & 1u);
-            const uint32_t m1 = 0u - ((T1 >> (31 - c)) & 1u);
-            const uint32_t w0 = __funnelshift_lc(Pb0, Pa0, c + 1);
-            const uint32_t w1 = __funnelshift_lc(Pb1, Pa1, c + 1);
-            PMC[c] = c < real_cols ? ((w0 ^ m0) | (w1 ^ m1)) : kFull;
-            XA[c] = prefix_mask(mw - (colbase + c) + B0);
+            for (int c = 0; c < C; ++c) {
+                const uint32_t m0 = 0u - ((T0 >> (31 - c)) & 1u);
+                const uint32_t m1 = 0u - ((T1 >> (31 - c)) & 1u);
+                const uint32_t w0 = __funnelshift_lc(Pb0, Pa0, c + 1);
+                const uint32_t w1 = __funnelshift_lc(Pb1, Pa1, c + 1);
+                PMC[c] = (T)(c < real_cols ? ((w0 ^ m0) | (w1 ^ m1)) : kFull);
+                XA[c] = band_prefix(T(0), mw - (colbase + c) + B0);
+            }
+        } else {
+            // pattern planes from pj + colbase - 32: column colbase + c starts c + 1 bits in
+            uint32_t Q0[3], Q1[3];
+#pragma unroll
+            for (int w = 0; w < 3; ++w) load32(bw.pseq, bw.pblk, (int64_t)bw.pj + colbase - 32 + 32 * w, Q0[w], Q1[w]);
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                const uint32_t m0 = 0u - ((T0 >> (31 - c)) & 1u);
+                const uint32_t m1 = 0u - ((T1 >> (31 - c)) & 1u);
+                const uint32_t h = (__funnelshift_l(Q0[1], Q0[0], c + 1) ^ m0) | (__funnelshift_l(Q1[1], Q1[0], c + 1) ^ m1);
+                const uint32_t o = (__funnelshift_l(Q0[2], Q0[1], c + 1) ^ m0) | (__funnelshift_l(Q1[2], Q1[1], c + 1) ^ m1);
+                PMC[c] = c < real_cols ? (T)(((uint64_t)h << 32) | o) : ~T(0);
+                XA[c] = band_prefix(T(0), mw - (colbase + c) + B0);
+            }
         }
         if (active && l == G - 1) {
 #pragma unroll
-            for (int w = 0; w <= 2; ++w) {
+            for (int w = 0; w <= NW; ++w) {
                 uint32_t a, b;
                 load32(bw.tseq, bw.tblk, (int64_t)bw.ti + 32 * w, a, b);
                 stage[w] = a;
-                stage[3 + w] = b;
+                stage[(NW + 1) + w] = b;
                 load32(bw.pseq, bw.pblk, (int64_t)bw.pj + 32 * w, a, b);
-                stage[6 + w] = a;
-                stage[9 + w] = b;
+                stage[2 * (NW + 1) + w] = a;
+                stage[3 * (NW + 1) + w] = b;
             }
         }
     }
@@ -184,26 +251,33 @@ __device__ __forceinline__ void band_window_dc(const AlignParams &p, const BandW
     // ---- GenASM-DC in the band, rows in a pipeline over the lanes of each pair
     uint32_t done_mask = __ballot_sync(kFull, l == G - 1 && !active);
     int d_opt = -1;
-    uint32_t bottom = 0u;
+    T bottom = T(0);
     for (int st = 0; done_mask != tbl_all; ++st) {
         const int d = st - l;
         const bool dc_done = (done_mask >> tbl) & 1u;
-        const uint32_t v = __shfl_up_sync(kFull, bottom, 1);
-        // lane 0 starts from column 64, whose bits j < m_w - d are 1
-        uint32_t pR = (l == 0) ? prefix_mask(mw - d - WMAX + B0) : v;
+        T v;
+        if (BW == 1) {
+            v = (T)__shfl_up_sync(kFull, (uint32_t)bottom, 1);
+        } else {
+            const uint32_t hi = __shfl_up_sync(kFull, (uint32_t)((uint64_t)bottom >> 32), 1);
+            const uint32_t lo = __shfl_up_sync(kFull, (uint32_t)bottom, 1);
+            v = (T)(((uint64_t)hi << 32) | lo);
+        }
+        // lane 0 starts from column W_max, whose bits j < m_w - d are 1
+        T pR = (l == 0) ? band_prefix(T(0), mw - d - WMAX + B0) : v;
         bool found = false;
         if (!dc_done && d >= 0 && d <= dmax) {
             uint32_t *rowp = band_row(d) + colbase * COLW;
 #pragma unroll
             for (int c = C - 1; c >= 0; --c) {
-                const uint32_t R = XA[c] & (pR | PMC[c]);
-                if (lane_stores) rowp[c * COLW] = R;
+                const T R = XA[c] & (pR | PMC[c]);
+                if (lane_stores) store_band(rowp + c * COLW, R);
                 // next row: S = V[i+1][d], D = V[i+1][d] >> 1, I = V[i][d] << 1 (1s shifted in)
-                XA[c] = pR & __funnelshift_r(pR, kFull, 1) & __funnelshift_l(kFull, R, 1);
+                XA[c] = pR & shr1_fill(pR) & shl1_fill(R);
                 pR = R;
             }
             bottom = pR;
-            found = (l == G - 1) && (((pR >> (31 - B0)) & 1u) == 0u);
+            found = (l == G - 1) && (((pR >> (BITS - 1 - B0)) & T(1)) == T(0));
         }
         const uint32_t fmask = __ballot_sync(kFull, found);
         const int dl = st - (G - 1);  // row finished by the traceback lane
@@ -212,12 +286,12 @@ __device__ __forceinline__ void band_window_dc(const AlignParams &p, const BandW
         if (dl >= dmax) done_mask = tbl_all;
     }
 
-    // ---- windows beyond the band: full-width DC (Algorithm 1 on two words)
-    const uint32_t full_mask = __ballot_sync(kFull, l == G - 1 && active && d_opt < 0 && k >= kBandRows);
+    // ---- windows beyond the band: full-width DC (Algorithm 1 on NW words)
+    const uint32_t full_mask = __ballot_sync(kFull, l == G - 1 && active && d_opt < 0 && k >= band_rows<BW>());
     const bool full = (full_mask >> tbl) & 1u;
     if (full_mask)
-        full_width_dc<G>(bw.pseq, bw.pblk, bw.pj, bw.tseq, bw.tblk, bw.ti, nw, mw, k, l, tbl, tbl_all, full_mask,
-                         lane_stores, fb + ((int64_t)colbase * PPW + g) * 2, ncolp * PPW * 2, d_opt);
+        full_width_dc<G, NW>(bw.pseq, bw.pblk, bw.pj, bw.tseq, bw.tblk, bw.ti, nw, mw, k, l, tbl, tbl_all, full_mask,
+                             lane_stores, fb + ((int64_t)colbase * PPW + g) * NW, ncolp * PPW * NW, d_opt);
     d_opt_out = d_opt;
     full_out = full;
 }
@@ -227,19 +301,20 @@ __device__ __forceinline__ void band_window_dc(const AlignParams &p, const BandW
 // a warp of G-lane pairs (pair index g) in `tab` / `spill`, its full-width rows in `fb`, its
 // staged bases at `stage`. Emits the window's CIGAR runs, counts the window in the statistics and
 // advances the cursors by what it consumed.
-template <int G>
+template <int G, int BW>
 __device__ __forceinline__ void band_window_tb(const AlignParams &p, uint32_t mask, bool active, int d_opt,
                                                bool full, int nw, int mw, const uint32_t *stage,
                                                const uint32_t *tab, const uint32_t *spill, const uint32_t *fb,
                                                int g, CigarOut &out, int &ti, int &pj, bool &failed,
                                                int64_t &st_rows, int64_t &st_cells, int32_t &st_windows) {
+    constexpr int NW = 2 * BW;
     constexpr int PPW = 32 / G;
-    constexpr int COLW = PPW;
-    constexpr int B0 = kBandDiag;
+    constexpr int COLW = PPW * BW;
+    constexpr int B0 = band_diag<BW>();
     const int L = p.W - p.O, rcap = p.rcap, rstride = p.rstride;
-    const int fb_row = p.ncol * PPW * 2;
+    const int fb_row = p.ncol * PPW * NW;
     auto band_row = [&](int row) -> const uint32_t * {
-        return row < rcap ? tab + row * rstride + g : spill + (row - rcap) * rstride + g;
+        return row < rcap ? tab + (row * rstride + g) * BW : spill + ((row - rcap) * rstride + g) * BW;
     };
     const bool tb_live = active && d_opt >= 0;
     if (active) st_windows += 1;
@@ -248,18 +323,27 @@ __device__ __forceinline__ void band_window_tb(const AlignParams &p, uint32_t ma
         st_rows += d_opt + 1;
         st_cells += (int64_t)(d_opt + 1) * nw;
     }
-    const uint64_t qT0 = ((uint64_t)stage[0] << 32) | stage[1];
-    const uint64_t qT1 = ((uint64_t)stage[3] << 32) | stage[4];
-    const uint64_t qP0 = ((uint64_t)stage[6] << 32) | stage[7];
-    const uint64_t qP1 = ((uint64_t)stage[9] << 32) | stage[10];
+    const uint32_t *T0s = stage, *T1s = stage + (NW + 1);
+    const uint32_t *P0s = stage + 2 * (NW + 1), *P1s = stage + 3 * (NW + 1);
+    // windows of 64 bases: the four planes in 64-bit registers (a match run never reaches past
+    // the window, so the zeros shifted in are never compared); wider windows read the stage
+    uint64_t qT0 = 0, qT1 = 0, qP0 = 0, qP1 = 0;
+    if (BW == 1) {
+        qT0 = ((uint64_t)T0s[0] << 32) | T0s[1];
+        qT1 = ((uint64_t)T1s[0] << 32) | T1s[1];
+        qP0 = ((uint64_t)P0s[0] << 32) | P0s[1];
+        qP1 = ((uint64_t)P1s[0] << 32) | P1s[1];
+    }
     int i = 0, j = 0, d = d_opt;
     bool going = tb_live && (j < mw && i < L && j < L);
     while (__any_sync(mask, going)) {
         if (going) {
             const int lim = min(min(nw - i, mw - j), min(L - i, L - j));
-            // a match run never reaches past the window: the zeros shifted in are never compared
-            const uint32_t x = (uint32_t)(((qT0 << i) ^ (qP0 << j)) >> 32) |
-                               (uint32_t)(((qT1 << i) ^ (qP1 << j)) >> 32);
+            uint32_t x;
+            if (BW == 1)
+                x = (uint32_t)(((qT0 << i) ^ (qP0 << j)) >> 32) | (uint32_t)(((qT1 << i) ^ (qP1 << j)) >> 32);
+            else
+                x = (stage_ext(T0s, i) ^ stage_ext(P0s, j)) | (stage_ext(T1s, i) ^ stage_ext(P1s, j));
             const int z = __clz(x);
             const int run = min(z, lim);
             out.emit_maybe(kOpEq, run);
@@ -277,30 +361,29 @@ __device__ __forceinline__ void band_window_tb(const AlignParams &p, uint32_t ma
                 const int lim_r = mw - (d - 1);  // bits < lim_r of the right column R[n][d-1] are 1
                 const int r = d - 1;
                 const bool ld1 = tx && i + 1 < nw;
-                // entries (i+1, d-1) and (i, d-1) as 64-bit words; t1 = bits j, j+1 of the
-                // first, r0b = bit j+1 of the second
-                uint64_t q1, q0;
-                int s1, s0;
+                // t1 = bits j, j+1 of entry (i+1, d-1); r0b = bit j+1 of entry (i, d-1)
+                uint32_t t1, r0b;
                 if (!full) {
                     const uint32_t *rp = band_row(r) + i * COLW;
-                    const uint32_t v1 = ld1 ? rp[COLW] : 0u;
-                    const uint32_t v0 = tx ? rp[0] : 0u;
-                    const int kk = j - i + B0;  // band bit of (i, j); 0..30 on the path
-                    q1 = (1ull << 63) | ((uint64_t)v1 << 31);  // band bit kk-1 at position kk
-                    q0 = (uint64_t)v0 << 32;
-                    s1 = kk;
-                    s0 = kk + 1;
+                    const int kk = j - i + B0;  // band bit of (i, j); 0..2 B0 on the path
+                    if (BW == 1) {
+                        const uint32_t v1 = ld1 ? rp[COLW] : 0u;
+                        const uint32_t v0 = tx ? rp[0] : 0u;
+                        const uint64_t q1 = (1ull << 63) | ((uint64_t)v1 << 31);  // band bit kk-1 at position kk
+                        t1 = (uint32_t)((q1 << kk) >> 62);
+                        r0b = (uint32_t)((((uint64_t)v0 << 32) << (kk + 1)) >> 63);
+                    } else {
+                        const uint64_t v1 = ld1 ? load_band64(rp + COLW) : 0ull;
+                        const uint64_t v0 = tx ? load_band64(rp) : 0ull;
+                        const uint32_t lo = kk == 0 ? 1u : (uint32_t)((v1 >> (64 - kk)) & 1ull);  // bit kk-1
+                        t1 = (lo << 1) | (uint32_t)((v1 >> (63 - kk)) & 1ull);
+                        r0b = (uint32_t)((v0 >> (62 - kk)) & 1ull);
+                    }
                 } else {
-                    const uint2 *fp = reinterpret_cast<const uint2 *>(fb + (int64_t)r * fb_row) + (i * PPW + g);
-                    const uint2 a = ld1 ? fp[PPW] : make_uint2(0u, 0u);
-                    const uint2 b = tx ? fp[0] : make_uint2(0u, 0u);
-                    q1 = ((uint64_t)a.x << 32) | a.y;
-                    q0 = ((uint64_t)b.x << 32) | b.y;
-                    s1 = j;
-                    s0 = j + 1;
+                    const uint32_t *fp = fb + (int64_t)r * fb_row + (i * PPW + g) * NW;
+                    t1 = ld1 ? entry_bits2<NW>(fp + PPW * NW, j) : 0u;
+                    r0b = tx ? (entry_bits2<NW>(fp, j) & 1u) : 0u;
                 }
-                const uint32_t t1 = (uint32_t)((q1 << s1) >> 62);
-                const uint32_t r0b = (uint32_t)((q0 << (s0 & 63)) >> 63);  // s0 == 64 only when !j1
                 const uint32_t r1j = ld1 ? (t1 >> 1) : (j < lim_r ? 1u : 0u);
                 const uint32_t r1j1 = !j1 ? 0u : (ld1 ? (t1 & 1u) : (j + 1 < lim_r ? 1u : 0u));
                 const uint32_t r0j1 = !j1 ? 0u : (tx ? r0b : (j + 1 < lim_r ? 1u : 0u));
@@ -332,10 +415,11 @@ __device__ __forceinline__ void band_window_tb(const AlignParams &p, uint32_t ma
     }
 }
 
-template <int G>
-__global__ void __launch_bounds__(64, BandMinBlocks<G>::value) align_band_kernel(const AlignParams p) {
+template <int G, int BW>
+__global__ void __launch_bounds__(64, (BandMinBlocks<G, BW>::value)) align_band_kernel(const AlignParams p) {
     constexpr int PPW = 32 / G;
-    static_assert((64 / G) * G == 64 && 64 / G <= 32 && 32 % G == 0, "unsupported shape");
+    constexpr int NW = 2 * BW;
+    static_assert((64 * BW / G) * G == 64 * BW && 64 * BW / G <= 32 && 32 % G == 0, "unsupported shape");
 
     extern __shared__ __align__(16) uint32_t smem[];
     const int lane = threadIdx.x & 31;
@@ -349,11 +433,11 @@ __global__ void __launch_bounds__(64, BandMinBlocks<G>::value) align_band_kernel
     for (int q = 0; q < PPW; ++q) tbl_all |= 1u << (q * G + G - 1);
 
     uint32_t *tab = smem + (int64_t)wib * p.smem_words_per_warp;
-    uint32_t *stage = tab + p.table_words_per_warp + g * (4 * 3);
+    uint32_t *stage = tab + p.table_words_per_warp + g * (4 * (NW + 1));
     const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
     const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
     uint32_t *spill = p.spill + gw * p.spill_words_per_pair;
-    // full-width fallback rows: [row][column][pair][2 words]
+    // full-width fallback rows: [row][column][pair][NW words]
     uint32_t *fb = p.fb ? p.fb + gw * p.fb_words_per_warp : nullptr;
 
     Slot s;
@@ -381,11 +465,11 @@ __global__ void __launch_bounds__(64, BandMinBlocks<G>::value) align_band_kernel
         bw.pj = s.pj;
         int d_opt;
         bool full;
-        band_window_dc<G>(p, bw, l, g, tbl, tbl_all, tab, spill, fb, stage, d_opt, full);
+        band_window_dc<G, BW>(p, bw, l, g, tbl, tbl_all, tab, spill, fb, stage, d_opt, full);
         __syncwarp();  // entries written by every lane are visible to the traceback lane
         if (l == G - 1)
-            band_window_tb<G>(p, tbl_all, bw.active, d_opt, full, bw.nw, bw.mw, stage, tab, spill, fb, g, out, s.ti,
-                              s.pj, s.failed, s.st_rows, s.st_cells, s.st_windows);
+            band_window_tb<G, BW>(p, tbl_all, bw.active, d_opt, full, bw.nw, bw.mw, stage, tab, spill, fb, g, out,
+                                  s.ti, s.pj, s.failed, s.st_rows, s.st_cells, s.st_windows);
         slot_window_done<G>(p, s, out, l, tbl);
     }
 }
@@ -551,7 +635,7 @@ __global__ void __launch_bounds__(32 * (kWsDcWarps + 1), 3) align_ws_kernel(cons
             uint32_t *stage = tab + p.table_words_per_warp + g * (4 * 3);
             int d_opt;
             bool full;
-            band_window_dc<G>(p, bw, l, g, tbl, tbl_all, tab, set_scratch(p.spill, p.spill_words_per_pair, w, x),
+            band_window_dc<G, 1>(p, bw, l, g, tbl, tbl_all, tab, set_scratch(p.spill, p.spill_words_per_pair, w, x),
                               set_scratch(p.fb, p.fb_words_per_warp, w, x), stage, d_opt, full);
             if (l == G - 1) {
                 sl.d_opt = d_opt;
@@ -619,7 +703,7 @@ __global__ void __launch_bounds__(32 * (kWsDcWarps + 1), 3) align_ws_kernel(cons
                 out.edits = 0;
             }
             const uint32_t *tab = set_tab(w, x);
-            band_window_tb<G>(p, kFull, active, d_opt, full, nw, mw, tab + p.table_words_per_warp + g * (4 * 3), tab,
+            band_window_tb<G, 1>(p, kFull, active, d_opt, full, nw, mw, tab + p.table_words_per_warp + g * (4 * 3), tab,
                               set_scratch(p.spill, p.spill_words_per_pair, w, x),
                               set_scratch(p.fb, p.fb_words_per_warp, w, x), g, out, ti, pj, failed, st_rows, st_cells,
                               st_windows);
@@ -673,47 +757,54 @@ cudaError_t occupancy_ws_kernel(size_t smem, int *per_sm) {
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, align_ws_kernel, 32 * (kWsDcWarps + 1), smem);
 }
 
-template <int G>
+template <int G, int BW>
 cudaError_t launch_g(const AlignParams &p, int wpb, int blocks, size_t smem, cudaStream_t st) {
-    align_band_kernel<G><<<blocks, 32 * wpb, smem, st>>>(p);
+    align_band_kernel<G, BW><<<blocks, 32 * wpb, smem, st>>>(p);
     return cudaGetLastError();
 }
 
 // The dynamic shared-memory limit of a kernel is only ever raised: one call may launch the same
 // instantiation with two shapes (the long-pair launch and the main one).
-template <int G>
+template <int G, int BW>
 cudaError_t occupancy_g(int wpb, size_t smem, int *per_sm) {
     cudaFuncAttributes a;
-    cudaError_t e = cudaFuncGetAttributes(&a, align_band_kernel<G>);
+    cudaError_t e = cudaFuncGetAttributes(&a, align_band_kernel<G, BW>);
     if (e != cudaSuccess) return e;
     if ((size_t)a.maxDynamicSharedSizeBytes < smem &&
-        (e = cudaFuncSetAttribute(align_band_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+        (e = cudaFuncSetAttribute(align_band_kernel<G, BW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
             cudaSuccess)
         return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, align_band_kernel<G>, 32 * wpb, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, align_band_kernel<G, BW>, 32 * wpb, smem);
 }
 
 }  // namespace kern
 
-cudaError_t launch_align_band(const AlignParams &p, int lanes, int wpb, int blocks, size_t smem, cudaStream_t st) {
-    switch (lanes) {
-        case 2: return kern::launch_g<2>(p, wpb, blocks, smem, st);
-        case 4: return kern::launch_g<4>(p, wpb, blocks, smem, st);
-        case 8: return kern::launch_g<8>(p, wpb, blocks, smem, st);
+cudaError_t launch_align_band(const AlignParams &p, int bw, int lanes, int wpb, int blocks, size_t smem,
+                              cudaStream_t st) {
+    switch (bw * 100 + lanes) {
+        case 102: return kern::launch_g<2, 1>(p, wpb, blocks, smem, st);
+        case 104: return kern::launch_g<4, 1>(p, wpb, blocks, smem, st);
+        case 108: return kern::launch_g<8, 1>(p, wpb, blocks, smem, st);
+        case 208: return kern::launch_g<8, 2>(p, wpb, blocks, smem, st);
+        case 216: return kern::launch_g<16, 2>(p, wpb, blocks, smem, st);
         default: return cudaErrorInvalidValue;
     }
 }
 
-cudaError_t occupancy_band(int lanes, int wpb, size_t smem, int *per_sm) {
-    switch (lanes) {
-        case 2: return kern::occupancy_g<2>(wpb, smem, per_sm);
-        case 4: return kern::occupancy_g<4>(wpb, smem, per_sm);
-        case 8: return kern::occupancy_g<8>(wpb, smem, per_sm);
+cudaError_t occupancy_band(int bw, int lanes, int wpb, size_t smem, int *per_sm) {
+    switch (bw * 100 + lanes) {
+        case 102: return kern::occupancy_g<2, 1>(wpb, smem, per_sm);
+        case 104: return kern::occupancy_g<4, 1>(wpb, smem, per_sm);
+        case 108: return kern::occupancy_g<8, 1>(wpb, smem, per_sm);
+        case 208: return kern::occupancy_g<8, 2>(wpb, smem, per_sm);
+        case 216: return kern::occupancy_g<16, 2>(wpb, smem, per_sm);
         default: return cudaErrorInvalidValue;
     }
 }
 
-bool supported_band(int lanes) { return lanes == 2 || lanes == 4 || lanes == 8; }
+bool supported_band(int bw, int lanes) {
+    return bw == 1 ? (lanes == 2 || lanes == 4 || lanes == 8) : (bw == 2 && (lanes == 8 || lanes == 16));
+}
 
 cudaError_t launch_align_ws(const AlignParams &p, int blocks, size_t smem, cudaStream_t st) {
     return kern::launch_ws_kernel(p, blocks, smem, st);

@@ -18,7 +18,8 @@ bool align_supported(int words, int lanes) {
         case 1: return lanes == 1 || lanes == 2 || lanes == 4;
         case 2: return lanes == 2 || lanes == 4 || lanes == 8;
         case 4: return lanes == 8 || lanes == 16;
-        case 0: return supported_band(lanes);
+        case 0: return supported_band(1, lanes);
+        case 3: return supported_band(2, lanes);
         default: return false;
     }
 }
@@ -234,7 +235,7 @@ namespace {
 // One alignment-kernel launch: which kernel, its shape and its parameters.
 struct LaunchPlan {
     bool band = false, sene = true, ws = false;
-    int words = 0, G = 0, wpb = 1, blocks = 0;
+    int words = 0, bw = 1, G = 0, wpb = 1, blocks = 0;
     size_t smem = 0;
     TableShape ts{};
     AlignParams p{};
@@ -247,19 +248,23 @@ struct LaunchPlan {
 int make_plan(scrooge_ctx *c, const AlignParams &base, bool band, uint32_t flags, DevBuf &spill, DevBuf &fallback,
               int slots, LaunchPlan &out) {
     const int W = base.W, O = base.O, k = base.k;
-    const int words = words_for(W);
+    const int bw = band_words_for(W);
+    // the banded kernels' full-width fallback and staged bases use 2 * bw words
+    const int words = band ? 2 * bw : words_for(W);
     const bool sene = !(flags & SCROOGE_NO_SENE);
     const bool dent = !(flags & SCROOGE_NO_DENT);
-    const KernelConfig kc = c->kcfg[kcfg_index(band ? 0 : words)];
-    // warp-specialised blocks: banded, persistent, four lanes per pair, not the long-pair launch
-    const bool ws = band && slots == 0 && (flags & SCROOGE_WARP_SPECIALIZED) && (flags & SCROOGE_PERSISTENT);
+    const KernelConfig kc = c->kcfg[kcfg_index(band ? band_slot_for(W) : words)];
+    // warp-specialised blocks: 64-base bands, persistent, four lanes per pair, not the long-pair launch
+    const bool ws = band && bw == 1 && slots == 0 && (flags & SCROOGE_WARP_SPECIALIZED) &&
+                    (flags & SCROOGE_PERSISTENT);
     int G = ws ? 4 : kc.lanes;
     auto supported = [&](int lanes, int swp) {
         return words == 1 ? supported_w32(lanes, sene, swp)
                           : (words == 2 ? supported_w64(lanes, sene, swp) : supported_w128(lanes, sene, swp));
     };
+    if (band && !supported_band(bw, G)) G = bw == 1 ? 4 : 8;
     TableShape ts = table_shape(W, O, words, G, dent, sene);
-    if (band) ts.swp = 1;  // one 32-bit band word per stored entry
+    if (band) ts.swp = bw;  // one band of bw 32-bit words per stored entry
     if (!band && !supported(G, ts.swp)) {  // the edge-storing ablation exists for the default lane count only
         G = words == 1 ? 2 : (words == 2 ? 4 : 8);
         ts = table_shape(W, O, words, G, dent, sene);
@@ -272,7 +277,7 @@ int make_plan(scrooge_ctx *c, const AlignParams &base, bool band, uint32_t flags
     p.ncol = ts.ncol;
     p.sw = ts.swp;
     p.rstride = row_stride_cells(ts, PPW, chunk);
-    const int rows_needed = band ? std::min(k, kBandRows - 1) + 1 : k + 1;  // rows the kernel may store
+    const int rows_needed = band ? std::min(k, band_rows_for(bw) - 1) + 1 : k + 1;  // rows the kernel may store
     int rcap = std::min(kc.rows, rows_needed);
     const int stage = stage_words_per_warp(words, PPW);
     int wpb = slots > 0 ? 1 : kc.wpb;
@@ -289,7 +294,7 @@ int make_plan(scrooge_ctx *c, const AlignParams &base, bool band, uint32_t flags
     const size_t smem = (size_t)(ws ? kWsSets : wpb) * p.smem_words_per_warp * 4 + meta;
     int per_sm = 0;
     cudaError_t e = ws ? occupancy_ws(smem, &per_sm)
-                  : band ? occupancy_band(G, wpb, smem, &per_sm)
+                  : band ? occupancy_band(bw, G, wpb, smem, &per_sm)
                          : (words == 1 ? occupancy_w32(G, sene, ts.swp, wpb, smem, &per_sm)
                                        : (words == 2 ? occupancy_w64(G, sene, ts.swp, wpb, smem, &per_sm)
                                                      : occupancy_w128(G, sene, ts.swp, wpb, smem, &per_sm)));
@@ -309,7 +314,7 @@ int make_plan(scrooge_ctx *c, const AlignParams &base, bool band, uint32_t flags
     p.fb = nullptr;
     p.fb_words_per_warp = 0;
     if (band) {
-        p.fb_words_per_warp = band_fallback_words(k, ts.ncol, PPW);
+        p.fb_words_per_warp = band_fallback_words(k, ts.ncol, PPW, bw);
         if (p.fb_words_per_warp > 0) {
             if ((rc = ensure(c, fallback, (size_t)blocks * sets * (size_t)p.fb_words_per_warp * 4,
                              "full-width fallback scratch")))
@@ -318,6 +323,7 @@ int make_plan(scrooge_ctx *c, const AlignParams &base, bool band, uint32_t flags
         }
     }
     out.band = band;
+    out.bw = bw;
     out.ws = ws;
     out.sene = sene;
     out.words = words;
@@ -332,7 +338,7 @@ int make_plan(scrooge_ctx *c, const AlignParams &base, bool band, uint32_t flags
 
 cudaError_t launch_plan(const LaunchPlan &lp, cudaStream_t st) {
     if (lp.ws) return launch_align_ws(lp.p, lp.blocks, lp.smem, st);
-    if (lp.band) return launch_align_band(lp.p, lp.G, lp.wpb, lp.blocks, lp.smem, st);
+    if (lp.band) return launch_align_band(lp.p, lp.bw, lp.G, lp.wpb, lp.blocks, lp.smem, st);
     switch (lp.words) {
         case 1: return launch_align_w32(lp.p, lp.G, lp.sene, lp.ts.swp, lp.wpb, lp.blocks, lp.smem, st);
         case 2: return launch_align_w64(lp.p, lp.G, lp.sene, lp.ts.swp, lp.wpb, lp.blocks, lp.smem, st);
@@ -668,10 +674,10 @@ int scrooge_autotune(scrooge_ctx *c, const uint32_t *texts, const int64_t *text_
     if (!c || n_pairs < 1 || repeats < 1) return SCROOGE_E_INVAL;
     if (W < 1 || W > 128) return fail(c, SCROOGE_E_INVAL, "W=%d outside 1..128", W);
     const int words = words_for(W);
-    const int ix = kcfg_index(use_band(W, flags) ? 0 : words);
+    const int ix = kcfg_index(use_band(W, flags) ? band_slot_for(W) : words);
     const KernelConfig saved = c->kcfg[ix];
     const int32_t saved_class = c->heavy_class;
-    const int lanes_opts[4][3] = {{1, 2, 4}, {2, 4, 8}, {8, 16, 0}, {2, 4, 8}};
+    const int lanes_opts[5][3] = {{1, 2, 4}, {2, 4, 8}, {8, 16, 0}, {2, 4, 8}, {8, 16, 0}};
     const int rows_opts[] = {1, 2, 3, 4, 6, 8, 10, 12, 16, 20};
     const int wpb_opts[] = {1, 2};
     const int classes[] = {16, 15, 14, 13, 12, 11, 10, 0};

@@ -30,8 +30,9 @@ struct scrooge_ctx {
     int sm_count = 0;
     size_t smem_optin = 0;
     std::string err;
-    // full-width kernels of 1, 2, 4 words, then the banded kernel (autotuned on GB300)
-    scrooge::KernelConfig kcfg[4] = {{2, 8, 2}, {4, 4, 2}, {8, 8, 2}, {4, 8, 2}};
+    // full-width kernels of 1, 2, 4 words, then the banded kernels of 64- and 128-base windows
+    // (autotuned on GB300)
+    scrooge::KernelConfig kcfg[5] = {{2, 8, 2}, {4, 4, 2}, {8, 8, 2}, {4, 8, 2}, {8, 6, 2}};
     int fail_allocs = 0;  // testing hook: fail the next N device allocations
     scrooge::DevBuf spill, status, fallback, spill2, spill3, fallback2;
     // learned launches: pairs in load classes >= heavy_class run on the full-width kernel, pairs in
@@ -79,9 +80,10 @@ inline int cuda_fail(scrooge_ctx *c, cudaError_t e, const char *what) {
     return fail(c, SCROOGE_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-// words 1, 2, 4: full-width kernels; 0: the banded kernel
+// settings slots: 1, 2, 4 = the full-width kernels of that many words; 0 = the banded kernel of
+// 33..64-base windows; 3 = the banded kernel of 65..128-base windows
 inline int kcfg_index(int words) {
-    return words == 1 ? 0 : (words == 2 ? 1 : (words == 4 ? 2 : (words == 0 ? 3 : -1)));
+    return words == 1 ? 0 : (words == 2 ? 1 : (words == 4 ? 2 : (words == 0 ? 3 : (words == 3 ? 4 : -1))));
 }
 
 // Grow a device buffer to at least `bytes` (contents are not kept).
@@ -114,10 +116,14 @@ inline void release(DevBuf &b) {
 
 inline int words_for(int W) { return W <= 32 ? 1 : (W <= 64 ? 2 : 4); }
 
-// The banded kernel serves windows of 33..64 bases with SENE and ET on.
+// The banded kernels serve windows of 33..128 bases with SENE and ET on.
 inline bool use_band(int W, uint32_t flags) {
-    return W > 32 && W <= 64 && !(flags & (SCROOGE_NO_SENE | SCROOGE_NO_ET | SCROOGE_NO_BAND));
+    return W > 32 && W <= 128 && !(flags & (SCROOGE_NO_SENE | SCROOGE_NO_ET | SCROOGE_NO_BAND));
 }
+
+// band words of the banded kernel for windows of W bases; its settings slot
+inline int band_words_for(int W) { return W > 64 ? 2 : 1; }
+inline int band_slot_for(int W) { return W > 64 ? 3 : 0; }
 
 // Order of the pairs by predicted load (learn_api.cu): features, MLP, bucket
 // keys, stable sort; writes ctx->l_order. Device pointers; asynchronous.

@@ -110,12 +110,18 @@ cudaError_t launch_align_w128(const AlignParams &, int lanes, bool sene, int swp
 cudaError_t occupancy_w32(int lanes, bool sene, int swp, int wpb, size_t smem, int *blocks_per_sm);
 cudaError_t occupancy_w64(int lanes, bool sene, int swp, int wpb, size_t smem, int *blocks_per_sm);
 cudaError_t occupancy_w128(int lanes, bool sene, int swp, int wpb, size_t smem, int *blocks_per_sm);
-// Banded kernel for windows of 64 bases (align_band.cu): lanes 2, 4 or 8.
-constexpr int kBandDiag = 15;  // band bit of the main diagonal j == i
-constexpr int kBandRows = 16;  // rows d = 0..15 are exact inside the 32-bit band
-cudaError_t launch_align_band(const AlignParams &, int lanes, int wpb, int blocks, size_t smem, cudaStream_t);
-cudaError_t occupancy_band(int lanes, int wpb, size_t smem, int *blocks_per_sm);
-bool supported_band(int lanes);
+// Banded kernels (align_band.cu): a band of 32 * bw diagonals per entry, bw = 1 for windows of
+// 33..64 bases (lanes 2, 4 or 8) and bw = 2 for 65..128 bases (lanes 8 or 16). Rows d < 16 * bw
+// are exact inside the band; other windows are recomputed at full width (2 * bw words).
+inline int band_rows_for(int bw) { return 16 * bw; }
+cudaError_t launch_align_band(const AlignParams &, int bw, int lanes, int wpb, int blocks, size_t smem,
+                              cudaStream_t);
+cudaError_t occupancy_band(int bw, int lanes, int wpb, size_t smem, int *blocks_per_sm);
+bool supported_band(int bw, int lanes);
+// words of the full-width fallback region of one warp of a banded kernel
+inline int64_t band_fallback_words(int k, int ncol, int ppw, int bw) {
+    return k >= band_rows_for(bw) ? (int64_t)(k + 1) * ncol * ppw * 2 * bw : 0;
+}
 // Warp-specialised banded kernel (align_band.cu): blocks of 4 DC warps (4 lanes per pair, two
 // sets of 8 pairs each) and one traceback warp; persistent launches only. Shared memory per block:
 // 8 sets x smem_words_per_warp words, then ws_meta_bytes().
@@ -123,10 +129,6 @@ constexpr int kWsSets = 8;
 cudaError_t launch_align_ws(const AlignParams &, int blocks, size_t smem, cudaStream_t);
 cudaError_t occupancy_ws(size_t smem, int *blocks_per_sm);
 size_t ws_meta_bytes();
-// words of the full-width fallback region of one warp of the banded kernel
-inline int64_t band_fallback_words(int k, int ncol, int ppw) {
-    return k >= kBandRows ? (int64_t)(k + 1) * ncol * ppw * 2 : 0;
-}
 bool supported_w32(int lanes, bool sene, int swp);
 bool supported_w64(int lanes, bool sene, int swp);
 bool supported_w128(int lanes, bool sene, int swp);

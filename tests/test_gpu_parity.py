@@ -46,9 +46,11 @@ def test_tiny_windows_full(ctx):
 def _kernels(W):
     """(settings slot, extra flags, label) of every kernel that serves windows of W bases."""
     words = 1 if W <= 32 else (2 if W <= 64 else 4)
-    out = [(words, sc.SCROOGE_NO_BAND if words == 2 else 0, f"full{words}")]
+    out = [(words, sc.SCROOGE_NO_BAND if words > 1 else 0, f"full{words}")]
     if words == 2:
-        out.append((0, 0, "band"))
+        out.append((0, 0, "band64"))
+    if words == 4:
+        out.append((3, 0, "band128"))
     return out
 
 
@@ -57,14 +59,14 @@ def test_random_edge_cases_all_lane_configs(ctx, W):
     rng = np.random.default_rng(W)
     b = synth.random_pairs(300, max_text=4 * W + 5, max_pattern=4 * W + 5, seed=100 + W)
     for slot, flags, name in _kernels(W):
-        lanes_opts = {1: [1, 2, 4], 2: [2, 4, 8], 4: [8, 16], 0: [2, 4, 8]}[slot]
+        lanes_opts = {1: [1, 2, 4], 2: [2, 4, 8], 4: [8, 16], 0: [2, 4, 8], 3: [8, 16]}[slot]
         saved = sc.scrooge_get_kernel_config(ctx, slot)
         try:
             for lanes in lanes_opts:
                 for rows in (1, 3, 40):
                     sc.scrooge_set_kernel_config(ctx, slot, lanes, rows, 2)
                     O = int(rng.integers(0, W))
-                    for k in (W, max(0, W // 8), 16, 15):
+                    for k in (W, max(0, W // 8), 16, 15, 32, 31):
                         if k > W:
                             continue
                         g, r = _both(ctx, b, W, O, k, flags)
@@ -290,3 +292,22 @@ def test_warp_specialized_few_pairs(ctx):
         r = oracle.align_batch(b, 64, 24, threads=THREADS)
         g = sc.align_host(ctx, sc.PackedBatch(b), 64, 24, None, sc.SCROOGE_PERSISTENT | sc.SCROOGE_WARP_SPECIALIZED)
         assert_same(g, r, label=f"warp-specialised {b.n_pairs} pairs")
+
+
+@pytest.mark.parametrize("lanes", [8, 16])
+def test_band128_windows_and_fallback(ctx, lanes):
+    """The 64-diagonal band for 65..128-base windows, with windows beyond it (d_opt > 31)."""
+    b = synth.concat([synth.fixed_error(20, 0.12, length=2000, seed=101), synth.fixed_error(20, 0.3, length=800, seed=102),
+                      synth.random_pairs(120, 500, 500, seed=103), synth.long_reads(3, seed=104)])
+    pb = sc.PackedBatch(b)
+    saved = sc.scrooge_get_kernel_config(ctx, 3)
+    try:
+        for rows in (1, 6, 32):
+            sc.scrooge_set_kernel_config(ctx, 3, lanes, rows, 2)
+            for W, O, k in ((128, 32, 128), (128, 64, 32), (128, 48, 31), (100, 37, 100), (65, 1, 65), (128, 0, 128),
+                            (128, 127, 40)):
+                g = sc.align_host(ctx, pb, W, O, k)
+                r = oracle.align_batch(b, W, O, k, threads=THREADS)
+                assert_same(g, r, label=f"band128 lanes={lanes} rows={rows} W={W} O={O} k={k}")
+    finally:
+        sc.scrooge_set_kernel_config(ctx, 3, *saved)
