@@ -74,6 +74,10 @@ typedef struct scrooge_ctx scrooge_ctx; /* opaque, owned by the library */
  * which hand windows over through shared-memory barriers (4 lanes per pair,
  * the banded kernel settings' shared-memory rows). */
 #define SCROOGE_WARP_SPECIALIZED (1u << 9)
+/* Implementation choice, never a change of results: windows of 33..64 bases
+ * use the 64-diagonal band (two words per entry, exact for d_opt <= 31)
+ * instead of the 32-diagonal one; lanes_per_pair 4 or 8. */
+#define SCROOGE_WIDE_BAND (1u << 10)
 
 /* CIGAR run encoding: (length << 4) | op, op in SAM codes. */
 #define SCROOGE_OP_I 1  /* base only in the pattern (read): insertion */

@@ -41,6 +41,7 @@ SCROOGE_LEARNED = 1 << 6
 SCROOGE_GRAPH = 1 << 7
 SCROOGE_NO_BAND = 1 << 8
 SCROOGE_WARP_SPECIALIZED = 1 << 9
+SCROOGE_WIDE_BAND = 1 << 10
 
 SCROOGE_OP_I, SCROOGE_OP_D, SCROOGE_OP_EQ, SCROOGE_OP_X = 1, 2, 7, 8
 

@@ -81,7 +81,7 @@ __device__ __forceinline__ uint64_t load_band64(const uint32_t *p) {
 }
 
 // resident blocks of two warps the register budget is sized for
-template <int G, int BW>
+template <int G, int NWW, int BW>
 struct BandMinBlocks {
     static constexpr int value = BW == 2 ? 6 : (G == 8 ? 12 : (G == 4 ? 8 : 6));
 };
@@ -176,14 +176,14 @@ struct BandWindow {
 // stages its text and pattern at `stage` (4 planes x (2 BW + 1) words per pair); windows beyond
 // the band are recomputed at full width into `fb`. On the traceback lane, d_opt gets the
 // window's edit distance (-1: none <= k) and full whether the full-width rows hold it.
-template <int G, int BW>
+template <int G, int NWW, int BW>
 __device__ __forceinline__ void band_window_dc(const AlignParams &p, const BandWindow &bw, int l, int g, int tbl,
                                                uint32_t tbl_all, uint32_t *tab, uint32_t *spill, uint32_t *fb,
                                                uint32_t *stage, int &d_opt_out, bool &full_out) {
     using T = typename BandT<BW>::T;
     constexpr int BITS = 32 * BW;
-    constexpr int NW = 2 * BW;  // words of a full-width entry
-    constexpr int WMAX = 64 * BW;
+    constexpr int NW = NWW;  // words of a full-width entry (windows of up to 32 NW bases)
+    constexpr int WMAX = 32 * NWW;
     constexpr int C = WMAX / G;
     constexpr int PPW = 32 / G;
     constexpr int COLW = PPW * BW;  // words between two columns of one stored band row
@@ -301,13 +301,13 @@ __device__ __forceinline__ void band_window_dc(const AlignParams &p, const BandW
 // a warp of G-lane pairs (pair index g) in `tab` / `spill`, its full-width rows in `fb`, its
 // staged bases at `stage`. Emits the window's CIGAR runs, counts the window in the statistics and
 // advances the cursors by what it consumed.
-template <int G, int BW>
+template <int G, int NWW, int BW>
 __device__ __forceinline__ void band_window_tb(const AlignParams &p, uint32_t mask, bool active, int d_opt,
                                                bool full, int nw, int mw, const uint32_t *stage,
                                                const uint32_t *tab, const uint32_t *spill, const uint32_t *fb,
                                                int g, CigarOut &out, int &ti, int &pj, bool &failed,
                                                int64_t &st_rows, int64_t &st_cells, int32_t &st_windows) {
-    constexpr int NW = 2 * BW;
+    constexpr int NW = NWW;
     constexpr int PPW = 32 / G;
     constexpr int COLW = PPW * BW;
     constexpr int B0 = band_diag<BW>();
@@ -328,7 +328,7 @@ __device__ __forceinline__ void band_window_tb(const AlignParams &p, uint32_t ma
     // windows of 64 bases: the four planes in 64-bit registers (a match run never reaches past
     // the window, so the zeros shifted in are never compared); wider windows read the stage
     uint64_t qT0 = 0, qT1 = 0, qP0 = 0, qP1 = 0;
-    if (BW == 1) {
+    if (NW == 2) {
         qT0 = ((uint64_t)T0s[0] << 32) | T0s[1];
         qT1 = ((uint64_t)T1s[0] << 32) | T1s[1];
         qP0 = ((uint64_t)P0s[0] << 32) | P0s[1];
@@ -340,7 +340,7 @@ __device__ __forceinline__ void band_window_tb(const AlignParams &p, uint32_t ma
         if (going) {
             const int lim = min(min(nw - i, mw - j), min(L - i, L - j));
             uint32_t x;
-            if (BW == 1)
+            if (NW == 2)
                 x = (uint32_t)(((qT0 << i) ^ (qP0 << j)) >> 32) | (uint32_t)(((qT1 << i) ^ (qP1 << j)) >> 32);
             else
                 x = (stage_ext(T0s, i) ^ stage_ext(P0s, j)) | (stage_ext(T1s, i) ^ stage_ext(P1s, j));
@@ -415,11 +415,11 @@ __device__ __forceinline__ void band_window_tb(const AlignParams &p, uint32_t ma
     }
 }
 
-template <int G, int BW>
-__global__ void __launch_bounds__(64, (BandMinBlocks<G, BW>::value)) align_band_kernel(const AlignParams p) {
+template <int G, int NWW, int BW>
+__global__ void __launch_bounds__(64, (BandMinBlocks<G, NWW, BW>::value)) align_band_kernel(const AlignParams p) {
     constexpr int PPW = 32 / G;
-    constexpr int NW = 2 * BW;
-    static_assert((64 * BW / G) * G == 64 * BW && 64 * BW / G <= 32 && 32 % G == 0, "unsupported shape");
+    constexpr int NW = NWW;
+    static_assert((32 * NWW / G) * G == 32 * NWW && 32 * NWW / G <= 32 && 32 % G == 0, "unsupported shape");
 
     extern __shared__ __align__(16) uint32_t smem[];
     const int lane = threadIdx.x & 31;
@@ -465,10 +465,10 @@ __global__ void __launch_bounds__(64, (BandMinBlocks<G, BW>::value)) align_band_
         bw.pj = s.pj;
         int d_opt;
         bool full;
-        band_window_dc<G, BW>(p, bw, l, g, tbl, tbl_all, tab, spill, fb, stage, d_opt, full);
+        band_window_dc<G, NWW, BW>(p, bw, l, g, tbl, tbl_all, tab, spill, fb, stage, d_opt, full);
         __syncwarp();  // entries written by every lane are visible to the traceback lane
         if (l == G - 1)
-            band_window_tb<G, BW>(p, tbl_all, bw.active, d_opt, full, bw.nw, bw.mw, stage, tab, spill, fb, g, out,
+            band_window_tb<G, NWW, BW>(p, tbl_all, bw.active, d_opt, full, bw.nw, bw.mw, stage, tab, spill, fb, g, out,
                                   s.ti, s.pj, s.failed, s.st_rows, s.st_cells, s.st_windows);
         slot_window_done<G>(p, s, out, l, tbl);
     }
@@ -635,7 +635,7 @@ __global__ void __launch_bounds__(32 * (kWsDcWarps + 1), 3) align_ws_kernel(cons
             uint32_t *stage = tab + p.table_words_per_warp + g * (4 * 3);
             int d_opt;
             bool full;
-            band_window_dc<G, 1>(p, bw, l, g, tbl, tbl_all, tab, set_scratch(p.spill, p.spill_words_per_pair, w, x),
+            band_window_dc<G, 2, 1>(p, bw, l, g, tbl, tbl_all, tab, set_scratch(p.spill, p.spill_words_per_pair, w, x),
                               set_scratch(p.fb, p.fb_words_per_warp, w, x), stage, d_opt, full);
             if (l == G - 1) {
                 sl.d_opt = d_opt;
@@ -703,7 +703,7 @@ __global__ void __launch_bounds__(32 * (kWsDcWarps + 1), 3) align_ws_kernel(cons
                 out.edits = 0;
             }
             const uint32_t *tab = set_tab(w, x);
-            band_window_tb<G, 1>(p, kFull, active, d_opt, full, nw, mw, tab + p.table_words_per_warp + g * (4 * 3), tab,
+            band_window_tb<G, 2, 1>(p, kFull, active, d_opt, full, nw, mw, tab + p.table_words_per_warp + g * (4 * 3), tab,
                               set_scratch(p.spill, p.spill_words_per_pair, w, x),
                               set_scratch(p.fb, p.fb_words_per_warp, w, x), g, out, ti, pj, failed, st_rows, st_cells,
                               st_windows);
@@ -757,53 +757,61 @@ cudaError_t occupancy_ws_kernel(size_t smem, int *per_sm) {
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, align_ws_kernel, 32 * (kWsDcWarps + 1), smem);
 }
 
-template <int G, int BW>
+template <int G, int NWW, int BW>
 cudaError_t launch_g(const AlignParams &p, int wpb, int blocks, size_t smem, cudaStream_t st) {
-    align_band_kernel<G, BW><<<blocks, 32 * wpb, smem, st>>>(p);
+    align_band_kernel<G, NWW, BW><<<blocks, 32 * wpb, smem, st>>>(p);
     return cudaGetLastError();
 }
 
 // The dynamic shared-memory limit of a kernel is only ever raised: one call may launch the same
 // instantiation with two shapes (the long-pair launch and the main one).
-template <int G, int BW>
+template <int G, int NWW, int BW>
 cudaError_t occupancy_g(int wpb, size_t smem, int *per_sm) {
     cudaFuncAttributes a;
-    cudaError_t e = cudaFuncGetAttributes(&a, align_band_kernel<G, BW>);
+    cudaError_t e = cudaFuncGetAttributes(&a, align_band_kernel<G, NWW, BW>);
     if (e != cudaSuccess) return e;
     if ((size_t)a.maxDynamicSharedSizeBytes < smem &&
-        (e = cudaFuncSetAttribute(align_band_kernel<G, BW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+        (e = cudaFuncSetAttribute(align_band_kernel<G, NWW, BW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem)) !=
             cudaSuccess)
         return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, align_band_kernel<G, BW>, 32 * wpb, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, align_band_kernel<G, NWW, BW>, 32 * wpb, smem);
 }
 
 }  // namespace kern
 
-cudaError_t launch_align_band(const AlignParams &p, int bw, int lanes, int wpb, int blocks, size_t smem,
+// Instantiations: (window words, band words, lanes) = (2, 1, 2|4|8), (2, 2, 4|8), (4, 2, 8|16).
+cudaError_t launch_align_band(const AlignParams &p, int nww, int bw, int lanes, int wpb, int blocks, size_t smem,
                               cudaStream_t st) {
-    switch (bw * 100 + lanes) {
-        case 102: return kern::launch_g<2, 1>(p, wpb, blocks, smem, st);
-        case 104: return kern::launch_g<4, 1>(p, wpb, blocks, smem, st);
-        case 108: return kern::launch_g<8, 1>(p, wpb, blocks, smem, st);
-        case 208: return kern::launch_g<8, 2>(p, wpb, blocks, smem, st);
-        case 216: return kern::launch_g<16, 2>(p, wpb, blocks, smem, st);
+    switch (nww * 1000 + bw * 100 + lanes) {
+        case 2102: return kern::launch_g<2, 2, 1>(p, wpb, blocks, smem, st);
+        case 2104: return kern::launch_g<4, 2, 1>(p, wpb, blocks, smem, st);
+        case 2108: return kern::launch_g<8, 2, 1>(p, wpb, blocks, smem, st);
+        case 2204: return kern::launch_g<4, 2, 2>(p, wpb, blocks, smem, st);
+        case 2208: return kern::launch_g<8, 2, 2>(p, wpb, blocks, smem, st);
+        case 4208: return kern::launch_g<8, 4, 2>(p, wpb, blocks, smem, st);
+        case 4216: return kern::launch_g<16, 4, 2>(p, wpb, blocks, smem, st);
         default: return cudaErrorInvalidValue;
     }
 }
 
-cudaError_t occupancy_band(int bw, int lanes, int wpb, size_t smem, int *per_sm) {
-    switch (bw * 100 + lanes) {
-        case 102: return kern::occupancy_g<2, 1>(wpb, smem, per_sm);
-        case 104: return kern::occupancy_g<4, 1>(wpb, smem, per_sm);
-        case 108: return kern::occupancy_g<8, 1>(wpb, smem, per_sm);
-        case 208: return kern::occupancy_g<8, 2>(wpb, smem, per_sm);
-        case 216: return kern::occupancy_g<16, 2>(wpb, smem, per_sm);
+cudaError_t occupancy_band(int nww, int bw, int lanes, int wpb, size_t smem, int *per_sm) {
+    switch (nww * 1000 + bw * 100 + lanes) {
+        case 2102: return kern::occupancy_g<2, 2, 1>(wpb, smem, per_sm);
+        case 2104: return kern::occupancy_g<4, 2, 1>(wpb, smem, per_sm);
+        case 2108: return kern::occupancy_g<8, 2, 1>(wpb, smem, per_sm);
+        case 2204: return kern::occupancy_g<4, 2, 2>(wpb, smem, per_sm);
+        case 2208: return kern::occupancy_g<8, 2, 2>(wpb, smem, per_sm);
+        case 4208: return kern::occupancy_g<8, 4, 2>(wpb, smem, per_sm);
+        case 4216: return kern::occupancy_g<16, 4, 2>(wpb, smem, per_sm);
         default: return cudaErrorInvalidValue;
     }
 }
 
-bool supported_band(int bw, int lanes) {
-    return bw == 1 ? (lanes == 2 || lanes == 4 || lanes == 8) : (bw == 2 && (lanes == 8 || lanes == 16));
+bool supported_band(int nww, int bw, int lanes) {
+    if (nww == 2 && bw == 1) return lanes == 2 || lanes == 4 || lanes == 8;
+    if (nww == 2 && bw == 2) return lanes == 4 || lanes == 8;
+    return nww == 4 && bw == 2 && (lanes == 8 || lanes == 16);
 }
 
 cudaError_t launch_align_ws(const AlignParams &p, int blocks, size_t smem, cudaStream_t st) {

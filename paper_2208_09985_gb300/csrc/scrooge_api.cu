@@ -18,8 +18,8 @@ bool align_supported(int words, int lanes) {
         case 1: return lanes == 1 || lanes == 2 || lanes == 4;
         case 2: return lanes == 2 || lanes == 4 || lanes == 8;
         case 4: return lanes == 8 || lanes == 16;
-        case 0: return supported_band(1, lanes);
-        case 3: return supported_band(2, lanes);
+        case 0: return supported_band(2, 1, lanes);
+        case 3: return supported_band(4, 2, lanes);
         default: return false;
     }
 }
@@ -235,7 +235,7 @@ namespace {
 // One alignment-kernel launch: which kernel, its shape and its parameters.
 struct LaunchPlan {
     bool band = false, sene = true, ws = false;
-    int words = 0, bw = 1, G = 0, wpb = 1, blocks = 0;
+    int words = 0, nww = 2, bw = 1, G = 0, wpb = 1, blocks = 0;
     size_t smem = 0;
     TableShape ts{};
     AlignParams p{};
@@ -248,21 +248,22 @@ struct LaunchPlan {
 int make_plan(scrooge_ctx *c, const AlignParams &base, bool band, uint32_t flags, DevBuf &spill, DevBuf &fallback,
               int slots, LaunchPlan &out) {
     const int W = base.W, O = base.O, k = base.k;
-    const int bw = band_words_for(W);
-    // the banded kernels' full-width fallback and staged bases use 2 * bw words
-    const int words = band ? 2 * bw : words_for(W);
+    // the banded kernels: window words nww (their full-width fallback and staged bases), band words bw
+    const int nww = W > 64 ? 4 : 2;
+    const int bw = (W > 64 || (flags & SCROOGE_WIDE_BAND)) ? 2 : 1;
+    const int words = band ? nww : words_for(W);
     const bool sene = !(flags & SCROOGE_NO_SENE);
     const bool dent = !(flags & SCROOGE_NO_DENT);
     const KernelConfig kc = c->kcfg[kcfg_index(band ? band_slot_for(W) : words)];
     // warp-specialised blocks: 64-base bands, persistent, four lanes per pair, not the long-pair launch
-    const bool ws = band && bw == 1 && slots == 0 && (flags & SCROOGE_WARP_SPECIALIZED) &&
+    const bool ws = band && nww == 2 && bw == 1 && slots == 0 && (flags & SCROOGE_WARP_SPECIALIZED) &&
                     (flags & SCROOGE_PERSISTENT);
     int G = ws ? 4 : kc.lanes;
     auto supported = [&](int lanes, int swp) {
         return words == 1 ? supported_w32(lanes, sene, swp)
                           : (words == 2 ? supported_w64(lanes, sene, swp) : supported_w128(lanes, sene, swp));
     };
-    if (band && !supported_band(bw, G)) G = bw == 1 ? 4 : 8;
+    if (band && !supported_band(nww, bw, G)) G = nww == 2 ? 4 : 8;
     TableShape ts = table_shape(W, O, words, G, dent, sene);
     if (band) ts.swp = bw;  // one band of bw 32-bit words per stored entry
     if (!band && !supported(G, ts.swp)) {  // the edge-storing ablation exists for the default lane count only
@@ -294,7 +295,7 @@ int make_plan(scrooge_ctx *c, const AlignParams &base, bool band, uint32_t flags
     const size_t smem = (size_t)(ws ? kWsSets : wpb) * p.smem_words_per_warp * 4 + meta;
     int per_sm = 0;
     cudaError_t e = ws ? occupancy_ws(smem, &per_sm)
-                  : band ? occupancy_band(bw, G, wpb, smem, &per_sm)
+                  : band ? occupancy_band(nww, bw, G, wpb, smem, &per_sm)
                          : (words == 1 ? occupancy_w32(G, sene, ts.swp, wpb, smem, &per_sm)
                                        : (words == 2 ? occupancy_w64(G, sene, ts.swp, wpb, smem, &per_sm)
                                                      : occupancy_w128(G, sene, ts.swp, wpb, smem, &per_sm)));
@@ -314,7 +315,7 @@ int make_plan(scrooge_ctx *c, const AlignParams &base, bool band, uint32_t flags
     p.fb = nullptr;
     p.fb_words_per_warp = 0;
     if (band) {
-        p.fb_words_per_warp = band_fallback_words(k, ts.ncol, PPW, bw);
+        p.fb_words_per_warp = band_fallback_words(k, ts.ncol, PPW, nww, bw);
         if (p.fb_words_per_warp > 0) {
             if ((rc = ensure(c, fallback, (size_t)blocks * sets * (size_t)p.fb_words_per_warp * 4,
                              "full-width fallback scratch")))
@@ -323,6 +324,7 @@ int make_plan(scrooge_ctx *c, const AlignParams &base, bool band, uint32_t flags
         }
     }
     out.band = band;
+    out.nww = nww;
     out.bw = bw;
     out.ws = ws;
     out.sene = sene;
@@ -338,7 +340,7 @@ int make_plan(scrooge_ctx *c, const AlignParams &base, bool band, uint32_t flags
 
 cudaError_t launch_plan(const LaunchPlan &lp, cudaStream_t st) {
     if (lp.ws) return launch_align_ws(lp.p, lp.blocks, lp.smem, st);
-    if (lp.band) return launch_align_band(lp.p, lp.bw, lp.G, lp.wpb, lp.blocks, lp.smem, st);
+    if (lp.band) return launch_align_band(lp.p, lp.nww, lp.bw, lp.G, lp.wpb, lp.blocks, lp.smem, st);
     switch (lp.words) {
         case 1: return launch_align_w32(lp.p, lp.G, lp.sene, lp.ts.swp, lp.wpb, lp.blocks, lp.smem, st);
         case 2: return launch_align_w64(lp.p, lp.G, lp.sene, lp.ts.swp, lp.wpb, lp.blocks, lp.smem, st);

@@ -121,8 +121,7 @@ inline bool use_band(int W, uint32_t flags) {
     return W > 32 && W <= 128 && !(flags & (SCROOGE_NO_SENE | SCROOGE_NO_ET | SCROOGE_NO_BAND));
 }
 
-// band words of the banded kernel for windows of W bases; its settings slot
-inline int band_words_for(int W) { return W > 64 ? 2 : 1; }
+// the settings slot of the banded kernel for windows of W bases
 inline int band_slot_for(int W) { return W > 64 ? 3 : 0; }
 
 // Order of the pairs by predicted load (learn_api.cu): features, MLP, bucket

@@ -110,17 +110,19 @@ cudaError_t launch_align_w128(const AlignParams &, int lanes, bool sene, int swp
 cudaError_t occupancy_w32(int lanes, bool sene, int swp, int wpb, size_t smem, int *blocks_per_sm);
 cudaError_t occupancy_w64(int lanes, bool sene, int swp, int wpb, size_t smem, int *blocks_per_sm);
 cudaError_t occupancy_w128(int lanes, bool sene, int swp, int wpb, size_t smem, int *blocks_per_sm);
-// Banded kernels (align_band.cu): a band of 32 * bw diagonals per entry, bw = 1 for windows of
-// 33..64 bases (lanes 2, 4 or 8) and bw = 2 for 65..128 bases (lanes 8 or 16). Rows d < 16 * bw
-// are exact inside the band; other windows are recomputed at full width (2 * bw words).
+// Banded kernels (align_band.cu): windows of up to 32 * nww bases, a band of 32 * bw diagonals
+// per entry. (nww, bw) = (2, 1) for windows of 33..64 bases (lanes 2, 4 or 8), (2, 2) for the
+// same windows with the wide band (lanes 4 or 8), (4, 2) for 65..128 bases (lanes 8 or 16).
+// Rows d < 16 * bw are exact inside the band; other windows are recomputed at full width (nww
+// words).
 inline int band_rows_for(int bw) { return 16 * bw; }
-cudaError_t launch_align_band(const AlignParams &, int bw, int lanes, int wpb, int blocks, size_t smem,
+cudaError_t launch_align_band(const AlignParams &, int nww, int bw, int lanes, int wpb, int blocks, size_t smem,
                               cudaStream_t);
-cudaError_t occupancy_band(int bw, int lanes, int wpb, size_t smem, int *blocks_per_sm);
-bool supported_band(int bw, int lanes);
+cudaError_t occupancy_band(int nww, int bw, int lanes, int wpb, size_t smem, int *blocks_per_sm);
+bool supported_band(int nww, int bw, int lanes);
 // words of the full-width fallback region of one warp of a banded kernel
-inline int64_t band_fallback_words(int k, int ncol, int ppw, int bw) {
-    return k >= band_rows_for(bw) ? (int64_t)(k + 1) * ncol * ppw * 2 * bw : 0;
+inline int64_t band_fallback_words(int k, int ncol, int ppw, int nww, int bw) {
+    return k >= band_rows_for(bw) ? (int64_t)(k + 1) * ncol * ppw * nww : 0;
 }
 // Warp-specialised banded kernel (align_band.cu): blocks of 4 DC warps (4 lanes per pair, two
 // sets of 8 pairs each) and one traceback warp; persistent launches only. Shared memory per block:

@@ -311,3 +311,23 @@ def test_band128_windows_and_fallback(ctx, lanes):
                 assert_same(g, r, label=f"band128 lanes={lanes} rows={rows} W={W} O={O} k={k}")
     finally:
         sc.scrooge_set_kernel_config(ctx, 3, *saved)
+
+
+@pytest.mark.parametrize("lanes", [4, 8])
+def test_wide_band_for_64_base_windows(ctx, lanes):
+    """SCROOGE_WIDE_BAND: 64 diagonals for 64-base windows, exact for d_opt <= 31, full width beyond."""
+    b = synth.concat([synth.fixed_error(20, 0.25, length=600, seed=111), synth.fixed_error(20, 0.4, length=400, seed=112),
+                      synth.random_pairs(150, 300, 300, seed=113), synth.long_reads(3, seed=114),
+                      synth.short_reads(200, seed=115)])
+    pb = sc.PackedBatch(b)
+    saved = sc.scrooge_get_kernel_config(ctx, 0)
+    try:
+        for rows in (1, 8, 32):
+            sc.scrooge_set_kernel_config(ctx, 0, lanes, rows, 2)
+            for W, O, k in ((64, 24, 64), (64, 24, 32), (64, 24, 31), (64, 33, 16), (48, 10, 48), (64, 0, 64)):
+                for extra in (0, sc.SCROOGE_PERSISTENT):
+                    g = sc.align_host(ctx, pb, W, O, k, sc.SCROOGE_WIDE_BAND | extra)
+                    r = oracle.align_batch(b, W, O, k, threads=THREADS)
+                    assert_same(g, r, label=f"wide band lanes={lanes} rows={rows} W={W} O={O} k={k} flags={extra}")
+    finally:
+        sc.scrooge_set_kernel_config(ctx, 0, *saved)
