@@ -46,7 +46,7 @@ def bind(path: str):
     i32, i64 = ctypes.c_int, ctypes.c_int64
     lib.orc_window_table.argtypes = [P, i32, P, i32, i32, P, P]
     lib.orc_pattern_masks.argtypes = [P, i32, P]
-    lib.orc_align_pair.argtypes = [P, i64, P, i64, i32, i32, i32, P, P, P, i64, P, P, i64, P]
+    lib.orc_align_pair.argtypes = [P, i64, P, i64, i32, i32, i32, P, P, P, i64, P, P, P, i64, P]
     lib.orc_align_batch.argtypes = [P, P, P, P, i64, i32, i32, i32, i32, P, P, P, P, P]
     for f in (lib.orc_window_table, lib.orc_pattern_masks, lib.orc_align_pair, lib.orc_align_batch):
         f.restype = ctypes.c_int
@@ -101,8 +101,10 @@ def align_pair(text, pattern, W: int = 64, O: int = 24, k: int | None = None):
     """Windowed alignment of one pair.
 
     Returns dict(edit_count, text_consumed, cigar (uint32 runs, len << 4 | op),
-    d_opt (per window), status). status 0 = aligned, 1 = some window had no
-    d <= k (edit_count -1), -2 = CIGAR overflow.
+    d_opt (per window), window_edits (per window: edits of its kept
+    traceback, i.e. how many rows it descended below d_opt), status).
+    status 0 = aligned, 1 = some window had no d <= k (edit_count -1),
+    -2 = CIGAR overflow.
     """
     k = W if k is None else k
     t, p = _codes(text), _codes(pattern)
@@ -111,14 +113,17 @@ def align_pair(text, pattern, W: int = 64, O: int = 24, k: int | None = None):
     cig = np.zeros(cap, dtype=np.uint32)
     nwin_cap = m + 1
     dopt = np.full(nwin_cap, -1, dtype=np.int32)
+    wed = np.full(nwin_cap, -1, dtype=np.int32)
     ec = ctypes.c_int32(0)
     tc, cl, nw = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int64(0)
     st = _load().orc_align_pair(_ptr(t), n, _ptr(p), m, W, O, k, ctypes.byref(ec), ctypes.byref(tc),
-                                _ptr(cig), cap, ctypes.byref(cl), _ptr(dopt), nwin_cap, ctypes.byref(nw))
+                                _ptr(cig), cap, ctypes.byref(cl), _ptr(dopt), _ptr(wed), nwin_cap,
+                                ctypes.byref(nw))
     if st == -1:
         raise ValueError("bad arguments or internal oracle error")
     return {"edit_count": ec.value, "text_consumed": tc.value,
             "cigar": cig[: max(cl.value, 0)].copy(), "d_opt": dopt[: min(nw.value, nwin_cap)].copy(),
+            "window_edits": wed[: min(nw.value, nwin_cap)].copy(),
             "status": st}
 
 

@@ -242,7 +242,7 @@ static int min_int(int64_t a, int64_t b) { return (int)(a < b ? a : b); }
  */
 static int align_pair(orc_work *w, const uint8_t *text, int64_t n, const uint8_t *pattern, int64_t m,
                       int W, int O, int k, orc_cigar *cig, int64_t *text_consumed, int64_t *n_windows,
-                      int32_t *dopt_log, int64_t dopt_cap) {
+                      int32_t *dopt_log, int32_t *wedit_log, int64_t dopt_cap) {
     int64_t ti = 0, pj = 0, win = 0;
     while (pj < m) {
         int nw = min_int(W, n - ti);
@@ -259,7 +259,10 @@ static int align_pair(orc_work *w, const uint8_t *text, int64_t n, const uint8_t
             return 1;
         }
         int ci = 0, cj = 0;
+        const int64_t edits_before = cig->edits;
         if (genasm_tb(&w->tab, d_opt, W - O, cig, &ci, &cj) != 0) return -1;
+        /* edits of the kept traceback: the rows it descended below d_opt */
+        if (wedit_log && win - 1 < dopt_cap) wedit_log[win - 1] = (int32_t)(cig->edits - edits_before);
         ti += ci;
         pj += cj;
     }
@@ -304,16 +307,19 @@ static int check_args(int W, int O, int k) {
     return 0;
 }
 
-/* One pair; cigar must hold cigar_cap runs. Returns the align_pair status. */
+/* One pair; cigar must hold cigar_cap runs. Returns the align_pair status.
+ * Optional per-window logs (dopt_cap entries each, may be NULL): dopt_log the
+ * window's edit distance, wedit_log the edits its kept traceback took. */
 int orc_align_pair(const uint8_t *text, int64_t n, const uint8_t *pattern, int64_t m, int W, int O, int k,
                    int32_t *edit_count, int64_t *text_consumed, uint32_t *cigar, int64_t cigar_cap,
-                   int64_t *cigar_len, int32_t *dopt_log, int64_t dopt_cap, int64_t *n_windows) {
+                   int64_t *cigar_len, int32_t *dopt_log, int32_t *wedit_log, int64_t dopt_cap,
+                   int64_t *n_windows) {
     if (check_args(W, O, k) != 0 || n < 0 || m < 0) return -1;
     orc_work w;
     if (work_init(&w, k) != 0) return -1;
     orc_cigar c = {cigar, cigar_cap, 0, 0, 0};
     int64_t tc = 0, nwin = 0;
-    int st = align_pair(&w, text, n, pattern, m, W, O, k, &c, &tc, &nwin, dopt_log, dopt_cap);
+    int st = align_pair(&w, text, n, pattern, m, W, O, k, &c, &tc, &nwin, dopt_log, wedit_log, dopt_cap);
     work_free(&w);
     /* a CIGAR overflow still aligned the pair: only the run count reports it */
     *edit_count = (st == 0 || st == -2) ? (int32_t)c.edits : -1;
@@ -359,7 +365,7 @@ static void *batch_worker(void *arg) {
         orc_cigar c = {b->cigar + b->cigar_off[p], b->cigar_off[p + 1] - b->cigar_off[p], 0, 0, 0};
         int64_t tc = 0, nwin = 0;
         int st = align_pair(&w, b->texts + b->text_off[p], n, b->patterns + b->pattern_off[p], m, b->W, b->O,
-                            b->k, &c, &tc, &nwin, NULL, 0);
+                            b->k, &c, &tc, &nwin, NULL, NULL, 0);
         if (st == -1) {
             pthread_mutex_lock(&b->lock);
             b->err = -1;

@@ -228,3 +228,58 @@ def test_free_end_row_recurrence_matches_its_definition():
         n, m = int(rng.integers(0, 50)), int(rng.integers(0, 50))
         t, p = rng.integers(0, 4, n), rng.integers(0, 4, m)
         assert free_end_distance_rows(t, p) == free_end_distance(t, p)
+
+
+def _first_window_extent(runs, n, m, W, O):
+    """(text chars, pattern chars, edits) of the first window's kept traceback.
+
+    The traceback of a window stops at the first point where j == m_w, i == W-O
+    or j == W-O (Section 2.2.3), so walking the stitched CIGAR one operation at
+    a time and stopping at the first such point recovers the first window.
+    """
+    L, mw = W - O, min(W, m)
+    i = j = e = 0
+    for op, ln in brute.cigar_ops(runs):
+        for _ in range(ln):
+            if j >= mw or i >= L or j >= L:
+                return i, j, e
+            i += op in (7, 8, 2)
+            j += op in (7, 8, 1)
+            e += op != 7
+    return i, j, e
+
+
+def test_traceback_rows_extended_dent(oracle_mod):
+    """Supplementary Section 1 (DENT extended to rows): a window's kept traceback descends at most
+    W-O rows below d_opt, so only rows d_opt-(W-O) .. d_opt are ever read.
+
+    Why: the traceback path is part of an optimal alignment, so its part up to (i, j) costs
+    lev(text[:i], pattern[:j]) <= max(i, j) <= W-O. Checked by brute force on the first window of
+    every pair (the edits logged for it equal that Levenshtein distance), on every window (logged
+    edits <= W-O, and they sum to the edit count), and shown tight: an all-substitution window
+    descends exactly W-O rows.
+    """
+    rng = np.random.default_rng(17)
+    for it in range(300):
+        W = int(rng.choice([8, 12, 16, 32]))
+        O = int(rng.integers(0, W))
+        # from unrelated strings (edit rates near 3/4) down to close copies
+        rate = float(rng.choice([0.0, 0.1, 0.3, 1.0]))
+        m = int(rng.integers(1, 3 * W))
+        t = rng.integers(0, 4, m + int(rng.integers(0, W))).astype(np.uint8)
+        p = t[:m].copy()
+        hit = rng.random(m) < rate
+        p[hit] = rng.integers(0, 4, int(hit.sum())).astype(np.uint8)
+        r = oracle_mod.align_pair(t, p, W, O, W)
+        assert r["status"] == 0
+        we = r["window_edits"]
+        assert len(we) == len(r["d_opt"]) and (we >= 0).all()
+        assert (we <= W - O).all(), (W, O, we)
+        assert (we <= r["d_opt"]).all()
+        assert int(we.sum()) == r["edit_count"]
+        i1, j1, e1 = _first_window_extent(r["cigar"], len(t), len(p), W, O)
+        assert e1 == we[0] == brute.lev(t[:i1], p[:j1]), (W, O, i1, j1)
+    # tight: text all A, pattern all C -> every traceback step is a substitution
+    for W, O in ((8, 3), (16, 0), (32, 17), (64, 33), (64, 24)):
+        r = oracle_mod.align_pair(np.zeros(3 * W, np.uint8), np.ones(2 * W, np.uint8), W, O, W)
+        assert r["status"] == 0 and int(r["window_edits"].max()) == W - O
