@@ -78,6 +78,13 @@ typedef struct scrooge_ctx scrooge_ctx; /* opaque, owned by the library */
  * use the 64-diagonal band (two words per entry, exact for d_opt <= 31)
  * instead of the 32-diagonal one; lanes_per_pair 4 or 8. */
 #define SCROOGE_WIDE_BAND (1u << 10)
+/* Ablation switch, results identical: keep every full-width row of a window
+ * instead of DENT extended to rows (Supplementary Section 1). By default,
+ * with SENE, DENT and ET all on, the full-width row store of a window is a
+ * cycle of W-O+G row slots (G = lanes per pair; row d in slot d mod (W-O+G))
+ * instead of k+1 rows: the traceback only reads rows d_opt-(W-O)..d_opt, and
+ * the row pipeline over a pair's lanes stores at most G-1 rows past d_opt. */
+#define SCROOGE_NO_EXT_DENT (1u << 11)
 
 /* CIGAR run encoding: (length << 4) | op, op in SAM codes. */
 #define SCROOGE_OP_I 1  /* base only in the pattern (read): insertion */
@@ -204,12 +211,13 @@ int scrooge_set_long_class(scrooge_ctx *ctx, int32_t work_class);
 int32_t scrooge_get_long_class(const scrooge_ctx *ctx);
 
 /* Launch shape of the last scrooge_align_batch call on this context, for
- * reports: up to 12 int64 into shape[0..n): kernel (0 banded, else the words
+ * reports: up to 13 int64 into shape[0..n): kernel (0 banded, else the words
  * of the full-width kernel), lanes per pair, DP rows kept in shared memory,
  * warps per block, dynamic shared memory per block (bytes), blocks, stored
  * columns per row, stored words per entry, shared-memory table bytes per
  * warp, device-scratch row bytes per warp, full-width fallback bytes per
- * warp, pairs per warp. */
+ * warp, pairs per warp, row slots of a window's full-width rows (W-O+lanes
+ * with DENT extended to rows, else k+1; see SCROOGE_NO_EXT_DENT). */
 int scrooge_last_launch_shape(const scrooge_ctx *ctx, int64_t *shape, int32_t n);
 
 /* Autotuner (no counterpart in the paper: it picks implementation

@@ -42,6 +42,7 @@ SCROOGE_GRAPH = 1 << 7
 SCROOGE_NO_BAND = 1 << 8
 SCROOGE_WARP_SPECIALIZED = 1 << 9
 SCROOGE_WIDE_BAND = 1 << 10
+SCROOGE_NO_EXT_DENT = 1 << 11
 
 SCROOGE_OP_I, SCROOGE_OP_D, SCROOGE_OP_EQ, SCROOGE_OP_X = 1, 2, 7, 8
 
@@ -249,7 +250,7 @@ def scrooge_set_timing_events(ctx, start=None, stop=None):
 
 LAUNCH_SHAPE_KEYS = ("kernel", "lanes", "smem_rows", "warps_per_block", "smem_bytes_per_block", "blocks",
                      "stored_columns", "stored_words", "table_bytes_per_warp", "scratch_bytes_per_warp",
-                     "fallback_bytes_per_warp", "pairs_per_warp")
+                     "fallback_bytes_per_warp", "pairs_per_warp", "row_slots")
 
 
 def scrooge_last_launch_shape(ctx) -> dict:

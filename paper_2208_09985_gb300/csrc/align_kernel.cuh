@@ -24,7 +24,9 @@
 // both use the layout [row][column][pair of the warp][word], so a step needs
 // one row pointer and every column store has a compile-time offset. Without
 // SENE the three GenASM edge vectors I, D, M of every cell are stored instead
-// (ablation).
+// (ablation). DENT extended to rows (Supplementary Section 1): row d goes to
+// row slot d mod `ring`, a cycle of W-O+G slots that always holds the rows
+// d_opt-(W-O) .. d_opt the traceback reads (ring = k+1 keeps every row).
 //
 // Traceback (GenASM-TB, Section 2.2.2) runs on lane G-1 of each pair. Along
 // the path every visited entry holds a 0 (Theorem 1), so when text[i] equals
@@ -55,6 +57,10 @@ constexpr int kOpI = 1, kOpD = 2, kOpEq = 7, kOpX = 8;
 __device__ __forceinline__ uint32_t prefix_mask(int bits) {
     return bits <= 0 ? 0u : (bits >= 32 ? kFull : (kFull << (32 - bits)));
 }
+
+// Slot of stored row `row` (>= 0) in a cyclic row store of `ring` slots; rows below `ring`,
+// all of them when ring = k + 1, keep their own index, so the division runs only on wrap.
+__device__ __forceinline__ int ring_slot(int row, int ring) { return row < ring ? row : row % ring; }
 
 __device__ __forceinline__ uint2 load_block(const uint2 *seq, int64_t b, int64_t nblk) {
     return (b >= 0 && b < nblk) ? __ldg(seq + b) : make_uint2(0u, 0u);
@@ -281,7 +287,7 @@ __global__ void __launch_bounds__(64, 6) align_kernel(const AlignParams p) {
     const int l = lane - g * G;
     const int tbl = g * G + G - 1;  // traceback lane of this pair (owns column 0)
     const int W = p.W, L = p.W - p.O, k = p.k;
-    const int ncolp = p.ncol, rcap = p.rcap;  // ncolp: stored columns
+    const int ncolp = p.ncol, rcap = p.rcap, ring = p.ring;  // ncolp: stored columns
     const int colbase = (G - 1 - l) * C;
     const bool lane_stores = colbase < ncolp;  // stored columns come in whole lane chunks
     uint32_t tbl_all = 0;                      // one bit per pair: its traceback lane
@@ -297,8 +303,9 @@ __global__ void __launch_bounds__(64, 6) align_kernel(const AlignParams p) {
     // word 0 of column 0 of `row` of this pair (shared memory or scratch)
     const int rstride = p.rstride;
     auto row_base = [&](int row) -> uint32_t * {
-        return row < rcap ? tab + ((int64_t)row * rstride + g) * CELL
-                          : spill + ((int64_t)(row - rcap) * rstride + g) * CELL;
+        const int slot = ring_slot(row, ring);
+        return slot < rcap ? tab + ((int64_t)slot * rstride + g) * CELL
+                           : spill + ((int64_t)(slot - rcap) * rstride + g) * CELL;
     };
 
     // Each pair slot of the warp refills itself as soon as its pair is done:
@@ -564,7 +571,7 @@ __global__ void __launch_bounds__(64, 6) align_kernel(const AlignParams p) {
                             uint32_t bS, bI, bD;
                             if (SENE) {
                                 // entries (i+1, d-1) and (i, d-1): shared memory or scratch
-                                const int r = d - 1;
+                                const int r = ring_slot(d - 1, ring);
                                 const bool ld1 = tx && i + 1 < nw;
                                 uint32_t e1 = 0u, e0 = 0u;
                                 if (r < rcap) {

@@ -149,14 +149,16 @@ extern "C" int scrooge_align_batch_noalloc(const uint32_t *texts, const int64_t 
     p.ncol = ts.ncol;
     p.sw = ts.swp;
     p.rstride = row_stride_cells(ts, PPW, 32 * words / sh.lanes);
-    int rcap = std::min(sh.rows, k + 1);
+    // DENT extended to rows: W-O+G row slots per window instead of k+1 (with DENT and ET)
+    p.ring = ext_dent_ring(W, O, k, sh.lanes, dent && p.et && !(flags & SCROOGE_NO_EXT_DENT));
+    int rcap = std::min(sh.rows, (int)p.ring);
     const int stage = stage_words_per_warp(words, PPW);
     while (rcap > 1 && (size_t)sh.wpb * (table_words_per_warp(rcap, ts, PPW, 32 * words / sh.lanes) + stage) * 4 > d->smem_optin) --rcap;
     p.rcap = rcap;
     p.table_words_per_warp = (int32_t)table_words_per_warp(rcap, ts, PPW, 32 * words / sh.lanes);
     p.smem_words_per_warp = p.table_words_per_warp + stage;
     const size_t smem = (size_t)sh.wpb * p.smem_words_per_warp * 4;
-    p.spill_words_per_pair = table_words_per_warp(std::max(0, k + 1 - rcap), ts, PPW, 32 * words / sh.lanes);  // per warp
+    p.spill_words_per_pair = table_words_per_warp(std::max(0, p.ring - rcap), ts, PPW, 32 * words / sh.lanes);  // per warp
     // the static row scratch bounds how many warps may be resident
     const int64_t words_per_block = (int64_t)sh.wpb * std::max<int64_t>(p.spill_words_per_pair, 4);
     const int64_t fit_blocks = kNoAllocRowWords / words_per_block;

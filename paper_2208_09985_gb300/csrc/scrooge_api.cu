@@ -199,7 +199,7 @@ int32_t scrooge_get_long_class(const scrooge_ctx *c) { return c ? c->long_class 
 
 int scrooge_last_launch_shape(const scrooge_ctx *c, int64_t *shape, int32_t n) {
     if (!c || !shape || n < 1) return SCROOGE_E_INVAL;
-    memcpy(shape, c->last_shape, sizeof(int64_t) * (size_t)std::min(n, 12));
+    memcpy(shape, c->last_shape, sizeof(int64_t) * (size_t)std::min(n, 13));
     return SCROOGE_OK;
 }
 
@@ -278,7 +278,10 @@ int make_plan(scrooge_ctx *c, const AlignParams &base, bool band, uint32_t flags
     p.ncol = ts.ncol;
     p.sw = ts.swp;
     p.rstride = row_stride_cells(ts, PPW, chunk);
-    const int rows_needed = band ? std::min(k, band_rows_for(bw) - 1) + 1 : k + 1;  // rows the kernel may store
+    // full-width rows: a cycle of W-O+G slots with SENE, DENT and ET (DENT extended to rows), else k+1
+    p.ring = ext_dent_ring(W, O, k, G, sene && dent && p.et && !(flags & SCROOGE_NO_EXT_DENT));
+    // rows the kernel may store: the band's rows (banded kernels), or the full-width row slots
+    const int rows_needed = band ? std::min(k, band_rows_for(bw) - 1) + 1 : p.ring;
     int rcap = std::min(kc.rows, rows_needed);
     const int stage = stage_words_per_warp(words, PPW);
     int wpb = slots > 0 ? 1 : kc.wpb;
@@ -315,7 +318,7 @@ int make_plan(scrooge_ctx *c, const AlignParams &base, bool band, uint32_t flags
     p.fb = nullptr;
     p.fb_words_per_warp = 0;
     if (band) {
-        p.fb_words_per_warp = band_fallback_words(k, ts.ncol, PPW, nww, bw);
+        p.fb_words_per_warp = band_fallback_words(k, p.ring, ts.ncol, PPW, nww, bw);
         if (p.fb_words_per_warp > 0) {
             if ((rc = ensure(c, fallback, (size_t)blocks * sets * (size_t)p.fb_words_per_warp * 4,
                              "full-width fallback scratch")))
@@ -527,9 +530,10 @@ int scrooge_align_batch(scrooge_ctx *c, const uint32_t *texts, const int64_t *te
     }
     {
         const TableShape &ts = plan.ts;
-        const int64_t shape[12] = {plan.band ? 0 : plan.words, plan.G, plan.p.rcap, plan.wpb, (int64_t)plan.smem,
+        const int64_t shape[13] = {plan.band ? 0 : plan.words, plan.G, plan.p.rcap, plan.wpb, (int64_t)plan.smem,
                                    plan.blocks, plan.p.ncol, ts.swp, plan.p.table_words_per_warp * 4LL,
-                                   plan.p.spill_words_per_pair * 4, plan.p.fb_words_per_warp * 4, 32 / plan.G};
+                                   plan.p.spill_words_per_pair * 4, plan.p.fb_words_per_warp * 4, 32 / plan.G,
+                                   plan.p.ring};
         memcpy(c->last_shape, shape, sizeof shape);
     }
     int64_t *dense_off = dev ? cigar_offsets : (int64_t *)c->out_off.p;

@@ -56,7 +56,7 @@ struct scrooge_ctx {
     // optional events recorded around the alignment kernel (not in graph mode)
     cudaEvent_t t_start = nullptr, t_stop = nullptr;
     int32_t last_kernels = 0;  // kernels launched by the last alignment call
-    int64_t last_shape[12] = {0};  // launch shape of the last alignment call (scrooge_last_launch_shape)
+    int64_t last_shape[13] = {0};  // launch shape of the last alignment call (scrooge_last_launch_shape)
     // CUDA graph of the learned pipeline, keyed by the call it was captured for
     cudaGraphExec_t graph = nullptr;
     unsigned long long graph_key[28] = {0};

@@ -151,6 +151,7 @@ def main(argv=None):
                                "scratch_bytes_per_pair": shape["scratch_bytes_per_warp"] / pps,
                                "kernel": "band" if shape["kernel"] == 0 else f"full{shape['kernel']}",
                                "lanes": shape["lanes"], "smem_rows": shape["smem_rows"],
+                               "row_slots": shape["row_slots"],
                                "mean_rows_per_window": mean_rows,
                                "free_end_mean": fe_mean, "global_mean": gl_mean, **acc}
                         rows.append(rec)

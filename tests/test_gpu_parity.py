@@ -331,3 +331,35 @@ def test_wide_band_for_64_base_windows(ctx, lanes):
                     assert_same(g, r, label=f"wide band lanes={lanes} rows={rows} W={W} O={O} k={k} flags={extra}")
     finally:
         sc.scrooge_set_kernel_config(ctx, 0, *saved)
+
+
+@pytest.mark.parametrize("W,O", [(16, 12), (32, 24), (32, 31), (64, 56), (64, 63), (100, 90), (128, 120)])
+def test_extended_dent_row_cycle(ctx, W, O):
+    """DENT extended to rows (Supplementary Section 1): each window keeps W-O+lanes full-width row
+    slots (row d in slot d mod that), which these high-error windows with small W-O wrap around
+    many times. Results equal the oracle's, and those of the ablation keeping all k+1 rows."""
+    b = synth.concat([synth.random_pairs(200, 3 * W, 3 * W, seed=900 + W + O),
+                      synth.fixed_error(20, 0.35, length=8 * W, seed=901 + O),
+                      synth.fixed_error(20, 0.10, length=8 * W, seed=902)])
+    pb = sc.PackedBatch(b)
+    r = oracle.align_batch(b, W, O, W, threads=THREADS)
+    for slot, flags, name in _kernels(W):
+        lanes_opts = {1: [1, 2, 4], 2: [2, 4, 8], 4: [8, 16], 0: [2, 4, 8], 3: [8, 16]}[slot]
+        saved = sc.scrooge_get_kernel_config(ctx, slot)
+        try:
+            for lanes in lanes_opts:
+                for rows in (1, 4, 64):
+                    sc.scrooge_set_kernel_config(ctx, slot, lanes, rows, 2)
+                    g = sc.align_host(ctx, pb, W, O, W, flags)
+                    assert_same(g, r, label=f"{name} W={W} O={O} lanes={lanes} rows={rows}")
+                    shape = sc.scrooge_last_launch_shape(ctx)
+                    assert shape["row_slots"] == min(W + 1, W - O + shape["lanes"]), shape
+                    g = sc.align_host(ctx, pb, W, O, W, flags | sc.SCROOGE_NO_EXT_DENT)
+                    assert_same(g, r, label=f"{name} W={W} O={O} lanes={lanes} rows={rows} all rows")
+                    assert sc.scrooge_last_launch_shape(ctx)["row_slots"] == W + 1
+        finally:
+            sc.scrooge_set_kernel_config(ctx, slot, *saved)
+    if W == 64:
+        for extra in (sc.SCROOGE_PERSISTENT | sc.SCROOGE_WARP_SPECIALIZED, sc.SCROOGE_WIDE_BAND):
+            g = sc.align_host(ctx, pb, W, O, W, extra)
+            assert_same(g, r, label=f"W={W} O={O} flags={extra}")

@@ -17,7 +17,7 @@ from paper_2208_09985_gb300 import synth
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("W,O,k", [(64, 24, 64), (32, 17, 32), (128, 64, 128), (64, 33, 12)])
+@pytest.mark.parametrize("W,O,k", [(64, 24, 64), (32, 17, 32), (128, 64, 128), (64, 33, 12), (64, 60, 64), (32, 28, 32)])
 def test_noalloc_matches_allocating_entry_point(W, O, k):
     import torch
     assert torch.cuda.is_available()
