@@ -80,10 +80,12 @@ typedef struct scrooge_ctx scrooge_ctx; /* opaque, owned by the library */
 #define SCROOGE_WIDE_BAND (1u << 10)
 /* Ablation switch, results identical: keep every full-width row of a window
  * instead of DENT extended to rows (Supplementary Section 1). By default,
- * with SENE, DENT and ET all on, the full-width row store of a window is a
- * cycle of W-O+G row slots (G = lanes per pair; row d in slot d mod (W-O+G))
- * instead of k+1 rows: the traceback only reads rows d_opt-(W-O)..d_opt, and
- * the row pipeline over a pair's lanes stores at most G-1 rows past d_opt. */
+ * with SENE, DENT and ET all on, the row store of a full-width kernel's window
+ * (and of the allocation-free entry point) is a
+ * cycle of R = max(W-O+G, ceil((k+1)/2)) row slots (G = lanes per pair; row d
+ * in slot d mod R) instead of k+1 rows: the traceback only reads rows
+ * d_opt-(W-O)..d_opt, and the row pipeline over a pair's lanes stores at most
+ * G-1 rows past d_opt. The lower bound lets a row wrap at most once. */
 #define SCROOGE_NO_EXT_DENT (1u << 11)
 
 /* CIGAR run encoding: (length << 4) | op, op in SAM codes. */
@@ -216,8 +218,8 @@ int32_t scrooge_get_long_class(const scrooge_ctx *ctx);
  * warps per block, dynamic shared memory per block (bytes), blocks, stored
  * columns per row, stored words per entry, shared-memory table bytes per
  * warp, device-scratch row bytes per warp, full-width fallback bytes per
- * warp, pairs per warp, row slots of a window's full-width rows (W-O+lanes
- * with DENT extended to rows, else k+1; see SCROOGE_NO_EXT_DENT). */
+ * warp, pairs per warp, row slots of a window's full-width rows (see
+ * SCROOGE_NO_EXT_DENT; k+1 without it). */
 int scrooge_last_launch_shape(const scrooge_ctx *ctx, int64_t *shape, int32_t n);
 
 /* Autotuner (no counterpart in the paper: it picks implementation

@@ -88,15 +88,14 @@ struct BandMinBlocks {
 
 // Full-width DC of the windows in `full_mask` (Algorithm 1 on NW words per
 // entry, as in the full-width kernel), rows stored to `rows` (this lane's first
-// column of row slot 0; [slot][column][pair][NW words], row d in slot d mod
-// `ring`, DENT extended to rows); d_opt of those windows is set
+// column of row 0; [row][column][pair][NW words]); d_opt of those windows is set
 // on their traceback lanes. Kept out of line: it is rare, and its registers
 // must not count against the banded loop.
 template <int G, int NW>
 __device__ __noinline__ void full_width_dc(const uint2 *pseq, int64_t pblk, int pj, const uint2 *tseq, int64_t tblk,
                                            int ti, int nw, int mw, int k, int l, int tbl, uint32_t tbl_all,
                                            uint32_t full_mask, bool lane_stores, uint32_t *rows, int row_words,
-                                           int ring, int &d_opt) {
+                                           int &d_opt) {
     constexpr int C = 32 * NW / G;
     constexpr int PPW = 32 / G;
     const bool full = (full_mask >> tbl) & 1u;
@@ -130,7 +129,7 @@ __device__ __noinline__ void full_width_dc(const uint2 *pseq, int64_t pblk, int 
         bool found = false;
         if (!ddone && d >= 0 && d <= k) {
             shl1<NW>(pR, pS);
-            uint32_t *rowp = rows + (int64_t)ring_slot(d, ring) * row_words;
+            uint32_t *rowp = rows + (int64_t)d * row_words;
 #pragma unroll
             for (int c = C - 1; c >= 0; --c) {
                 // PM[text[i]] from the pattern planes
@@ -292,7 +291,7 @@ __device__ __forceinline__ void band_window_dc(const AlignParams &p, const BandW
     const bool full = (full_mask >> tbl) & 1u;
     if (full_mask)
         full_width_dc<G, NW>(bw.pseq, bw.pblk, bw.pj, bw.tseq, bw.tblk, bw.ti, nw, mw, k, l, tbl, tbl_all, full_mask,
-                             lane_stores, fb + ((int64_t)colbase * PPW + g) * NW, ncolp * PPW * NW, p.ring, d_opt);
+                             lane_stores, fb + ((int64_t)colbase * PPW + g) * NW, ncolp * PPW * NW, d_opt);
     d_opt_out = d_opt;
     full_out = full;
 }
@@ -381,7 +380,7 @@ __device__ __forceinline__ void band_window_tb(const AlignParams &p, uint32_t ma
                         r0b = (uint32_t)((v0 >> (62 - kk)) & 1ull);
                     }
                 } else {
-                    const uint32_t *fp = fb + (int64_t)ring_slot(r, p.ring) * fb_row + (i * PPW + g) * NW;
+                    const uint32_t *fp = fb + (int64_t)r * fb_row + (i * PPW + g) * NW;
                     t1 = ld1 ? entry_bits2<NW>(fp + PPW * NW, j) : 0u;
                     r0b = tx ? (entry_bits2<NW>(fp, j) & 1u) : 0u;
                 }
@@ -413,26 +412,6 @@ __device__ __forceinline__ void band_window_tb(const AlignParams &p, uint32_t ma
     if (tb_live) {
         ti += i;
         pj += j;
-    }
-}
-
-// The band rows rcap .. top of one warp (every pair, every stored column) sit in its device
-// scratch; pull their 128-byte lines into L1, the lines spread over the 32 lanes. The traceback
-// reads these rows one dependent step after another (row d_opt - 1 first, one row per edit), so
-// with the lines requested together up front the chain waits for L2 about once per window
-// instead of once per row. Every address lies inside the rows [rcap, top] of the region.
-template <int G, int BW>
-__device__ __forceinline__ void prefetch_scratch_rows(const AlignParams &p, const uint32_t *spill, int top,
-                                                      int lane) {
-    constexpr int PPW = 32 / G;
-    const int row_words = p.ncol * PPW * BW;       // words of one stored row of the warp
-    const int lines = (row_words + 31) / 32 + 1;   // 128-byte lines such a row can touch
-    const int total = (top - p.rcap + 1) * lines;
-    for (int t = lane; t < total; t += 32) {
-        const int r = t / lines, q = t - r * lines;
-        const uint32_t *row = spill + (int64_t)r * p.rstride * BW;
-        const uint32_t *a = row + min(q * 32, row_words - 1);
-        asm volatile("{\n\t.reg .u64 ga;\n\tcvta.to.global.u64 ga, %0;\n\tprefetch.global.L1 [ga];\n\t}" ::"l"(a));
     }
 }
 
@@ -488,8 +467,6 @@ __global__ void __launch_bounds__(64, (BandMinBlocks<G, NWW, BW>::value)) align_
         bool full;
         band_window_dc<G, NWW, BW>(p, bw, l, g, tbl, tbl_all, tab, spill, fb, stage, d_opt, full);
         __syncwarp();  // entries written by every lane are visible to the traceback lane
-        // deepest band row any traceback of the warp reads: d_opt - 1 (d_opt <= the band's rows)
-        const int top = __reduce_max_sync(kFull, (l == G - 1 && bw.active && !full) ? d_opt - 1 : -1);
         if (l == G - 1)
             band_window_tb<G, NWW, BW>(p, tbl_all, bw.active, d_opt, full, bw.nw, bw.mw, stage, tab, spill, fb, g, out,
                                   s.ti, s.pj, s.failed, s.st_rows, s.st_cells, s.st_windows);

@@ -25,8 +25,8 @@
 // one row pointer and every column store has a compile-time offset. Without
 // SENE the three GenASM edge vectors I, D, M of every cell are stored instead
 // (ablation). DENT extended to rows (Supplementary Section 1): row d goes to
-// row slot d mod `ring`, a cycle of W-O+G slots that always holds the rows
-// d_opt-(W-O) .. d_opt the traceback reads (ring = k+1 keeps every row).
+// row slot d mod `ring`, a cycle of at least W-O+G slots that always holds the
+// rows d_opt-(W-O) .. d_opt the traceback reads (ring = k+1 keeps every row).
 //
 // Traceback (GenASM-TB, Section 2.2.2) runs on lane G-1 of each pair. Along
 // the path every visited entry holds a 0 (Theorem 1), so when text[i] equals
@@ -58,9 +58,9 @@ __device__ __forceinline__ uint32_t prefix_mask(int bits) {
     return bits <= 0 ? 0u : (bits >= 32 ? kFull : (kFull << (32 - bits)));
 }
 
-// Slot of stored row `row` (>= 0) in a cyclic row store of `ring` slots; rows below `ring`,
-// all of them when ring = k + 1, keep their own index, so the division runs only on wrap.
-__device__ __forceinline__ int ring_slot(int row, int ring) { return row < ring ? row : row % ring; }
+// Slot of stored row `row` (0 <= row <= k) in a cyclic row store of `ring` slots. The host keeps
+// ring >= (k + 1) / 2, so a row wraps at most once: one compare and subtract, no division.
+__device__ __forceinline__ int ring_slot(int row, int ring) { return row >= ring ? row - ring : row; }
 
 __device__ __forceinline__ uint2 load_block(const uint2 *seq, int64_t b, int64_t nblk) {
     return (b >= 0 && b < nblk) ? __ldg(seq + b) : make_uint2(0u, 0u);

@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(kH) mlp_grad_kernel(const float *model, const 
                                                       const int32_t *rows, int32_t n, float inv_n, float *grad,
                                                       float *loss_sum) {
     __shared__ float w[kModelFloats];
-    __shared__ float h1s[kH], h2s[kH], d2s[kH], xs[kF], red[kH];
+    __shared__ float h1s[kH], d2s[kH], xs[kF], red[kH];
     for (int i = threadIdx.x; i < kModelFloats; i += blockDim.x) w[i] = model[i];
     __syncthreads();
     const int o = threadIdx.x;
@@ -216,7 +216,6 @@ __global__ void __launch_bounds__(kH) mlp_grad_kernel(const float *model, const 
 #pragma unroll 8
         for (int i = 0; i < kH; ++i) a2 = fmaf(w[oW2 + o * kH + i], h1s[i], a2);
         const float h2 = fmaxf(a2, 0.f);
-        h2s[o] = h2;
         red[o] = w[ow3 + o] * h2;
         __syncthreads();
         for (int st = kH / 2; st > 0; st >>= 1) {

@@ -278,8 +278,10 @@ int make_plan(scrooge_ctx *c, const AlignParams &base, bool band, uint32_t flags
     p.ncol = ts.ncol;
     p.sw = ts.swp;
     p.rstride = row_stride_cells(ts, PPW, chunk);
-    // full-width rows: a cycle of W-O+G slots with SENE, DENT and ET (DENT extended to rows), else k+1
-    p.ring = ext_dent_ring(W, O, k, G, sene && dent && p.et && !(flags & SCROOGE_NO_EXT_DENT));
+    // full-width kernels: rows in a cycle (DENT extended to rows) with SENE, DENT and ET. The banded
+    // kernels keep all k+1 rows of their rare full-width fallback: the slot arithmetic in their
+    // traceback loop cost more than the memory it saves.
+    p.ring = band ? k + 1 : ext_dent_ring(W, O, k, G, sene && dent && p.et && !(flags & SCROOGE_NO_EXT_DENT));
     // rows the kernel may store: the band's rows (banded kernels), or the full-width row slots
     const int rows_needed = band ? std::min(k, band_rows_for(bw) - 1) + 1 : p.ring;
     int rcap = std::min(kc.rows, rows_needed);
@@ -318,7 +320,7 @@ int make_plan(scrooge_ctx *c, const AlignParams &base, bool band, uint32_t flags
     p.fb = nullptr;
     p.fb_words_per_warp = 0;
     if (band) {
-        p.fb_words_per_warp = band_fallback_words(k, p.ring, ts.ncol, PPW, nww, bw);
+        p.fb_words_per_warp = band_fallback_words(k, ts.ncol, PPW, nww, bw);
         if (p.fb_words_per_warp > 0) {
             if ((rc = ensure(c, fallback, (size_t)blocks * sets * (size_t)p.fb_words_per_warp * 4,
                              "full-width fallback scratch")))

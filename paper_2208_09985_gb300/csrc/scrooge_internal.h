@@ -121,18 +121,22 @@ cudaError_t launch_align_band(const AlignParams &, int nww, int bw, int lanes, i
                               cudaStream_t);
 cudaError_t occupancy_band(int nww, int bw, int lanes, int wpb, size_t smem, int *blocks_per_sm);
 bool supported_band(int nww, int bw, int lanes);
-// words of the full-width fallback region of one warp of a banded kernel (`rows` row slots)
-inline int64_t band_fallback_words(int k, int rows, int ncol, int ppw, int nww, int bw) {
-    return k >= band_rows_for(bw) ? (int64_t)rows * ncol * ppw * nww : 0;
+// words of the full-width fallback region of one warp of a banded kernel
+inline int64_t band_fallback_words(int k, int ncol, int ppw, int nww, int bw) {
+    return k >= band_rows_for(bw) ? (int64_t)(k + 1) * ncol * ppw * nww : 0;
 }
 // Row slots of a window's full-width row store. DENT extended to rows (Supplementary Section 1):
 // the part of a window's traceback that is kept spends at most W-O edits (it is part of an optimal
 // alignment, so its cost up to (i, j) is lev(text[:i], pattern[:j]) <= max(i, j) <= W-O), so with
 // early termination it reads rows d_opt-(W-O) .. d_opt only. The DC pipeline over the G lanes of a
 // pair stores up to G-1 rows past d_opt before the stop reaches its first lane, so W-O+G slots,
-// row d in slot d mod (W-O+G), never overwrite a row the traceback reads. Without it: k+1 rows.
+// row d in slot d mod (W-O+G), never overwrite a row the traceback reads. The cycle has at least
+// ceil((k+1)/2) slots, so a row wraps at most once and its slot is one compare and subtract
+// (ring_slot); that keeps the full W-O+G at every operating point with W-O+G >= (k+1)/2, which
+// includes the paper's. Without it: k+1 rows.
 inline int ext_dent_ring(int W, int O, int k, int lanes, bool on) {
-    const int ring = W - O + lanes;
+    int ring = W - O + lanes;
+    if (ring < (k + 2) / 2) ring = (k + 2) / 2;
     return on && ring < k + 1 ? ring : k + 1;
 }
 // Warp-specialised banded kernel (align_band.cu): blocks of 4 DC warps (4 lanes per pair, two

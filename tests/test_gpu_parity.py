@@ -335,14 +335,18 @@ def test_wide_band_for_64_base_windows(ctx, lanes):
 
 @pytest.mark.parametrize("W,O", [(16, 12), (32, 24), (32, 31), (64, 56), (64, 63), (100, 90), (128, 120)])
 def test_extended_dent_row_cycle(ctx, W, O):
-    """DENT extended to rows (Supplementary Section 1): each window keeps W-O+lanes full-width row
-    slots (row d in slot d mod that), which these high-error windows with small W-O wrap around
-    many times. Results equal the oracle's, and those of the ablation keeping all k+1 rows."""
+    """DENT extended to rows (Supplementary Section 1): each window of a full-width kernel keeps
+    max(W-O+lanes, ceil((k+1)/2)) row slots (row d in slot d mod that), which these high-error
+    windows with small W-O wrap around. Results equal the oracle's, and those of the ablation
+    keeping all k+1 rows; the banded kernels, which keep all rows, are checked beside them."""
     b = synth.concat([synth.random_pairs(200, 3 * W, 3 * W, seed=900 + W + O),
                       synth.fixed_error(20, 0.35, length=8 * W, seed=901 + O),
                       synth.fixed_error(20, 0.10, length=8 * W, seed=902)])
     pb = sc.PackedBatch(b)
     r = oracle.align_batch(b, W, O, W, threads=THREADS)
+    # these small W-O give the floor of ceil((k+1)/2) slots; windows this deep wrap the cycle
+    deep = max(int(oracle.align_pair(b.text(p), b.pattern(p), W, O, W)["d_opt"].max(initial=-1)) for p in range(40))
+    assert deep >= (W + 2) // 2
     for slot, flags, name in _kernels(W):
         lanes_opts = {1: [1, 2, 4], 2: [2, 4, 8], 4: [8, 16], 0: [2, 4, 8], 3: [8, 16]}[slot]
         saved = sc.scrooge_get_kernel_config(ctx, slot)
@@ -353,7 +357,8 @@ def test_extended_dent_row_cycle(ctx, W, O):
                     g = sc.align_host(ctx, pb, W, O, W, flags)
                     assert_same(g, r, label=f"{name} W={W} O={O} lanes={lanes} rows={rows}")
                     shape = sc.scrooge_last_launch_shape(ctx)
-                    assert shape["row_slots"] == min(W + 1, W - O + shape["lanes"]), shape
+                    cycle = min(W + 1, max(W - O + shape["lanes"], (W + 2) // 2))
+                    assert shape["row_slots"] == (W + 1 if name.startswith("band") else cycle), shape
                     g = sc.align_host(ctx, pb, W, O, W, flags | sc.SCROOGE_NO_EXT_DENT)
                     assert_same(g, r, label=f"{name} W={W} O={O} lanes={lanes} rows={rows} all rows")
                     assert sc.scrooge_last_launch_shape(ctx)["row_slots"] == W + 1
