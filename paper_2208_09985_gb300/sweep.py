@@ -20,6 +20,14 @@ that its edit counts and CIGAR offsets match the first run of the same
 
 This prints one JSON line per run and a markdown summary at the end. The
 library's CUDA kernels do all the work; this module only drives them.
+
+With --ext-dent it measures DENT extended to rows (Supplementary Section 1)
+instead: the full-width kernels at (W, O) = (32, 17), (32, 8), (64, 33) and
+(64, 24), each with the cycle of row slots (the default) and with
+SCROOGE_NO_EXT_DENT, on one batch per edit rate. It checks that the results are
+identical, and reports throughput, row slots and scratch bytes per pair.
+
+    python -m paper_2208_09985_gb300.sweep --ext-dent --pairs 20000 --rates 0.10,0.15
 """
 from __future__ import annotations
 
@@ -93,7 +101,10 @@ def main(argv=None):
     ap.add_argument("--train-pairs", type=int, default=20_000)
     ap.add_argument("--model", default="", help="saved ordering model (JSON); default: train one first")
     ap.add_argument("--out", default="")
+    ap.add_argument("--ext-dent", action="store_true", help="measure DENT extended to rows instead of the grid")
     args = ap.parse_args(argv)
+    if args.ext_dent:
+        return ext_dent(args)
 
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
@@ -163,6 +174,47 @@ def main(argv=None):
         del db
     sc.scrooge_destroy(ctx)
     print(summary(rows))
+
+
+def ext_dent(args):
+    """DENT extended to rows on the full-width kernels: the cycle of row slots against all k+1 rows."""
+    import torch
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    ctx = sc.scrooge_create(0, stream)
+    lines = ["| rate | W | O | kernel | row slots | scratch B/pair | aln/s | all k+1 rows: slots | scratch B/pair | "
+             "aln/s |", "|---|---|---|---|---|---|---|---|---|---|"]
+    for rate in (float(x) for x in args.rates.split(",")):
+        batch = synth.fixed_error(args.pairs, rate, seed=500 + int(rate * 1000), length=args.length)
+        db = sc.DeviceBatch(sc.PackedBatch(batch))
+        for W, O in ((32, 17), (32, 8), (64, 33), (64, 24)):
+            k = W
+            cells = []
+            ref = None
+            for extra in (0, sc.SCROOGE_NO_EXT_DENT):
+                fl = sc.SCROOGE_NO_BAND | extra
+                ms = timed(ctx, db, W, O, k, fl, args.steps, stream)
+                shape = sc.scrooge_last_launch_shape(ctx)
+                res = sc.device_results(db)
+                if ref is None:
+                    ref = res
+                elif not (np.array_equal(res["edit_counts"], ref["edit_counts"])
+                          and np.array_equal(res["cigar_off"], ref["cigar_off"])):
+                    raise SystemExit(f"ext-dent: rate {rate} W {W} O {O} changed the results")
+                rec = {"rate": rate, "W": W, "O": O, "k": k, "ext_dent": int(extra == 0), "ms": ms,
+                       "alignments_per_s": db.n_pairs / (ms / 1e3), "row_slots": shape["row_slots"],
+                       "smem_rows": shape["smem_rows"], "lanes": shape["lanes"],
+                       "scratch_bytes_per_pair": shape["scratch_bytes_per_warp"] / shape["pairs_per_warp"],
+                       "kernel": f"full{shape['kernel']}"}
+                print(json.dumps(rec), flush=True)
+                cells.append(rec)
+            a, b = cells
+            lines.append(f"| {rate:.2f} | {W} | {O} | {a['kernel']} | {a['row_slots']} | "
+                         f"{a['scratch_bytes_per_pair']:.0f} | {a['alignments_per_s'] / 1e6:.3f}M | {b['row_slots']} | "
+                         f"{b['scratch_bytes_per_pair']:.0f} | {b['alignments_per_s'] / 1e6:.3f}M |")
+        del db
+    sc.scrooge_destroy(ctx)
+    print("\n".join(lines))
 
 
 def summary(rows) -> str:
