@@ -72,7 +72,8 @@ typedef struct scrooge_ctx scrooge_ctx; /* opaque, owned by the library */
 /* Implementation choice, never a change of results: persistent launches of
  * the banded kernel run as blocks of four DC warps and one traceback warp,
  * which hand windows over through shared-memory barriers (4 lanes per pair,
- * the banded kernel settings' shared-memory rows). */
+ * the banded kernel settings' shared-memory rows). Every barrier wait is
+ * bounded; if one gives up, the synchronous call returns SCROOGE_E_TIMEOUT. */
 #define SCROOGE_WARP_SPECIALIZED (1u << 9)
 /* Implementation choice, never a change of results: windows of 33..64 bases
  * use the 64-diagonal band (two words per entry, exact for d_opt <= 31)

@@ -640,6 +640,8 @@ int scrooge_align_batch(scrooge_ctx *c, const uint32_t *texts, const int64_t *te
             (e = cudaMemcpyAsync(&total, dense_off + n_pairs, 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
             (e = cudaStreamSynchronize(st)) != cudaSuccess)
             return cuda_fail(c, e, "stream synchronise");
+        if (status_h & 8)
+            return fail(c, SCROOGE_E_TIMEOUT, "a bounded device wait gave up (status %d)", status_h);
         if (status_h != 0) return fail(c, SCROOGE_E_INTERNAL, "kernel status %d", status_h);
         if (total > cigar_capacity)
             return fail(c, SCROOGE_E_CAPACITY, "CIGAR needs %lld runs, capacity %lld", (long long)total,
@@ -651,6 +653,8 @@ int scrooge_align_batch(scrooge_ctx *c, const uint32_t *texts, const int64_t *te
         (e = cudaMemcpyAsync(&status_h, plan.p.status, 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
         (e = cudaStreamSynchronize(st)) != cudaSuccess)
         return cuda_fail(c, e, "CIGAR offsets copy");
+    if (status_h & 8)
+        return fail(c, SCROOGE_E_TIMEOUT, "a bounded device wait gave up (status %d)", status_h);
     if (status_h != 0) return fail(c, SCROOGE_E_INTERNAL, "kernel status %d", status_h);
     const int64_t total = cigar_offsets[np];
     const int64_t keep = std::min(total, cigar_capacity);
