@@ -425,9 +425,9 @@ int scrooge_align_batch(scrooge_ctx *c, const uint32_t *texts, const int64_t *te
             (e = cudaStreamSynchronize(st)) != cudaSuccess)
             return cuda_fail(c, e, "CIGAR scratch size");
     } else {
-        // host pointers: check the layout, then stage everything on the device
+        // host pointers: check the layout, then stage everything on the device (the run scratch
+        // offsets are laid out on the device from the copied lengths, as for device pointers)
         int64_t text_words = 0, pat_words = 0;
-        std::vector<int64_t> soff(np + 1, 0);
         for (int32_t q = 0; q < n_pairs; ++q) {
             const int64_t to = text_offsets[q], po = pattern_offsets[q];
             const int32_t tl = text_lengths[q], pl = pattern_lengths[q];
@@ -435,9 +435,8 @@ int scrooge_align_batch(scrooge_ctx *c, const uint32_t *texts, const int64_t *te
                 return fail(c, SCROOGE_E_INVAL, "pair %d: offsets must be >= 0 multiples of 64, lengths >= 0", q);
             text_words = std::max(text_words, to / 16 + scrooge_packed_words(tl));
             pat_words = std::max(pat_words, po / 16 + scrooge_packed_words(pl));
-            soff[q + 1] = soff[q] + (int64_t)tl + pl + 1;
+            scratch_runs += (int64_t)tl + pl + 1;
         }
-        scratch_runs = soff[np];
         if ((rc = ensure(c, c->in_text, text_words * 4, "texts")) ||
             (rc = ensure(c, c->in_pat, pat_words * 4, "patterns")) ||
             (rc = ensure(c, c->in_toff, np * 8, "text offsets")) ||
@@ -445,7 +444,8 @@ int scrooge_align_batch(scrooge_ctx *c, const uint32_t *texts, const int64_t *te
             (rc = ensure(c, c->in_poff, np * 8, "pattern offsets")) ||
             (rc = ensure(c, c->in_plen, np * 4, "pattern lengths")) ||
             (rc = ensure(c, c->out_ec, np * 4, "edit counts")) || (rc = ensure(c, c->out_tc, np * 4, "text consumed")) ||
-            (rc = ensure(c, c->out_off, (np + 1) * 8, "cigar offsets")))
+            (rc = ensure(c, c->out_off, (np + 1) * 8, "cigar offsets")) ||
+            (rc = ensure(c, c->scr_cap, np * 8, "CIGAR capacities")))
             return rc;
         struct {
             void *d;
@@ -453,11 +453,15 @@ int scrooge_align_batch(scrooge_ctx *c, const uint32_t *texts, const int64_t *te
             size_t b;
         } cp[] = {{c->in_text.p, texts, (size_t)text_words * 4}, {c->in_pat.p, patterns, (size_t)pat_words * 4},
                   {c->in_toff.p, text_offsets, np * 8},          {c->in_tlen.p, text_lengths, np * 4},
-                  {c->in_poff.p, pattern_offsets, np * 8},       {c->in_plen.p, pattern_lengths, np * 4},
-                  {c->scr_off.p, soff.data(), (np + 1) * 8}};
+                  {c->in_poff.p, pattern_offsets, np * 8},       {c->in_plen.p, pattern_lengths, np * 4}};
         for (auto &x : cp)
             if (x.b && (e = cudaMemcpyAsync(x.d, x.h, x.b, cudaMemcpyHostToDevice, st)) != cudaSuccess)
                 return cuda_fail(c, e, "host-to-device copy");
+        if ((e = launch_capacity((const int32_t *)c->in_tlen.p, (const int32_t *)c->in_plen.p, n_pairs,
+                                 (int64_t *)c->scr_cap.p, st)) != cudaSuccess ||
+            (e = exclusive_scan(c->scr_cap.p, 1, n_pairs, (int64_t *)c->scr_off.p, (int64_t *)c->scan_tmp.p, st)) !=
+                cudaSuccess)
+            return cuda_fail(c, e, "CIGAR scratch layout");
         p.texts = (const uint32_t *)c->in_text.p;
         p.patterns = (const uint32_t *)c->in_pat.p;
         p.text_off = (const int64_t *)c->in_toff.p;
