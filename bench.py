@@ -51,7 +51,7 @@ WORKLOADS = {
 }
 
 METRIC = "alignments/s and Gbases/s on 1 GB300 (10 kbp, 10% err), learned+persistent vs plain"
-INT_LOGIC_OPS_PER_CLK_PER_SM = 64  # LOP3/SHF pipe, measured on GB300
+INT_LOGIC_OPS_PER_CLK_PER_SM = 64  # LOP3/SHF pipe: a probe of 8 independent LOP3/SHF chains per thread on GB300
 
 
 def parse():
