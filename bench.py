@@ -51,7 +51,8 @@ WORKLOADS = {
 }
 
 METRIC = "alignments/s and Gbases/s on 1 GB300 (10 kbp, 10% err), learned+persistent vs plain"
-INT_LOGIC_OPS_PER_CLK_PER_SM = 64  # LOP3/SHF pipe: a probe of 8 independent LOP3/SHF chains per thread on GB300
+INT_LOGIC_OPS_PER_CLK_PER_SM = 64  # LOP3/SHF pipe per SM per clock (scrooge_logic_peak measures it on the GPU)
+PAPER_OPS_PER_CELL = 7  # bit-vector ops of one GenASM-DC cell: 3 shifts, 1 OR, 3 AND
 
 
 def parse():
@@ -124,9 +125,11 @@ def measured_peaks():
         return {}
 
 
-def kernel_traffic(kernel: str, workload: str):
-    """DRAM bytes per launch of an alignment kernel on a workload, from the committed ncu summary
-    (profiles/<kernel>_traffic.txt), or None when the kernel source changed since the counters were taken."""
+def kernel_traffic(kernel: str, workload: str, n_pairs: int):
+    """DRAM bytes per launch of an alignment kernel on `n_pairs` pairs of a workload, from the
+    committed ncu summary (profiles/<kernel>_traffic.txt). The counters come from a capture of
+    one launch on a smaller batch of the same workload and are scaled by the pairs processed.
+    None when the kernel source changed since the counters were taken."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_traffic.txt")
     try:
         rec = dict(line.split(": ", 1) for line in open(path).read().splitlines()
@@ -138,7 +141,27 @@ def kernel_traffic(kernel: str, workload: str):
         h.update(open(os.path.join(ROOT, "paper_2208_09985_gb300", "csrc", name), "rb").read())
     if rec.get("source_sha256") != h.hexdigest() or rec.get("workload") != workload:
         return None
-    return int(rec["dram_bytes_per_launch"])
+    captured = int(rec["pairs_captured"])
+    return {"bytes": int(rec["dram_bytes_captured"]) * n_pairs / captured, "pairs_captured": captured,
+            "bytes_captured": int(rec["dram_bytes_captured"])}
+
+
+def cpu_model() -> str:
+    """Model name of the host CPU (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
 
 
 def cpu_baseline(batch, W, O, budget_s: float):
@@ -155,7 +178,7 @@ def cpu_baseline(batch, W, O, budget_s: float):
     dt = time.perf_counter() - t0
     bases = int(np.diff(batch.pattern_off)[:done].sum())
     return {"value": done / dt, "unit": "alignments/s", "cores": cores, "kind": "oracle",
-            "gbases_per_s": bases / dt / 1e9,
+            "cpu_model": cpu_model(), "gbases_per_s": bases / dt / 1e9,
             "sample": f"first {done} pairs of the workload (time-bounded at {budget_s:g} s), {cores} threads"}
 
 
@@ -187,6 +210,7 @@ def run_reference(args):
                    "W": wl["W"], "O": wl["O"], "k": wl["W"]},
         "gbases_per_s": float(np.diff(batch.pattern_off).sum()) / (ms / 1e3) / 1e9,
         "cpu_baseline": {"value": value, "unit": "alignments/s", "cores": cores, "kind": "oracle",
+                         "cpu_model": cpu_model(),
                          "sample": f"first {per_step} pairs of the workload per step, {cores} threads"},
         "e2e": {"value": value, "unit": "alignments/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -205,6 +229,11 @@ def path_flags(sc, name: str) -> int:
 # sources of each alignment kernel, hashed to tell whether committed ncu counters still apply
 KERNEL_SOURCES = {"align_band_kernel": ("align_band.cu", "align_kernel.cuh"),
                   "align_kernel": ("align_kernel.cuh",)}
+
+
+def kernel_name(sc, W: int, flags: int) -> str:
+    """The alignment kernel a call with these flags runs."""
+    return "align_band_kernel" if sc.settings_slot(W, flags) == 0 else "align_kernel"
 
 
 def prepare_model(sc, ctx, args):
@@ -273,6 +302,17 @@ def main():
     total_runs = int(ref_off[-1])
     if (ec < 0).any() or total_runs > db.cigar_capacity:
         raise SystemExit("bench: some pairs failed or the CIGAR buffer is too small")
+    ref_tc = db.text_consumed.clone()
+    ref_cig = db.cigar[:total_runs].clone()
+
+    def same_as_reference(tag):
+        """Every timed path must give the stats run's results: edit counts, text consumed, CIGAR
+        offsets and every CIGAR run (compared on the device, outside the timed region)."""
+        import torch
+        ok = (np.array_equal(db.edit_counts.cpu().numpy(), ec) and np.array_equal(db.cigar_off.cpu().numpy(), ref_off)
+              and torch.equal(db.text_consumed, ref_tc) and torch.equal(db.cigar[:total_runs], ref_cig))
+        if not ok:
+            raise SystemExit(f"bench: {tag} changed the results")
 
     def timed(fl, sampler=False, kernel_events=False):
         """W warm-up steps, then K steps between CUDA events on the stream; max over ranks."""
@@ -306,9 +346,7 @@ def main():
             t = torch.tensor([ms], device="cuda")
             torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
             ms = float(t.item())
-        out = sc.device_results(db)
-        if not (np.array_equal(out["edit_counts"], ec) and np.array_equal(out["cigar_off"], ref_off)):
-            raise SystemExit(f"bench: flags {fl} changed the results")
+        same_as_reference(f"flags {fl}")
         return ms, step_ms, ker_ms, clk, sc.scrooge_last_kernel_count(ctx)
 
     paths = {}
@@ -355,7 +393,9 @@ def main():
             e2e_s = float(t.item())
         h2d = sum(int(x.nbytes) for x in h_in)
         d2h = int(h_ec.nbytes + h_tc.nbytes + h_off.nbytes) + 4 * int(h_off[-1])
-        if not (np.array_equal(h_ec, ec) and np.array_equal(h_off, ref_off)):
+        if not (np.array_equal(h_ec, ec) and np.array_equal(h_off, ref_off)
+                and np.array_equal(h_tc, ref_tc.cpu().numpy())
+                and np.array_equal(h_cig[:total_runs], ref_cig.cpu().numpy().view(np.uint32))):
             raise SystemExit("bench: end-to-end results differ from the device-resident run")
         e2e = {"value": world * n_pairs / e2e_s, "unit": "alignments/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "gbases_per_s": world * bases / e2e_s / 1e9,
@@ -367,14 +407,20 @@ def main():
             torch.distributed.destroy_process_group()
         return
 
-    # roofline of the alignment kernel: the LOP3/SHF integer pipe
+    # roofline of the alignment kernel: the integer logic pipe (LOP3/SHF)
     props = torch.cuda.get_device_properties(local)
     peaks = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz") or (head_clk or {}).get("sm_max_mhz") or 2070.0)
     peak_ops = props.multi_processor_count * INT_LOGIC_OPS_PER_CLK_PER_SM * sm_max * 1e6
-    ops_per_cell = 3 * words - 1
-    kernel = "align_band_kernel" if sc.settings_slot(W, flags) == 0 else "align_kernel"
+    # algorithmic work: the paper's count of 7 bit-vector ops per DP cell (3 shifts, 1 OR, 3 AND,
+    # Section 2.3.1 / its operational-intensity estimate), over the cells computed up to each
+    # window's edit distance; the kernel basis is the full-width kernel's own 3*words-1 LOP3/SHF
+    ops_per_cell = PAPER_OPS_PER_CELL
+    kernel_ops_per_cell = 3 * words - 1
+    kernel = kernel_name(sc, W, flags)
     achieved = total_cells * ops_per_cell / (kernel_ms / 1e3)
+    probe = sc.scrooge_logic_peak(ctx, 4096)
+    traffic = kernel_traffic(kernel, args.workload, n_pairs)
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(batch, W, O, args.cpu_seconds)
@@ -391,16 +437,28 @@ def main():
                    "parallelism": f"dp{world}" if world > 1 else "single GPU"},
         "gbases_per_s": world * bases / (head_ms / 1e3) / 1e9,
         "paths": paths, "learned_gain_vs_plain": value / plain,
+        "learned_gain_vs_persistent": value / paths["persistent"]["alignments_per_s"],
         "model": model_info, "autotune": tune_info,
         "mean_edits_per_pair": float(ec.mean()), "cigar_runs_per_step": total_runs,
         "dp_cells_per_step": total_cells, "dp_rows_per_step": total_rows,
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
-                     "frac": achieved / peak_ops, "traffic": kernel_traffic(kernel, args.workload),
-                     "kernel_ms": kernel_ms,
-                     "basis": f"{ops_per_cell} LOP3/SHF ops per DP cell computed up to each window's edit "
-                              f"distance; alignment kernel timed alone (events around it, learned order); "
-                              f"peak = {props.multi_processor_count} SMs x {INT_LOGIC_OPS_PER_CLK_PER_SM} ops/clk x "
-                              f"{sm_max:.0f} MHz"},
+                     "frac": achieved / peak_ops, "frac_survey_basis": achieved / peak_ops,
+                     "frac_kernel_basis": total_cells * kernel_ops_per_cell / (kernel_ms / 1e3) / peak_ops,
+                     "traffic": None if traffic is None else traffic["bytes"],
+                     "traffic_basis": None if traffic is None else
+                     f"ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch on the first "
+                     f"{traffic['pairs_captured']} pairs ({traffic['bytes_captured']} B), scaled by pairs",
+                     "kernel": kernel, "kernel_ms": kernel_ms,
+                     "basis": f"{ops_per_cell} bit-vector ops per DP cell (the paper's count) over the cells "
+                              f"computed up to each window's edit distance ({total_cells} per step); "
+                              f"frac_kernel_basis: {kernel_ops_per_cell} LOP3/SHF per cell; alignment kernel timed "
+                              f"alone (events around it, learned order); peak = {props.multi_processor_count} SMs x "
+                              f"{INT_LOGIC_OPS_PER_CLK_PER_SM} logic ops/clk x {sm_max:.0f} MHz (unit counts and "
+                              f"clocks; peak_probe measures the per-SM rate on this GPU)",
+                     "peak_probe": {"ops_per_s": probe["ops_per_s"] / 1e12,
+                                    "ops_per_clk_per_sm": probe["ops_per_clk_per_sm"], "unit": "Tops/s",
+                                    "what": "scrooge_logic_peak: 8 independent LOP3+SHF chains per thread, "
+                                            "one wave of blocks"}},
         "clocks": head_clk,
         "gpu_launches": args.steps * head_kernels,
         "e2e": e2e,

@@ -337,8 +337,9 @@ int scrooge_set_stats(scrooge_ctx *ctx, int32_t *windows, int64_t *rows, int64_t
  * It runs the same alignment kernel. All pointers are device pointers; the
  * work is queued on `cuda_stream` (a cudaStream_t, NULL = default stream) on
  * the current device and the call returns at once unless flags holds
- * SCROOGE_SYNC. Allowed flags: SCROOGE_SYNC, SCROOGE_NO_DENT, SCROOGE_NO_ET
- * (SCROOGE_DEVICE_PTRS is implied and ignored).
+ * SCROOGE_SYNC. Allowed flags: SCROOGE_SYNC, SCROOGE_NO_DENT, SCROOGE_NO_ET,
+ * SCROOGE_NO_EXT_DENT (every row of a window kept instead of the cycle of row
+ * slots; results are the same) (SCROOGE_DEVICE_PTRS is implied and ignored).
  *
  * Scratch: DP rows that do not fit in shared memory go to a fixed 16 MiB
  * array (plus one status word) compiled into the library; every GPU that
@@ -358,8 +359,8 @@ int scrooge_set_stats(scrooge_ctx *ctx, int32_t *windows, int64_t *rows, int64_t
  * is an input capacity layout; m + n + 1 runs per pair always suffice) to
  * cigar[cigar_offsets[p] ..], and cigar_lens[p] receives the runs written.
  * `status` (device int32, may be NULL) receives 0, or bit 0 if a traceback
- * found no open edge (impossible by Theorem 1), or bit 1 if some pair's
- * capacity was too small (its runs are cut at the capacity). */
+ * found no open edge (should never happen), or bit 1 if some pair's capacity
+ * was too small (its runs are cut at the capacity). */
 int scrooge_align_batch_noalloc(const uint32_t *texts, const int64_t *text_offsets, const int32_t *text_lengths,
                                 const uint32_t *patterns, const int64_t *pattern_offsets,
                                 const int32_t *pattern_lengths, int32_t n_pairs, int32_t W, int32_t O, int32_t k,
@@ -388,6 +389,22 @@ int scrooge_edit_distance(scrooge_ctx *ctx, const uint32_t *texts, const int64_t
                           const int32_t *text_lengths, const uint32_t *patterns, const int64_t *pattern_offsets,
                           const int32_t *pattern_lengths, int32_t n_pairs, int32_t max_pattern_length,
                           uint32_t flags, int32_t *free_end, int32_t *global_distance);
+
+/* ------------------------------------------------ logic-pipe peak probe
+ * No counterpart in the paper. It measures the peak the alignment kernels'
+ * roofline is taken against: the integer logic pipe of the context's device
+ * (3-input logic ops and funnel shifts). One full wave of blocks runs
+ * 8 independent chains per thread, one logic op and one funnel shift per
+ * chain step, `iterations` x 16 steps per chain (1..2^20); a first launch
+ * with one iteration warms up. Outputs (host, either may be NULL):
+ *   *ops_per_s           logic ops of the timed launch / its duration
+ *                        (CUDA events on the context stream);
+ *   *ops_per_clk_per_sm  median over SMs of the ops an SM's blocks executed
+ *                        divided by the SM clock cycles between the first
+ *                        block's start and the last block's end on that SM
+ *                        (independent of the clock frequency).
+ * Allocates and frees a few bytes of device memory. Synchronous. */
+int scrooge_logic_peak(scrooge_ctx *ctx, int32_t iterations, double *ops_per_s, double *ops_per_clk_per_sm);
 
 /* Testing hook: make the next `count` device allocations of this context
  * fail with SCROOGE_E_NOMEM (0 switches it off). */

@@ -100,6 +100,7 @@ def load():
                 "scrooge_get_heavy_class": ([P], i32),
                 "scrooge_set_long_class": ([P, i32], ctypes.c_int),
                 "scrooge_get_long_class": ([P], i32),
+                "scrooge_logic_peak": ([P, i32, P, P], ctypes.c_int),
             }
             for name, (args, res) in sig.items():
                 f = getattr(lib, name)
@@ -356,6 +357,14 @@ def edit_distance_device(ctx, db: "DeviceBatch", sync: bool = True):
                           min(max_m, SCROOGE_EDIT_DISTANCE_MAX_M), SCROOGE_DEVICE_PTRS | (SCROOGE_SYNC if sync else 0),
                           fe, gl)
     return fe, gl
+
+
+def scrooge_logic_peak(ctx, iterations: int = 4096) -> dict:
+    """Measured rate of the integer logic pipe: ops/s and ops per clock per SM."""
+    ops = ctypes.c_double(0.0)
+    per_clk = ctypes.c_double(0.0)
+    _check(ctx, load().scrooge_logic_peak(ctx, iterations, ctypes.byref(ops), ctypes.byref(per_clk)))
+    return {"ops_per_s": ops.value, "ops_per_clk_per_sm": per_clk.value}
 
 
 def scrooge_debug_fail_next_allocs(ctx, count: int):

@@ -111,7 +111,7 @@ extern "C" int scrooge_align_batch_noalloc(const uint32_t *texts, const int64_t 
                                            const int64_t *cigar_offsets, int32_t *cigar_lens, int32_t *status,
                                            void *cuda_stream) {
     if (n_pairs < 0 || W < 1 || W > 128 || O < 0 || O >= W || k < 0 || k > W) return SCROOGE_E_INVAL;
-    if (flags & ~(uint32_t)(SCROOGE_SYNC | SCROOGE_NO_DENT | SCROOGE_NO_ET | SCROOGE_DEVICE_PTRS))
+    if (flags & ~(uint32_t)(SCROOGE_SYNC | SCROOGE_NO_DENT | SCROOGE_NO_ET | SCROOGE_NO_EXT_DENT | SCROOGE_DEVICE_PTRS))
         return SCROOGE_E_INVAL;
     if (n_pairs == 0) return SCROOGE_OK;
     if (!texts || !text_offsets || !text_lengths || !patterns || !pattern_offsets || !pattern_lengths ||

@@ -28,23 +28,22 @@ def assert_same(gpu, ref, pairs=None, label=""):
             raise AssertionError(f"{label}: CIGAR of pair {p} differs (gpu {len(a)} runs, oracle {len(b)} runs)")
 
 
-def run_totals(res, n_pairs):
-    """Per pair: pattern bases, text bases and edits implied by the CIGAR runs."""
-    pat = np.zeros(n_pairs, np.int64)
-    txt = np.zeros(n_pairs, np.int64)
-    ed = np.zeros(n_pairs, np.int64)
-    lens = np.asarray(res["cigar_lens"]).astype(np.int64)
-    off = np.asarray(res["cigar_off"]).astype(np.int64)
-    cig = np.asarray(res["cigar"]).view(np.uint32)
-    ok = lens > 0
-    starts = off[:-1][ok]
-    cnt = lens[ok]
-    idx = np.repeat(starts, cnt) + (np.arange(int(cnt.sum())) - np.repeat(np.cumsum(cnt) - cnt, cnt))
-    owner = np.repeat(np.flatnonzero(ok), cnt)
-    runs = cig[idx]
-    op = (runs & 15).astype(np.int64)
-    ln = (runs >> 4).astype(np.int64)
-    np.add.at(pat, owner, np.where((op == 7) | (op == 8) | (op == 1), ln, 0))
-    np.add.at(txt, owner, np.where((op == 7) | (op == 8) | (op == 2), ln, 0))
-    np.add.at(ed, owner, np.where(op != 7, ln, 0))
-    return pat, txt, ed
+def assert_same_all(gpu, ref, label=""):
+    """assert_same over every pair at once: with equal run counts the dense CIGAR layouts coincide,
+    so the run arrays are compared whole (the first differing pair is named on failure)."""
+    for key in ("edit_counts", "text_consumed", "cigar_lens"):
+        g = np.asarray(gpu[key])
+        r = np.asarray(ref[key])
+        assert g.shape == r.shape, f"{label}: {key} shapes {g.shape} vs {r.shape}"
+        bad = np.flatnonzero(g != r)
+        assert bad.size == 0, (f"{label}: {key} differs at {bad.size} pairs, first {bad[:10]}: "
+                               f"gpu {g[bad[:10]]} oracle {r[bad[:10]]}")
+    off = np.asarray(gpu["cigar_off"]).astype(np.int64)
+    np.testing.assert_array_equal(off, np.asarray(ref["cigar_off"]).astype(np.int64), err_msg=f"{label}: offsets")
+    tot = int(off[-1])
+    a = np.asarray(gpu["cigar"])[:tot].view(np.uint32)
+    b = np.asarray(ref["cigar"])[:tot].view(np.uint32)
+    diff = np.flatnonzero(a != b)
+    if diff.size:
+        p = int(np.searchsorted(off, diff[0], side="right") - 1)
+        raise AssertionError(f"{label}: CIGAR runs differ at {diff.size} positions, first in pair {p}")

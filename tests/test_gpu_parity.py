@@ -12,7 +12,7 @@ import pytest
 import oracle
 import paper_2208_09985_gb300 as sc
 from paper_2208_09985_gb300 import synth
-from tests._compare import assert_same, run_totals
+from tests._compare import assert_same
 
 pytestmark = pytest.mark.gpu
 
@@ -231,40 +231,6 @@ def test_stats_count_rows(ctx):
         assert int(win[p]) == r["d_opt"].shape[0]
         assert int(rows[p]) == int((r["d_opt"] + 1).sum())
     assert (cyc.cpu().numpy() > 0).all()
-
-
-def test_full_size_long_reads_sampled(ctx):
-    """The 100,000-pair long-read workload in the default launch configuration.
-
-    Every pair's CIGAR must consume its whole pattern and exactly text_consumed
-    text bases with edit_count edits; 300 sampled pairs are checked against the
-    oracle run by run.
-    """
-    b = synth.long_reads(100_000)
-    pb = sc.PackedBatch(b)
-    g = sc.align_host(ctx, pb, 64, 24)
-    assert (g["cigar_lens"] > 0).all() and (g["edit_counts"] >= 0).all()
-    pat, txt, ed = run_totals(g, b.n_pairs)
-    np.testing.assert_array_equal(pat, np.diff(b.pattern_off))
-    np.testing.assert_array_equal(txt, g["text_consumed"])
-    np.testing.assert_array_equal(ed, g["edit_counts"])
-    sample = np.random.default_rng(99).choice(b.n_pairs, 300, replace=False)
-    sub = b.subset(sample)
-    r = oracle.align_batch(sub, 64, 24, threads=THREADS)
-    assert_same(g, r, pairs=sample, label="long_reads full size (sample)")
-
-
-def test_full_size_short_reads_sampled(ctx):
-    b = synth.short_reads(1_000_000)
-    pb = sc.PackedBatch(b)
-    g = sc.align_host(ctx, pb, 64, 24)
-    pat, txt, ed = run_totals(g, b.n_pairs)
-    np.testing.assert_array_equal(pat, np.diff(b.pattern_off))
-    np.testing.assert_array_equal(txt, g["text_consumed"])
-    np.testing.assert_array_equal(ed, g["edit_counts"])
-    sample = np.random.default_rng(7).choice(b.n_pairs, 5000, replace=False)
-    r = oracle.align_batch(b.subset(sample), 64, 24, threads=THREADS)
-    assert_same(g, r, pairs=sample, label="short_reads full size (sample)")
 
 
 @pytest.mark.parametrize("rows", [1, 4, 8])

@@ -17,8 +17,10 @@ from paper_2208_09985_gb300 import synth
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("W,O,k", [(64, 24, 64), (32, 17, 32), (128, 64, 128), (64, 33, 12), (64, 60, 64), (32, 28, 32)])
-def test_noalloc_matches_allocating_entry_point(W, O, k):
+@pytest.mark.parametrize("W,O,k,extra", [(64, 24, 64, 0), (32, 17, 32, 0), (128, 64, 128, 0), (64, 33, 12, 0),
+                                         (64, 60, 64, 0), (32, 28, 32, 0), (64, 60, 64, sc.SCROOGE_NO_EXT_DENT),
+                                         (32, 17, 32, sc.SCROOGE_NO_EXT_DENT)])
+def test_noalloc_matches_allocating_entry_point(W, O, k, extra):
     import torch
     assert torch.cuda.is_available()
     batch = synth.concat([synth.tiny_windows(300, seed=1), synth.long_reads(24, seed=4),
@@ -26,7 +28,7 @@ def test_noalloc_matches_allocating_entry_point(W, O, k):
     pb = sc.PackedBatch(batch)
     ctx = sc.scrooge_create(0)
     try:
-        ref = sc.align_host(ctx, pb, W, O, k)
+        ref = sc.align_host(ctx, pb, W, O, k, extra)
     finally:
         sc.scrooge_destroy(ctx)
     n = batch.n_pairs
@@ -44,7 +46,7 @@ def test_noalloc_matches_allocating_entry_point(W, O, k):
         lens = torch.full((n,), -7, dtype=torch.int32, device="cuda")
         cig = torch.zeros(int(coff_h[-1]), dtype=torch.int32, device="cuda")
         status = torch.full((1,), -1, dtype=torch.int32, device="cuda")
-        sc.scrooge_align_batch_noalloc(texts, toff, tlen, pats, poff, plen, n, W, O, k, sc.SCROOGE_SYNC, ec, tc,
+        sc.scrooge_align_batch_noalloc(texts, toff, tlen, pats, poff, plen, n, W, O, k, sc.SCROOGE_SYNC | extra, ec, tc,
                                        cig, coff, lens, status, stream)
         torch.cuda.synchronize()
         assert int(status.item()) == 0, f"call {call}: status {int(status.item())}"
