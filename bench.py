@@ -139,7 +139,8 @@ def kernel_traffic(kernel: str, workload: str, n_pairs: int):
     h = hashlib.sha256()
     for name in KERNEL_SOURCES[kernel]:
         h.update(open(os.path.join(ROOT, "paper_2208_09985_gb300", "csrc", name), "rb").read())
-    if rec.get("source_sha256") != h.hexdigest() or rec.get("workload") != workload:
+    if (rec.get("source_sha256") != h.hexdigest() or rec.get("workload") != workload
+            or "pairs_captured" not in rec or "dram_bytes_captured" not in rec):
         return None
     captured = int(rec["pairs_captured"])
     return {"bytes": int(rec["dram_bytes_captured"]) * n_pairs / captured, "pairs_captured": captured,

@@ -86,83 +86,6 @@ struct BandMinBlocks {
     static constexpr int value = BW == 2 ? 6 : (G == 8 ? 12 : (G == 4 ? 8 : 6));
 };
 
-// Full-width DC of the windows in `full_mask` (Algorithm 1 on NW words per
-// entry, as in the full-width kernel), rows stored to `rows` (this lane's first
-// column of row 0; [row][column][pair][NW words]); d_opt of those windows is set
-// on their traceback lanes. Kept out of line: it is rare, and its registers
-// must not count against the banded loop.
-template <int G, int NW>
-__device__ __noinline__ void full_width_dc(const uint2 *pseq, int64_t pblk, int pj, const uint2 *tseq, int64_t tblk,
-                                           int ti, int nw, int mw, int k, int l, int tbl, uint32_t tbl_all,
-                                           uint32_t full_mask, bool lane_stores, uint32_t *rows, int row_words,
-                                           int &d_opt) {
-    constexpr int C = 32 * NW / G;
-    constexpr int PPW = 32 / G;
-    const bool full = (full_mask >> tbl) & 1u;
-    const int colbase = (G - 1 - l) * C;
-    uint32_t P0[NW], P1[NW], mm[NW], T0, T1;
-#pragma unroll
-    for (int w = 0; w < NW; ++w) {
-        load32(pseq, pblk, (int64_t)pj + 32 * w, P0[w], P1[w]);
-        mm[w] = prefix_mask(mw - 32 * w);
-    }
-    load32(tseq, tblk, (int64_t)ti + colbase, T0, T1);
-    const int real_cols = nw - colbase;
-    uint32_t FX[C][NW];  // X of the next row
-#pragma unroll
-    for (int c = 0; c < C; ++c)
-#pragma unroll
-        for (int w = 0; w < NW; ++w) FX[c][w] = mm[w];
-    uint32_t fdone = tbl_all & ~full_mask;
-    uint32_t bot[NW];
-#pragma unroll
-    for (int w = 0; w < NW; ++w) bot[w] = 0u;
-    for (int st = 0; fdone != tbl_all; ++st) {
-        const int d = st - l;
-        const bool ddone = (fdone >> tbl) & 1u;
-        uint32_t pR[NW], pS[NW];
-#pragma unroll
-        for (int w = 0; w < NW; ++w) {
-            const uint32_t v = __shfl_up_sync(kFull, bot[w], 1);
-            pR[w] = (l == 0) ? prefix_mask(mw - d - 32 * w) : v;
-        }
-        bool found = false;
-        if (!ddone && d >= 0 && d <= k) {
-            shl1<NW>(pR, pS);
-            uint32_t *rowp = rows + (int64_t)d * row_words;
-#pragma unroll
-            for (int c = C - 1; c >= 0; --c) {
-                // PM[text[i]] from the pattern planes
-                const uint32_t m0 = 0u - ((T0 >> (31 - c)) & 1u);
-                const uint32_t m1 = 0u - ((T1 >> (31 - c)) & 1u);
-                const bool real = c < real_cols;
-                uint32_t R[NW], S[NW];
-#pragma unroll
-                for (int w = 0; w < NW; ++w) {
-                    const uint32_t pm = real ? ((P0[w] ^ m0) | (P1[w] ^ m1)) : kFull;
-                    R[w] = FX[c][w] & (pS[w] | pm);
-                }
-                shl1<NW>(R, S);
-                if (lane_stores) store_vec<NW, NW>(rowp + c * NW * PPW, R);
-#pragma unroll
-                for (int w = 0; w < NW; ++w) {
-                    FX[c][w] = S[w] & pR[w] & pS[w];
-                    pR[w] = R[w];
-                    pS[w] = S[w];
-                }
-            }
-#pragma unroll
-            for (int w = 0; w < NW; ++w) bot[w] = pR[w];
-            found = (l == G - 1) && ((pR[0] >> 31) == 0u);
-        }
-        const uint32_t fm = __ballot_sync(kFull, found);
-        const int dl = st - (G - 1);
-        if (full && !ddone && ((fm >> tbl) & 1u) && d_opt < 0) d_opt = dl;
-        fdone |= fm;
-        if (dl >= k) fdone = tbl_all;
-    }
-}
-
 // One window of one pair slot of a banded launch, as the DC and traceback routines see it.
 struct BandWindow {
     const uint2 *tseq, *pseq;
@@ -809,7 +732,7 @@ cudaError_t occupancy_band(int nww, int bw, int lanes, int wpb, size_t smem, int
 }
 
 bool supported_band(int nww, int bw, int lanes) {
-    if (nww == 2 && bw == 1) return lanes == 2 || lanes == 4 || lanes == 8;
+    if (nww == 2 && bw == 1) return lanes == 1 || lanes == 2 || lanes == 4 || lanes == 8;
     if (nww == 2 && bw == 2) return lanes == 4 || lanes == 8;
     return nww == 4 && bw == 2 && (lanes == 8 || lanes == 16);
 }

@@ -234,12 +234,80 @@ namespace {
 
 // One alignment-kernel launch: which kernel, its shape and its parameters.
 struct LaunchPlan {
-    bool band = false, sene = true, ws = false;
+    bool band = false, sene = true, ws = false, lane = false;
     int words = 0, nww = 2, bw = 1, G = 0, wpb = 1, blocks = 0;
     size_t smem = 0;
     TableShape ts{};
     AlignParams p{};
 };
+
+// Plan of the banded kernel with one lane per pair (windows of 33..64 bases, 32-diagonal band).
+int make_lane_plan(scrooge_ctx *c, const AlignParams &base, uint32_t flags, DevBuf &spill, DevBuf &fallback,
+                   const KernelConfig &kc, LaunchPlan &out) {
+    const int W = base.W, O = base.O, k = base.k, L = W - O;
+    const bool dent = !(flags & SCROOGE_NO_DENT);
+    AlignParams p = base;
+    const int ncol = std::min(64, (((dent ? std::min(L + 1, W) : W) + 7) / 8) * 8);
+    p.et = 1;
+    p.sene = 1;
+    p.ncol = ncol;
+    p.sw = 1;
+    p.rstride = ncol * 32;
+    p.ring = k + 1;
+    const int rows_needed = std::min(k, band_rows_for(1) - 1) + 1;
+    int rcap = std::min(kc.rows, rows_needed);
+    int wpb = kc.wpb;
+    auto warp_words = [&](int rows) { return (int64_t)kLaneTableBytes / 4 + (int64_t)rows * ncol * 32; };
+    while (rcap > 1 && (size_t)wpb * warp_words(rcap) * 4 > c->smem_optin) --rcap;
+    while (wpb > 1 && (size_t)wpb * warp_words(rcap) * 4 > c->smem_optin) --wpb;
+    p.rcap = rcap;
+    p.table_words_per_warp = (int32_t)(rcap * ncol * 32);
+    p.smem_words_per_warp = (int32_t)warp_words(rcap);
+    const size_t smem = (size_t)wpb * p.smem_words_per_warp * 4;
+    int per_sm = 0;
+    cudaError_t e = occupancy_lane(ncol, wpb, smem, &per_sm);
+    if (e != cudaSuccess) return cuda_fail(c, e, "occupancy query");
+    if (per_sm < 1) return fail(c, SCROOGE_E_INVAL, "kernel config does not fit on an SM (smem %zu B)", smem);
+    const int64_t warps = ((int64_t)p.n_pairs + 31) / 32;
+    const int64_t want_blocks = (warps + wpb - 1) / wpb;
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(want_blocks, (int64_t)per_sm * c->sm_count));
+    p.slots_per_warp = 0;
+    // rows evicted from the slot cycle: 0 .. rows_needed - 1 - rcap
+    p.spill_words_per_pair = (int64_t)std::max(0, rows_needed - rcap) * ncol * 32;  // per warp
+    int rc;
+    if ((rc = ensure(c, spill, (size_t)blocks * wpb * (size_t)std::max<int64_t>(p.spill_words_per_pair, 4) * 4,
+                     "DP row scratch")))
+        return rc;
+    p.spill = (uint32_t *)spill.p;
+    p.fb = nullptr;
+    p.fb_words_per_warp = 0;
+    p.fb_ncol = table_shape(W, O, 2, 4, dent, true).ncol;  // full-width fallback: 4 lanes per window
+    p.fb_words_per_warp = band_fallback_words(k, p.fb_ncol, 8, 2, 1);
+    if (p.fb_words_per_warp > 0) {
+        if ((rc = ensure(c, fallback, (size_t)blocks * wpb * (size_t)p.fb_words_per_warp * 4,
+                         "full-width fallback scratch")))
+            return rc;
+        p.fb = (uint32_t *)fallback.p;
+    }
+    TableShape ts;
+    ts.ncol = ncol;
+    ts.swp = 1;
+    ts.nv = 1;
+    out.band = true;
+    out.lane = true;
+    out.nww = 2;
+    out.bw = 1;
+    out.ws = false;
+    out.sene = true;
+    out.words = 2;
+    out.G = 1;
+    out.wpb = wpb;
+    out.blocks = blocks;
+    out.smem = smem;
+    out.ts = ts;
+    out.p = p;
+    return SCROOGE_OK;
+}
 
 // Shape of the kernel a call with these flags uses (banded or full width), sized for the device
 // and the context's kernel settings; sizes the row scratch in `spill` (and the banded kernel's
@@ -264,6 +332,9 @@ int make_plan(scrooge_ctx *c, const AlignParams &base, bool band, uint32_t flags
                           : (words == 2 ? supported_w64(lanes, sene, swp) : supported_w128(lanes, sene, swp));
     };
     if (band && !supported_band(nww, bw, G)) G = nww == 2 ? 4 : 8;
+    if (band && G == 1 && slots > 0) G = 4;  // a pair of its own per warp: the lanes of one pair share it
+    // one lane per pair (align_lane.cu): stored columns rounded to 8, not to a lane chunk
+    if (band && G == 1) return make_lane_plan(c, base, flags, spill, fallback, kc, out);
     TableShape ts = table_shape(W, O, words, G, dent, sene);
     if (band) ts.swp = bw;  // one band of bw 32-bit words per stored entry
     if (!band && !supported(G, ts.swp)) {  // the edge-storing ablation exists for the default lane count only
@@ -345,6 +416,7 @@ int make_plan(scrooge_ctx *c, const AlignParams &base, bool band, uint32_t flags
 
 cudaError_t launch_plan(const LaunchPlan &lp, cudaStream_t st) {
     if (lp.ws) return launch_align_ws(lp.p, lp.blocks, lp.smem, st);
+    if (lp.lane) return launch_align_lane(lp.p, lp.wpb, lp.blocks, lp.smem, st);
     if (lp.band) return launch_align_band(lp.p, lp.nww, lp.bw, lp.G, lp.wpb, lp.blocks, lp.smem, st);
     switch (lp.words) {
         case 1: return launch_align_w32(lp.p, lp.G, lp.sene, lp.ts.swp, lp.wpb, lp.blocks, lp.smem, st);
@@ -693,7 +765,7 @@ int scrooge_autotune(scrooge_ctx *c, const uint32_t *texts, const int64_t *text_
     const int ix = kcfg_index(use_band(W, flags) ? band_slot_for(W) : words);
     const KernelConfig saved = c->kcfg[ix];
     const int32_t saved_class = c->heavy_class;
-    const int lanes_opts[5][3] = {{1, 2, 4}, {2, 4, 8}, {8, 16, 0}, {2, 4, 8}, {8, 16, 0}};
+    const int lanes_opts[5][4] = {{1, 2, 4, 0}, {2, 4, 8, 0}, {8, 16, 0, 0}, {1, 2, 4, 8}, {8, 16, 0, 0}};
     const int rows_opts[] = {1, 2, 3, 4, 6, 8, 10, 12, 16, 20};
     const int wpb_opts[] = {1, 2};
     const int classes[] = {16, 15, 14, 13, 12, 11, 10, 0};
@@ -759,7 +831,7 @@ int scrooge_autotune(scrooge_ctx *c, const uint32_t *texts, const int64_t *text_
     if (tune_classes) rc = sweep_classes();
     float best = -1.f;
     KernelConfig best_cfg = saved;
-    for (int li = 0; li < 3 && rc == SCROOGE_OK; ++li) {
+    for (int li = 0; li < 4 && rc == SCROOGE_OK; ++li) {
         const int lanes = lanes_opts[ix][li];
         if (!lanes) continue;
         for (int rows : rows_opts) {

@@ -38,6 +38,7 @@ struct AlignParams {
     int64_t spill_words_per_pair;   // words of that region per warp
     uint32_t *fb;                   // banded kernel: full-width rows and state of windows beyond the band
     int64_t fb_words_per_warp;      // words of that region per warp
+    int32_t fb_ncol;                // one-lane-per-pair kernel: stored columns of a full-width fallback row
     int32_t smem_words_per_warp;
     int32_t table_words_per_warp;
     const int32_t *order;   // optional pair order (slot -> pair id)
@@ -139,6 +140,13 @@ inline int ext_dent_ring(int W, int O, int k, int lanes, bool on) {
     if (ring < (k + 2) / 2) ring = (k + 2) / 2;
     return on && ring < k + 1 ? ring : k + 1;
 }
+// Banded kernel with one lane per pair (align_lane.cu) for windows of 33..64 bases: ncol (a
+// multiple of 8, at most 64) stored columns per row, rcap rows per lane in shared memory after a
+// per-warp table of kLaneTableBytes; windows beyond the band are recomputed at full width by
+// groups of 4 lanes (fb: k+1 rows of fb_ncol columns x 8 windows x 2 words per warp).
+constexpr int kLaneTableBytes = 3072;
+cudaError_t launch_align_lane(const AlignParams &, int wpb, int blocks, size_t smem, cudaStream_t);
+cudaError_t occupancy_lane(int ncol, int wpb, size_t smem, int *blocks_per_sm);
 // Warp-specialised banded kernel (align_band.cu): blocks of 4 DC warps (4 lanes per pair, two
 // sets of 8 pairs each) and one traceback warp; persistent launches only. Shared memory per block:
 // 8 sets x smem_words_per_warp words, then ws_meta_bytes().

@@ -54,7 +54,7 @@ def _check_paths(ctx, batch, W, O, paths, label):
     pb = sc.PackedBatch(batch)
     ref = oracle.align_batch(batch, W, O, W, threads=THREADS)
     # capacity for every run of the batch (the oracle's count) so no call is cut short
-    db = sc.DeviceBatch(pb, cigar_capacity=int(ref["cigar_off"][-1]) + 16)
+    db = sc.DeviceBatch(pb, cigar_capacity=int(np.asarray(ref["cigar_lens"]).astype(np.int64).sum()) + 16)
     for name, flags in paths:
         got = _gpu(ctx, db, W, O, flags)
         assert_same_all(got, ref, label=f"{label} {name} W={W} O={O}")

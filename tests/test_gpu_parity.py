@@ -59,7 +59,7 @@ def test_random_edge_cases_all_lane_configs(ctx, W):
     rng = np.random.default_rng(W)
     b = synth.random_pairs(300, max_text=4 * W + 5, max_pattern=4 * W + 5, seed=100 + W)
     for slot, flags, name in _kernels(W):
-        lanes_opts = {1: [1, 2, 4], 2: [2, 4, 8], 4: [8, 16], 0: [2, 4, 8], 3: [8, 16]}[slot]
+        lanes_opts = {1: [1, 2, 4], 2: [2, 4, 8], 4: [8, 16], 0: [1, 2, 4, 8], 3: [8, 16]}[slot]
         saved = sc.scrooge_get_kernel_config(ctx, slot)
         try:
             for lanes in lanes_opts:
@@ -75,7 +75,7 @@ def test_random_edge_cases_all_lane_configs(ctx, W):
             sc.scrooge_set_kernel_config(ctx, slot, *saved)
 
 
-@pytest.mark.parametrize("lanes", [2, 4, 8])
+@pytest.mark.parametrize("lanes", [1, 2, 4, 8])
 def test_band_fallback_windows(ctx, lanes):
     """Windows whose edit distance exceeds the band (d_opt > 15) are recomputed at full width."""
     b = synth.concat([synth.fixed_error(30, 0.25, length=600, seed=61), synth.fixed_error(30, 0.35, length=400, seed=62),
@@ -112,7 +112,7 @@ def test_kernel_shapes_w64(ctx):
     for slot, flags, name in _kernels(64):
         saved = sc.scrooge_get_kernel_config(ctx, slot)
         try:
-            for lanes in (2, 4, 8):
+            for lanes in ((1, 2, 4, 8) if slot == 0 else (2, 4, 8)):
                 for rows in (1, 6, 12, 65):
                     for wpb in (1, 2):
                         sc.scrooge_set_kernel_config(ctx, slot, lanes, rows, wpb)
@@ -314,7 +314,7 @@ def test_extended_dent_row_cycle(ctx, W, O):
     deep = max(int(oracle.align_pair(b.text(p), b.pattern(p), W, O, W)["d_opt"].max(initial=-1)) for p in range(40))
     assert deep >= (W + 2) // 2
     for slot, flags, name in _kernels(W):
-        lanes_opts = {1: [1, 2, 4], 2: [2, 4, 8], 4: [8, 16], 0: [2, 4, 8], 3: [8, 16]}[slot]
+        lanes_opts = {1: [1, 2, 4], 2: [2, 4, 8], 4: [8, 16], 0: [1, 2, 4, 8], 3: [8, 16]}[slot]
         saved = sc.scrooge_get_kernel_config(ctx, slot)
         try:
             for lanes in lanes_opts:
