@@ -390,6 +390,18 @@ int scrooge_edit_distance(scrooge_ctx *ctx, const uint32_t *texts, const int64_t
                           const int32_t *pattern_lengths, int32_t n_pairs, int32_t max_pattern_length,
                           uint32_t flags, int32_t *free_end, int32_t *global_distance);
 
+/* Bounded device waits (no counterpart in the paper). The warp-specialised
+ * blocks (SCROOGE_WARP_SPECIALIZED) hand windows between warps through
+ * shared-memory barriers, and every wait on one is bounded: when it gives up,
+ * the warp leaves and a synchronous call returns SCROOGE_E_TIMEOUT. `polls`
+ * = 0 (the default) allows 2^24 polls with mbarrier.try_wait, which may
+ * suspend the waiting thread between polls; polls > 0 allows that many
+ * polls with the non-suspending mbarrier.test_wait, so a wait that nothing
+ * completes ends after a short, bounded time (a small value makes the waits
+ * give up, which is how the time-out path is tested). Applies to later calls
+ * on this context. */
+int scrooge_set_wait_limit(scrooge_ctx *ctx, int32_t polls);
+
 /* ------------------------------------------------ logic-pipe peak probe
  * No counterpart in the paper. It measures the peak the alignment kernels'
  * roofline is taken against: the integer logic pipe of the context's device

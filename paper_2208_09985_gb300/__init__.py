@@ -101,6 +101,7 @@ def load():
                 "scrooge_set_long_class": ([P, i32], ctypes.c_int),
                 "scrooge_get_long_class": ([P], i32),
                 "scrooge_logic_peak": ([P, i32, P, P], ctypes.c_int),
+                "scrooge_set_wait_limit": ([P, i32], ctypes.c_int),
             }
             for name, (args, res) in sig.items():
                 f = getattr(lib, name)
@@ -357,6 +358,11 @@ def edit_distance_device(ctx, db: "DeviceBatch", sync: bool = True):
                           min(max_m, SCROOGE_EDIT_DISTANCE_MAX_M), SCROOGE_DEVICE_PTRS | (SCROOGE_SYNC if sync else 0),
                           fe, gl)
     return fe, gl
+
+
+def scrooge_set_wait_limit(ctx, polls: int = 0):
+    """Polls per bounded device wait of later calls (0: the default bound)."""
+    return _check(ctx, load().scrooge_set_wait_limit(ctx, polls))
 
 
 def scrooge_logic_peak(ctx, iterations: int = 4096) -> dict:

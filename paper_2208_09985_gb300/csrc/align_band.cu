@@ -432,9 +432,24 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
                  : "memory");
 }
 
-// Wait for the completion of the phase of parity `parity`; false after about 2^24 tries.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
+// Wait for the completion of the phase of parity `parity`. limit == 0: up to 2^24 polls with
+// mbarrier.try_wait (which may suspend the thread for a while between polls); limit > 0: up to
+// `limit` polls with the non-suspending mbarrier.test_wait, so a wait that nothing completes ends
+// after a bounded, short time. False when the polls ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, int limit) {
     const uint32_t a = smem_addr(bar);
+    if (limit > 0) {
+        for (int it = 0; it < limit; ++it) {
+            uint32_t ok;
+            asm volatile(
+                "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+                : "=r"(ok)
+                : "r"(a), "r"(parity)
+                : "memory");
+            if (ok) return true;
+        }
+        return false;
+    }
     for (int it = 0; it < (1 << 24); ++it) {
         uint32_t ok;
         asm volatile(
@@ -494,7 +509,7 @@ __global__ void __launch_bounds__(32 * (kWsDcWarps + 1), 3) align_ws_kernel(cons
         for (int r = 0; !(fin[0] && fin[1]); ++r) {
             const int x = r & 1;
             if (fin[x]) continue;
-            const bool timed_out = rounds[x] > 0 && !mbar_wait(empty_bar + w * 2 + x, (rounds[x] - 1) & 1);
+            const bool timed_out = rounds[x] > 0 && !mbar_wait(empty_bar + w * 2 + x, (rounds[x] - 1) & 1, p.wait_limit);
             if (__any_sync(kFull, timed_out)) {  // the whole warp leaves together
                 if (lane == 0) atomicOr(p.status, 8);
                 return;
@@ -576,7 +591,7 @@ __global__ void __launch_bounds__(32 * (kWsDcWarps + 1), 3) align_ws_kernel(cons
         for (int r = 0; !__all_sync(kFull, fin[0] && fin[1]); ++r) {
             const int x = r & 1;
             const bool waited = !fin[x];
-            const bool timed_out = waited && !mbar_wait(full_bar + w * 2 + x, rounds[x] & 1);
+            const bool timed_out = waited && !mbar_wait(full_bar + w * 2 + x, rounds[x] & 1, p.wait_limit);
             if (__any_sync(kFull, timed_out)) {  // the whole warp leaves together
                 if (lane == 0) atomicOr(p.status, 8);
                 return;

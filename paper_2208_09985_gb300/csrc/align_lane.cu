@@ -14,19 +14,23 @@
 // with 1s shifted in at the band edges. It is exact for windows whose edit
 // distance is at most 15 (see align_band.cu); the others are recomputed at
 // full width (Algorithm 1 on two words, Section 2.2.1) by groups of four
-// lanes, eight such windows at a time.
+// lanes, up to eight such windows per round.
 //
 // Registers hold the whole window: X (the part of the next row that comes
-// from the current one) and PMrel for all 64 columns. A row is 64 cells of
-// one 3-input logic op on its dependency chain and two shifts and one logic
-// op off it.
+// from the current one) and PMrel for all 64 columns, both in complement
+// form (a set bit means reachable), where the band edges shift in 0s and the
+// two shifts of a cell are plain shifts. A row is 64 cells of one 3-input
+// logic op on its dependency chain and two shifts and one logic op off it.
+// The row is a single unrolled block: a second inlined copy of it (even one
+// never executed) measured 45% slower.
 //
 // Storage (SENE, Section 2.4.1; DENT, Section 2.4.2). Only entries of the
 // columns 0..W-O (rounded up to 8) are stored, one word per cell. The last
 // `rcap` rows of each lane are kept in a cycle of row slots in shared memory
 // laid out [slot][column][lane], so every access of a lane falls on its own
 // bank whatever its column. A row that is about to be overwritten is copied
-// to a per-warp device area first ([row][column][lane]). ET (Section 2.4.3)
+// to a per-warp device area first ([row][column][lane]). Stored entries are in
+// complement form; the traceback inverts what it reads. ET (Section 2.4.3)
 // stops a lane at the first row that reaches the window start, so the slots
 // then hold rows d_opt-rcap+1 .. d_opt: the rows the traceback (Section
 // 2.2.2) reads first, and usually the only ones it reads.
@@ -125,23 +129,22 @@ __device__ __forceinline__ void lane_fetch(const AlignParams &p, LaneTable &lt, 
     }
 }
 
-// One band row of a lane's window, columns 63 down to 0: pR enters as the column
-// right of the window and leaves as column 0. Stores the stored columns to `rowp`
-// (this lane's first word of the row slot) when `st`; with EVICT the row that held
-// the slot is first copied to `evp`.
-template <int NC8, bool EVICT>
-__device__ __forceinline__ void lane_dc_row(uint32_t (&XA)[64], const uint32_t (&PMC)[64], uint32_t &pR, bool st,
-                                            uint32_t *rowp, uint32_t *evp) {
+// One band row of a lane's window, columns 63 down to 0, in complement form (a set bit means
+// the entry is reachable: C = ~V). pC enters as the column right of the window and leaves as
+// column 0. With the complement the band edges shift in 0s, so both shifts are plain shifts:
+//     C[i][d] = CX[i] | (C[i+1][d] & CPM[i]),
+//     CX[i]   = C[i+1][d-1] | (C[i+1][d-1] >> 1) | (C[i][d-1] << 1)   (the next row's part).
+// Stores the stored columns to `rowp` (this lane's first word of the row slot) when `st`.
+template <int NC8>
+__device__ __forceinline__ void lane_dc_row(uint32_t (&CX)[64], const uint32_t (&CPM)[64], uint32_t &pC, bool st,
+                                            uint32_t *rowp) {
 #pragma unroll
     for (int c = 63; c >= 0; --c) {
-        const uint32_t R = XA[c] & (pR | PMC[c]);
-        if (c < 8 * NC8 && st) {
-            if (EVICT) evp[c * 32] = rowp[c * 32];
-            rowp[c * 32] = R;
-        }
-        // next row: S = V[i+1][d], D = V[i+1][d] >> 1, I = V[i][d] << 1 (1s shifted in)
-        XA[c] = pR & lane_shr1(pR) & lane_shl1(R);
-        pR = R;
+        const uint32_t C = CX[c] | (pC & CPM[c]);
+        if (c < 8 * NC8 && st) rowp[c * 32] = C;
+        // next row: S = C[i+1][d], D = C[i+1][d] >> 1, I = C[i][d] << 1
+        CX[c] = pC | (pC >> 1) | (C << 1);
+        pC = C;
     }
 }
 
@@ -225,8 +228,8 @@ __device__ __forceinline__ void lane_window_tb(const AlignParams &p, LaneTable &
                 if (fbg < 0) {
                     const uint32_t *rp = (r > ring_lo ? ring + rs * ROWW : spill + (int64_t)r * ROWW) + i * 32;
                     const int kk = j - i + kLB0;  // band bit of (i, j); 0..30 on the path
-                    const uint32_t v1 = ld1 ? rp[32] : 0u;
-                    const uint32_t v0 = tx ? rp[0] : 0u;
+                    const uint32_t v1 = ld1 ? ~rp[32] : 0u;  // stored in complement form
+                    const uint32_t v0 = tx ? ~rp[0] : 0u;
                     const uint64_t q1 = (1ull << 63) | ((uint64_t)v1 << 31);  // band bit kk-1 at position kk
                     t1 = (uint32_t)((q1 << kk) >> 62);
                     r0b = (uint32_t)((((uint64_t)v0 << 32) << (kk + 1)) >> 63);
@@ -324,7 +327,7 @@ __global__ void __launch_bounds__(64, 5) align_lane_kernel(const AlignParams p) 
         const uint2 *tseq = reinterpret_cast<const uint2 *>(p.texts + (active ? lt.toff[lane] >> 4 : 0));
         const uint2 *pseq = reinterpret_cast<const uint2 *>(p.patterns + (active ? lt.poff[lane] >> 4 : 0));
 
-        // ---- window set-up: X of row 0 and PMrel[text[i]] for the 64 columns
+        // ---- window set-up, in complement form: CX of row 0 and ~PMrel[text[i]] for the 64 columns
         uint32_t XA[64], PMC[64];
         {
             uint32_t Ta0, Ta1, Tb0, Tb1, Pa0, Pa1, Pb0, Pb1, Pc0, Pc1;
@@ -344,14 +347,14 @@ __global__ void __launch_bounds__(64, 5) align_lane_kernel(const AlignParams p) 
                 const uint32_t m1 = (uint32_t)((int32_t)(t1 << (c & 31)) >> 31);
                 const uint32_t w0 = c < 32 ? __funnelshift_lc(Pb0, Pa0, c + 1) : __funnelshift_lc(Pc0, Pb0, c - 31);
                 const uint32_t w1 = c < 32 ? __funnelshift_lc(Pb1, Pa1, c + 1) : __funnelshift_lc(Pc1, Pb1, c - 31);
-                PMC[c] = (w0 ^ m0) | (w1 ^ m1);
-                XA[c] = c < 32 ? __funnelshift_l(S1, S0, c) : __funnelshift_l(S2, S1, c - 32);
+                PMC[c] = ~((w0 ^ m0) | (w1 ^ m1));  // bit j set: pattern base j equals text base c
+                XA[c] = ~(c < 32 ? __funnelshift_l(S1, S0, c) : __funnelshift_l(S2, S1, c - 32));
             }
             if (__any_sync(kFull, nw < 64)) {
                 // columns at or past the end of the text window match nothing
                 const uint32_t v0 = ~prefix_mask(nw), v1 = ~prefix_mask(nw - 32);
 #pragma unroll
-                for (int c = 0; c < 64; ++c) PMC[c] |= (uint32_t)((int32_t)((c < 32 ? v0 : v1) << (c & 31)) >> 31);
+                for (int c = 0; c < 64; ++c) PMC[c] &= ~(uint32_t)((int32_t)((c < 32 ? v0 : v1) << (c & 31)) >> 31);
             }
         }
 
@@ -361,25 +364,35 @@ __global__ void __launch_bounds__(64, 5) align_lane_kernel(const AlignParams p) 
         int slot = 0;  // row slot of row d
         for (int d = 0; d <= dmax; ++d) {
             if (!__any_sync(kFull, busy)) break;
-            // the column right of the window: bits j < m_w - d of R[n][d] are 1
-            uint32_t pR = prefix_mask(mw - d - 64 + kLB0);
+            // the column right of the window: bits j < m_w - d of R[n][d] are 1 (0 in complement)
+            uint32_t pC = ~prefix_mask(mw - d - 64 + kLB0);
             uint32_t *rowp = ring + slot * ROWW;
-            if (d >= rcap)
-                lane_dc_row<NC8, true>(XA, PMC, pR, busy, rowp, spill + (int64_t)(d - rcap) * ROWW);
-            else
-                lane_dc_row<NC8, false>(XA, PMC, pR, busy, rowp, nullptr);
-            if (busy && ((pR >> (31 - kLB0)) & 1u) == 0u) {
+            if (d >= rcap) {  // the slot's row (d - rcap) goes to the device area first
+                uint32_t *evp = spill + (int64_t)(d - rcap) * ROWW;
+#pragma unroll 1
+                for (int c0 = 0; c0 < 8 * NC8; c0 += 8) {
+                    uint32_t v[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) v[q] = busy ? rowp[(c0 + q) * 32] : 0u;
+#pragma unroll
+                    for (int q = 0; q < 8; ++q)
+                        if (busy) evp[(c0 + q) * 32] = v[q];
+                }
+            }
+            lane_dc_row<NC8>(XA, PMC, pC, busy, rowp);
+            if (busy && ((pC >> (31 - kLB0)) & 1u) != 0u) {
                 d_opt = d;
                 busy = false;
             }
             slot = slot + 1 == rcap ? 0 : slot + 1;
         }
 
-        // ---- windows beyond the band: full-width DC by groups of kLFbLanes lanes, kLFbWin at a time
-        uint32_t pend = __ballot_sync(kFull, active && d_opt < 0 && k >= kLBandRows);
+        // ---- windows beyond the band: full-width DC by groups of kLFbLanes lanes, up to kLFbWin of
+        // them per round; a window beyond that waits (keeps its cursors) and is recomputed next round
+        const uint32_t pend = __ballot_sync(kFull, active && d_opt < 0 && k >= kLBandRows);
         int fbg = -1;
-        bool traced = false;
-        while (pend) {
+        bool wait = false;
+        if (pend) {
             uint32_t take = 0, rest = pend;
             for (int t = 0; t < kLFbWin && rest; ++t) {
                 const uint32_t b = rest & (0u - rest);
@@ -410,15 +423,11 @@ __global__ void __launch_bounds__(64, 5) align_lane_kernel(const AlignParams p) 
                 d_opt = got;
                 fbg = myg;
             }
-            pend &= ~take;
-            if (pend) {  // more windows wait for the fallback area: trace these now
-                lane_window_tb<NC8>(p, lt, lane, mine, d_opt, fbg, nw, mw, ring, spill, fb, rcap, stats);
-                if (mine) traced = true;
-            }
+            wait = ((rest >> lane) & 1u) != 0u;
         }
 
         // ---- GenASM-TB, every lane on its own pair
-        lane_window_tb<NC8>(p, lt, lane, active && !traced, d_opt, fbg, nw, mw, ring, spill, fb, rcap, stats);
+        lane_window_tb<NC8>(p, lt, lane, active && !wait, d_opt, fbg, nw, mw, ring, spill, fb, rcap, stats);
         __syncwarp();
     }
 }

@@ -87,6 +87,12 @@ int scrooge_set_stream(scrooge_ctx *c, void *cuda_stream) {
     return SCROOGE_OK;
 }
 
+int scrooge_set_wait_limit(scrooge_ctx *c, int32_t polls) {
+    if (!c || polls < 0) return SCROOGE_E_INVAL;
+    c->wait_limit = polls;
+    return SCROOGE_OK;
+}
+
 int scrooge_debug_fail_next_allocs(scrooge_ctx *c, int32_t count) {
     if (!c || count < 0) return SCROOGE_E_INVAL;
     c->fail_allocs = count;
@@ -571,6 +577,7 @@ int scrooge_align_batch(scrooge_ctx *c, const uint32_t *texts, const int64_t *te
     if ((flags & SCROOGE_PERSISTENT) && (rc = ensure(c, c->queue, 256, "work queues"))) return rc;
     for (LaunchPlan *lp : {&plan, &heavy, &lng}) {
         lp->p.status = (int32_t *)c->status.p;
+        lp->p.wait_limit = c->wait_limit;
         if (flags & SCROOGE_PERSISTENT) {
             lp->p.queue = (int32_t *)c->queue.p + (lp == &heavy ? 16 : (lp == &lng ? 32 : 0));
             lp->p.order = (c->order && c->order_n == n_pairs) ? c->order : nullptr;
@@ -674,7 +681,7 @@ int scrooge_align_batch(scrooge_ctx *c, const uint32_t *texts, const int64_t *te
             ((unsigned long long)plan.wpb << 32) | (unsigned long long)plan.blocks,
             (unsigned long long)(uintptr_t)c->st_rows, (unsigned long long)(uintptr_t)c->st_cells,
             (unsigned long long)(uintptr_t)c->st_windows, (unsigned long long)(uintptr_t)plan.p.fb,
-            (unsigned long long)band,
+            (unsigned long long)band | ((unsigned long long)(uint32_t)c->wait_limit << 8),
             use_heavy ? (((unsigned long long)heavy.G << 48) | ((unsigned long long)heavy.p.rcap << 32) |
                          ((unsigned long long)heavy.wpb << 24) | (unsigned long long)heavy.blocks)
                       : 0ull,

@@ -34,6 +34,7 @@ struct scrooge_ctx {
     // (autotuned on GB300)
     scrooge::KernelConfig kcfg[5] = {{2, 8, 2}, {4, 4, 2}, {8, 8, 2}, {4, 8, 2}, {8, 6, 2}};
     int fail_allocs = 0;  // testing hook: fail the next N device allocations
+    int32_t wait_limit = 0;  // polls per bounded device wait (0: the kernel's default bound)
     scrooge::DevBuf spill, status, fallback, spill2, spill3, fallback2;
     // learned launches: pairs in load classes >= heavy_class run on the full-width kernel, pairs in
     // work classes >= long_class one per warp on stream3 (16: none); the banded kernel runs the rest

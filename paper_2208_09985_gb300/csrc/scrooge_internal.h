@@ -46,6 +46,7 @@ struct AlignParams {
     const int64_t *range_lo;  // persistent mode: only slots [*range_lo, *range_hi) of the order
     const int64_t *range_hi;  // (nullptr: 0 and n_pairs)
     int32_t slots_per_warp;   // pair slots of a warp that take pairs (0: all 32/G)
+    int32_t wait_limit;       // warp-specialised kernel: polls per barrier wait (0: the default bound)
     int32_t *status;        // bit 0: traceback found no edge (impossible by Theorem 1)
     int32_t *st_windows;
     int64_t *st_rows;

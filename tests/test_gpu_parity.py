@@ -251,6 +251,31 @@ def test_warp_specialized_blocks(ctx, rows):
         sc.scrooge_set_kernel_config(ctx, 0, *saved)
 
 
+def test_bounded_wait_times_out_and_recovers(ctx):
+    """A barrier wait of the warp-specialised blocks that runs out of polls makes the call return
+    SCROOGE_E_TIMEOUT (no fault, no hang: every warp leaves); with the default bound restored the
+    same context gives the oracle's results. One poll per wait is far too few: the traceback warp
+    waits for a window the DC warps have only begun."""
+    b = synth.concat([synth.long_reads(4, seed=91), synth.short_reads(300, seed=92)])
+    pb = sc.PackedBatch(b)
+    r = oracle.align_batch(b, 64, 24, threads=THREADS)
+    fl = sc.SCROOGE_PERSISTENT | sc.SCROOGE_WARP_SPECIALIZED
+    codes = []
+    try:
+        sc.scrooge_set_wait_limit(ctx, 1)
+        for _ in range(3):
+            try:
+                sc.align_host(ctx, pb, 64, 24, None, fl)
+                codes.append(0)
+            except sc.ScroogeError as e:
+                codes.append(e.code)
+    finally:
+        sc.scrooge_set_wait_limit(ctx, 0)
+    assert sc.SCROOGE_E_TIMEOUT in codes and set(codes) <= {0, sc.SCROOGE_E_TIMEOUT}, codes
+    g = sc.align_host(ctx, pb, 64, 24, None, fl)
+    assert_same(g, r, label="after a timed-out wait")
+
+
 def test_warp_specialized_few_pairs(ctx):
     """Fewer pairs than slots, a single pair, and empty patterns."""
     for b in (synth.tiny_windows(1, seed=81), synth.tiny_windows(7, seed=82), synth.short_reads(65, seed=83),
