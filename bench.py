@@ -5,15 +5,19 @@ One step aligns a whole batch: every pair of the workload goes through the
 windowing loop (GenASM-DC with ET, DENT/SENE storage, GenASM-TB, slide).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload long_reads]
-                  [--impl ours|reference] [--pairs P] [--no-e2e] [--no-cpu-baseline]
+                  [--impl ours|reference] [--pairs P] [--scaling weak|strong]
+                  [--no-e2e] [--no-cpu-baseline]
 
 Prints one JSON line (rank 0). ``value`` is alignments/s of the device-resident
 batch (CUDA events around each launch on the launching stream, max over
 ranks); ``e2e`` is the same metric through the C ABI with pinned host buffers
 (host-to-device copies of the packed inputs and device-to-host copies of all
 outputs inside the timed region). ``--impl reference`` times the CPU oracle on
-the host cores instead. With N > 1 (torchrun), each rank aligns its own batch
-of the same size (weak scaling, no collective on the data path).
+the host cores instead. With N > 1 (torchrun, or launched by this script when
+WORLD_SIZE is unset), each rank aligns its own batch of the same size (weak
+scaling), or its cost-balanced shard of one batch (--scaling strong, results
+gathered on rank 0 and checked against a single-GPU run of the whole batch);
+there is no collective on the data path.
 """
 from __future__ import annotations
 
@@ -58,6 +62,8 @@ PAPER_OPS_PER_CELL = 7  # bit-vector ops of one GenASM-DC cell: 3 shifts, 1 OR, 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--scaling", choices=["weak", "strong"], default="weak",
+                    help="weak: each rank aligns a batch of the workload's size; strong: the ranks share one batch")
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
@@ -73,6 +79,27 @@ def parse():
     ap.add_argument("--train-pairs", type=int, default=50_000)
     ap.add_argument("--train-epochs", type=int, default=30)
     return ap.parse_args()
+
+
+def self_launch(args) -> int:
+    """Run this script as args.gpus ranks on this node under torch.distributed.run (127.0.0.1)."""
+    import socket
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={args.gpus}",
+           "--master-addr=127.0.0.1", f"--master-port={port}", os.path.abspath(__file__), *sys.argv[1:]]
+    return subprocess.call(cmd)
+
+
+def sharded_results(batch, world: int, rank: int, align_fn, cost=None, group=None):
+    """Strong scaling: this rank's shard of one batch (longest-processing-time-first on `cost`, else
+    contiguous), aligned by align_fn(sub_batch) -> result dict with a dense CIGAR, gathered on rank
+    0 in pair order (None on the other ranks). Returns (pair indices of this rank, merged result)."""
+    from paper_2208_09985_gb300 import shard
+    idx = shard.shard_indices(batch.n_pairs, world, rank, cost)
+    res = align_fn(batch.subset(idx))
+    return idx, shard.gather_to_rank0(batch.n_pairs, idx, res, group)
 
 
 def dist_env():
@@ -253,12 +280,21 @@ def prepare_model(sc, ctx, args):
 
 def main():
     args = parse()
+    rank, world, local = dist_env()
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        if args.impl == "ours":
+            import torch
+            have = torch.cuda.device_count()
+            if have < args.gpus:
+                raise SystemExit(f"bench: --gpus {args.gpus} needs {args.gpus} GPUs; {have} visible")
+        raise SystemExit(self_launch(args))
+    if world != args.gpus:
+        raise SystemExit(f"bench: --gpus {args.gpus} but WORLD_SIZE={world}")
     if args.impl == "reference":
         return run_reference(args)
     import torch
     import paper_2208_09985_gb300 as sc
 
-    rank, world, local = dist_env()
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
@@ -266,7 +302,12 @@ def main():
     wl = WORKLOADS[args.workload]
     n_pairs = args.pairs or wl["n"]
     W, O, k = wl["W"], wl["O"], wl["W"]
-    batch = wl["make"](n_pairs, wl["seed"] + 1000 * rank)
+    strong = args.scaling == "strong" and world > 1
+    full_batch = None
+    if strong:
+        # one batch for the whole job; this rank aligns its cost-balanced shard
+        full_batch = wl["make"](n_pairs, wl["seed"])
+    batch = full_batch if strong else wl["make"](n_pairs, wl["seed"] + 1000 * rank)
     pb = sc.PackedBatch(batch)
     stream = torch.cuda.Stream()  # graph capture needs a stream other than the legacy default one
     torch.cuda.set_stream(stream)
@@ -274,6 +315,27 @@ def main():
     words = 1 if W <= 32 else (2 if W <= 64 else 4)
     model_info = prepare_model(sc, ctx, args)
     flags = args.flags
+    n_job = world * n_pairs  # pairs of the whole job
+    if strong:
+        # shard by predicted work: (pattern length + 1) x (predicted DP rows per window + 1), computed on
+        # rank 0 with the ordering model and broadcast, so every rank sees the same partition
+        from paper_2208_09985_gb300 import learned
+        cost_t = torch.zeros(n_pairs, dtype=torch.float32, device="cuda")
+        if rank == 0:
+            fdb = sc.DeviceBatch(pb)
+            feat = learned.device_features(ctx, fdb)
+            pred = torch.zeros(n_pairs, dtype=torch.float32, device="cuda")
+            sc.scrooge_model_predict(ctx, feat, n_pairs, pred)
+            torch.cuda.synchronize()
+            cost_t = (fdb.pat_len.to(torch.float32) + 1.0) * torch.expm1(pred).clamp_min(0.0).add(1.0)
+            del fdb, feat, pred
+        torch.distributed.broadcast(cost_t, src=0)
+        cost_np = cost_t.cpu().numpy().astype(np.float64)
+        from paper_2208_09985_gb300 import shard
+        batch = full_batch.subset(shard.shard_indices(n_pairs, world, rank, cost_np))
+        pb = sc.PackedBatch(batch)
+        n_job = n_pairs
+        n_pairs = batch.n_pairs  # this rank's pairs
     tune_info = None
     if not args.no_autotune:
         # kernel settings and the heavy load classes, tuned on a same-size sample drawn with another seed
@@ -354,15 +416,16 @@ def main():
     for name in PATHS:
         fl = flags | path_flags(sc, name)
         ms, step_ms, _, clk, nk = timed(fl, sampler=(name == "learned_graph"))
-        paths[name] = {"ms_per_step": ms, "alignments_per_s": world * n_pairs / (ms / 1e3),
+        paths[name] = {"ms_per_step": ms, "alignments_per_s": n_job / (ms / 1e3),
                        "kernels_per_step": nk, "step_ms": [round(x, 4) for x in step_ms]}
         if name == "learned_graph":
             head_ms, head_steps, head_clk, head_kernels = ms, step_ms, clk, nk
     # the alignment kernel alone, timed inside the learned (non-graph) steps
     _, _, ker_ms, _, _ = timed(flags | sc.SCROOGE_LEARNED, kernel_events=True)
     kernel_ms = sum(ker_ms) / len(ker_ms)
-    value = world * n_pairs / (head_ms / 1e3)
+    value = n_job / (head_ms / 1e3)
     bases = int(np.diff(batch.pattern_off).sum())
+    bases_job = int(np.diff(full_batch.pattern_off).sum()) if strong else world * bases
 
     # end to end through the C ABI with pinned host buffers (learned + graph)
     e2e = None
@@ -398,9 +461,30 @@ def main():
                 and np.array_equal(h_tc, ref_tc.cpu().numpy())
                 and np.array_equal(h_cig[:total_runs], ref_cig.cpu().numpy().view(np.uint32))):
             raise SystemExit("bench: end-to-end results differ from the device-resident run")
-        e2e = {"value": world * n_pairs / e2e_s, "unit": "alignments/s", "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h, "gbases_per_s": world * bases / e2e_s / 1e9,
+        e2e = {"value": n_job / e2e_s, "unit": "alignments/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "gbases_per_s": bases_job / e2e_s / 1e9,
                "path": "learned + persistent + graph, host buffers"}
+
+    # strong scaling: the shards' results, gathered on rank 0, equal a single-GPU run of the whole batch
+    scaling_check = None
+    if strong:
+        mine = sc.device_results(db)
+        tot = int(mine["cigar_off"][-1])
+        local_res = {"edit_counts": mine["edit_counts"], "text_consumed": mine["text_consumed"],
+                     "cigar": mine["cigar"][:tot], "cigar_off": mine["cigar_off"]}
+        _, merged = sharded_results(full_batch, world, rank, lambda sub: local_res, cost_np)
+        if rank == 0:
+            fdb = sc.DeviceBatch(sc.PackedBatch(full_batch))
+            sc.align_device(ctx, fdb, W, O, k, flags | sc.SCROOGE_SYNC)
+            ref = sc.device_results(fdb)
+            tot = int(ref["cigar_off"][-1])
+            if not (np.array_equal(merged["edit_counts"], ref["edit_counts"])
+                    and np.array_equal(merged["text_consumed"], ref["text_consumed"])
+                    and np.array_equal(merged["cigar_off"], ref["cigar_off"])
+                    and np.array_equal(merged["cigar"], ref["cigar"][:tot])):
+                raise SystemExit("bench: the gathered shards differ from a single-GPU run of the whole batch")
+            scaling_check = {"pairs": n_job, "shard": "LPT on predicted work", "identical_to_single_gpu": True}
+            del fdb
 
     if rank != 0:
         sc.scrooge_destroy(ctx)
@@ -428,15 +512,17 @@ def main():
     plain = paths["plain"]["alignments_per_s"]
     line = {
         "metric": METRIC, "value": value, "unit": "alignments/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": head_ms, "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": head_ms, "higher_is_better": True,
+        "scaling": "strong" if strong else "weak",
         "vs_baseline": None, "dtype": "u32 bit-vectors", "data": "synthetic",
-        "config": {"workload": args.workload, "desc": wl["desc"], "pairs_per_gpu": n_pairs, "W": W, "O": O, "k": k,
+        "config": {"workload": args.workload, "desc": wl["desc"], "pairs_per_gpu": n_pairs, "pairs_per_job": n_job,
+                   "W": W, "O": O, "k": k,
                    "path": "learned ordering + persistent work queue + CUDA graph (value); plain, persistent and "
                            "learned without graph in `paths`", "flags": flags,
                    "kernel": kernel, "kernel_config": list(sc.scrooge_get_kernel_config(ctx, sc.settings_slot(W, flags))),
                    "l2": "inputs larger than L2 (packed inputs %.0f MB)" % (pb.texts.nbytes / 1e6 + pb.patterns.nbytes / 1e6),
                    "parallelism": f"dp{world}" if world > 1 else "single GPU"},
-        "gbases_per_s": world * bases / (head_ms / 1e3) / 1e9,
+        "gbases_per_s": bases_job / (head_ms / 1e3) / 1e9,
         "paths": paths, "learned_gain_vs_plain": value / plain,
         "learned_gain_vs_persistent": value / paths["persistent"]["alignments_per_s"],
         "model": model_info, "autotune": tune_info,
@@ -466,6 +552,8 @@ def main():
         "cpu_baseline": cpu,
         "step_ms": [round(x, 4) for x in head_steps],
     }
+    if scaling_check:
+        line["sharding"] = scaling_check
     print(json.dumps(line), flush=True)
     sc.scrooge_destroy(ctx)
     if world > 1:

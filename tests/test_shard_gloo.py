@@ -45,6 +45,42 @@ def _worker(rank, world, port, mode, outdir):
         dist.destroy_process_group()
 
 
+def _bench_worker(rank, world, port, outdir):
+    """The benchmark's strong-scaling step with the oracle standing in for the GPU aligner."""
+    import sys
+    import torch.distributed as dist
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    if root not in sys.path:
+        sys.path.insert(0, root)
+    import bench
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    try:
+        b = synth.concat([synth.random_pairs(60, 200, 200, seed=31), synth.short_reads(40, seed=32)])
+        cost = np.diff(b.pattern_off).astype(np.float64) * (1.0 + (np.arange(b.n_pairs) % 5))
+        idx, merged = bench.sharded_results(b, world, rank, lambda sub: _oracle_result(sub, np.arange(sub.n_pairs)),
+                                            cost)
+        np.save(os.path.join(outdir, f"idx_{rank}.npy"), idx)
+        if rank == 0:
+            np.savez(os.path.join(outdir, "merged_bench.npz"), **merged)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_bench_strong_scaling_two_ranks(tmp_path):
+    """bench.py --scaling strong: each rank aligns its LPT shard of one batch; rank 0 gathers the single-process
+    result (here with the CPU oracle as the aligner, on gloo)."""
+    import oracle
+    oracle.build()
+    mp.spawn(_bench_worker, args=(2, _free_port(), str(tmp_path)), nprocs=2, join=True)
+    got = dict(np.load(tmp_path / "merged_bench.npz"))
+    b = synth.concat([synth.random_pairs(60, 200, 200, seed=31), synth.short_reads(40, seed=32)])
+    ref = _oracle_result(b, np.arange(b.n_pairs))
+    for key in ("edit_counts", "text_consumed", "cigar_off", "cigar"):
+        np.testing.assert_array_equal(got[key], ref[key], err_msg=key)
+    i0, i1 = np.load(tmp_path / "idx_0.npy"), np.load(tmp_path / "idx_1.npy")
+    assert len(i0) and len(i1) and np.array_equal(np.sort(np.concatenate([i0, i1])), np.arange(b.n_pairs))
+
+
 @pytest.mark.parametrize("mode", ["contiguous", "lpt"])
 def test_two_rank_shards_gather_to_the_single_process_result(tmp_path, mode):
     import oracle
