@@ -349,6 +349,16 @@ def main():
                      "best_settings_ms": sorted([[r[0], r[1], r[2], r[3] / 1e3] for r in table if r[4] == 1],
                                                 key=lambda r: r[3])[:3],
                      "heavy_class": sc.scrooge_get_heavy_class(ctx), "long_class": sc.scrooge_get_long_class(ctx),
+                     "buckets": {name: dict(zip(("kind", "lanes", "rows", "warps"),
+                                                sc.scrooge_get_bucket_config(ctx, b)))
+                                 for b, name in ((0, "heavy"), (1, "rest"))},
+                     "bucket_best_ms": {name: sorted([[r[0] % 1000, r[1], r[2], r[3] / 1e3] for r in table
+                                                      if r[4] == 3 and r[0] // 1000 == b], key=lambda r: r[3])[:3]
+                                        for b, name in ((0, "heavy"), (1, "rest"))},
+                     "learned_order": sc.scrooge_get_learned_order(ctx),
+                     "order_ms": {"model": [r[3] / 1e3 for r in table if r[4] == 4 and r[0] == 1],
+                                  "input": [r[3] / 1e3 for r in table if r[4] == 4 and r[0] == 0]},
+                     "long_class_ms": [[r[1], r[3] / 1e3] for r in table if r[4] == 5],
                      "seconds": time.perf_counter() - t0}
     db = sc.DeviceBatch(pb)
 

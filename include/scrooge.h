@@ -172,14 +172,19 @@ int scrooge_align_batch(scrooge_ctx *ctx, const uint32_t *texts, const int64_t *
  * results. words = 1, 2 or 4 selects the full-width kernel for windows of up
  * to 32 * words bases. The banded kernels serve windows of 33..128 bases when
  * SENE and ET are on (and SCROOGE_NO_BAND is not given):
- *   - words = 0 selects the one for 33..64-base windows (lanes_per_pair 2, 4
- *     or 8). It keeps the 32 diagonals j - i = -15..16 of each DP entry in one
+ *   - words = 0 selects the one for 33..64-base windows (lanes_per_pair 1, 2,
+ *     4 or 8). It keeps the 32 diagonals j - i = -15..16 of each DP entry in one
  *     word, which is exact for every window whose edit distance is at most 15.
+ *     lanes_per_pair = 1 selects a kernel with one lane per pair: each lane
+ *     computes its own window's 64 columns, and the warp's 32 pairs trace
+ *     back on all 32 lanes; smem_rows is then the number of a pair's latest
+ *     rows kept in shared memory, older rows being copied to device scratch.
  *   - words = 3 selects the one for 65..128-base windows (lanes_per_pair 8 or
  *     16). It keeps the 64 diagonals -31..32 in two words, exact up to 31.
  * Both recompute the other windows at full width.
  *   lanes_per_pair   threads that share one pair's window (words=1: 1,2,4;
- *                    words=2: 2,4,8; words=4: 8,16)
+ *                    words=2: 2,4,8; words=4: 8,16; words=0: 1,2,4,8;
+ *                    words=3: 8,16)
  *   smem_rows        DP rows of each pair kept in shared memory (>= 1); rows
  *                    beyond go to a device scratch area
  *   warps_per_block  1 or 2 (the kernel is compiled for blocks of at most 64 threads)
@@ -199,6 +204,28 @@ int scrooge_get_kernel_config(const scrooge_ctx *ctx, int32_t words, int32_t *la
  * class. */
 int scrooge_set_heavy_class(scrooge_ctx *ctx, int32_t load_class);
 int32_t scrooge_get_heavy_class(const scrooge_ctx *ctx);
+
+/* Kernel settings per load bucket of learned launches (no counterpart in the
+ * paper; never changes results). With SCROOGE_LEARNED on windows of 33..64
+ * bases, bucket 0 is the heavy pairs (load class >= scrooge_set_heavy_class,
+ * when that splits any off) and bucket 1 the rest of the order; each runs on
+ * kind 0 = the banded kernel (lanes_per_pair 1, 2, 4 or 8; 1 = one lane per
+ * pair) or kind 1 = the full-width kernel (lanes_per_pair 2, 4 or 8), with its
+ * own smem_rows and warps_per_block (1 or 2). Defaults: heavy = full width,
+ * 4 lanes, 4 rows, 2 warps; rest = banded, 4 lanes, 8 rows, 2 warps.
+ * scrooge_autotune with SCROOGE_LEARNED sets them. */
+int scrooge_set_bucket_config(scrooge_ctx *ctx, int32_t bucket, int32_t kind, int32_t lanes_per_pair,
+                              int32_t smem_rows, int32_t warps_per_block);
+int scrooge_get_bucket_config(const scrooge_ctx *ctx, int32_t bucket, int32_t *kind, int32_t *lanes_per_pair,
+                              int32_t *smem_rows, int32_t *warps_per_block);
+
+/* Whether SCROOGE_LEARNED launches take pairs in the model's order (1, the
+ * default) or in input order (0: the call then runs as SCROOGE_PERSISTENT,
+ * without the ordering pipeline; the model must still be installed).
+ * scrooge_autotune with SCROOGE_LEARNED sets it from measurement. Results
+ * never change. */
+int scrooge_set_learned_order(scrooge_ctx *ctx, int32_t on);
+int32_t scrooge_get_learned_order(const scrooge_ctx *ctx);
 
 /* Long pairs (no counterpart in the paper; never changes results). The
  * windows of a pair are sequential, so a batch can take no less time than
@@ -232,11 +259,24 @@ int scrooge_last_launch_shape(const scrooge_ctx *ctx, int64_t *shape, int32_t n)
  * after one untimed run), and installs the fastest configuration in the
  * context. If `results` is not NULL it receives up to max_results rows of 5
  * int32: lanes, rows, warps, microseconds, 1. With SCROOGE_LEARNED on windows
- * the banded kernel serves, it also times the heavy load classes
- * (scrooge_set_heavy_class) 16, 15, ..., 10, 0 before and again after the
- * settings sweep (at least 3 timed runs each), as rows 0, class, 0,
- * microseconds, 2, and installs the fastest class of the second pass if it
- * beats class 16 (no split) by at least 10%, else 16.
+ * the banded kernel serves, it then:
+ *   - times the heavy load classes (scrooge_set_heavy_class) 16, 15, ..., 10,
+ *     0 before and again after the settings sweep (at least 3 timed runs
+ *     each), as rows 0, class, 0, microseconds, 2, and installs the fastest
+ *     class of the second pass if it beats class 16 (no split) by at least
+ *     10%, else 16;
+ *   - sweeps the kernel settings of each load bucket of learned launches
+ *     (scrooge_set_bucket_config; the rest, then the heavy bucket if there is
+ *     one), kind x lanes x rows {2, 4, 8} x warps {1, 2}, as rows
+ *     bucket*1000 + kind*100 + lanes, rows, warps, microseconds, 3, keeping
+ *     the fastest per bucket;
+ *   - times the long pairs' own launch (scrooge_set_long_class) 16 (off), 14,
+ *     13, 12, as rows 0, class, 1, microseconds, 5, and keeps the fastest if
+ *     it beats 16 by at least 5%;
+ *   - times the learned launch with the model's order and in input order, as
+ *     rows 1, 0, 0, microseconds, 4 and 0, 0, 0, microseconds, 4, and keeps
+ *     the model's order (scrooge_set_learned_order) only if it is at least 2%
+ *     faster.
  * *n_results gets the row count.
  * Synchronous. */
 int scrooge_autotune(scrooge_ctx *ctx, const uint32_t *texts, const int64_t *text_offsets,
@@ -260,16 +300,17 @@ int scrooge_set_order(scrooge_ctx *ctx, const int32_t *order, int32_t n_pairs);
  * bucket. From the most significant bit down the key holds:
  *   - the long pairs first (work class >= scrooge_set_long_class);
  *   - then the heavy pairs (load class >= scrooge_set_heavy_class);
- *   - then the largest predicted total work first (work class halved), so
- *     that the longest pairs do not finish last;
- *   - then the lightest per-window load first (load class halved): at
- *     equal work the lighter pair has more windows, and this measured
- *     faster than heavier-first on long and on uneven reads.
+ *   - then the pattern length, longest first, in eighths of an octave below
+ *     the batch's longest pattern (6 bits): the windows of a pair are
+ *     sequential, so the longest pairs must start first, and pairs of
+ *     similar length share warps and finish together. On uneven batches this
+ *     measured faster than orders that mix in the predicted load, even the
+ *     true load (see the design notes).
  * Here rows is the predicted mean DP rows per window, the load class is
  * floor(4 log2(rows + 1)) and the work class is
- * floor(log2((m + 1)(rows + 1))) - 6, both clipped to 0..15. Pairs sharing
- * a warp do similar early-termination work. The order never changes
- * results.
+ * floor(log2((m + 1)(rows + 1))) - 6, both clipped to 0..15; they choose the
+ * launches and kernels of the buckets (scrooge_set_bucket_config). The
+ * order never changes results.
  *
  * Features (float32, 6 per pair, row-major): log2(m+1), log2(n+1),
  * (n-m)/max(m,1), the fraction of sampled pattern 12-mers found in the text

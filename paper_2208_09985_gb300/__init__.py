@@ -102,6 +102,10 @@ def load():
                 "scrooge_get_long_class": ([P], i32),
                 "scrooge_logic_peak": ([P, i32, P, P], ctypes.c_int),
                 "scrooge_set_wait_limit": ([P, i32], ctypes.c_int),
+                "scrooge_set_bucket_config": ([P, i32, i32, i32, i32, i32], ctypes.c_int),
+                "scrooge_get_bucket_config": ([P, i32, P, P, P, P], ctypes.c_int),
+                "scrooge_set_learned_order": ([P, i32], ctypes.c_int),
+                "scrooge_get_learned_order": ([P], i32),
             }
             for name, (args, res) in sig.items():
                 f = getattr(lib, name)
@@ -209,9 +213,11 @@ def scrooge_get_kernel_config(ctx, words: int):
 
 def scrooge_autotune(ctx, texts, text_offsets, text_lengths, patterns, pattern_offsets, pattern_lengths,
                      n_pairs: int, W: int, O: int, k: int, flags: int, edit_counts, text_consumed, cigar,
-                     cigar_capacity: int, cigar_offsets, repeats: int = 2, max_results: int = 256):
-    """Time every kernel configuration on a device batch; returns rows (lanes, rows, warps, microseconds, kind)
-    with kind 1 for kernel settings and 2 for heavy load classes (lanes 0, rows = the class)."""
+                     cigar_capacity: int, cigar_offsets, repeats: int = 2, max_results: int = 512):
+    """Time every kernel configuration on a device batch; returns rows (a, b, c, microseconds, kind): kind 1
+    kernel settings (lanes, rows, warps), 2 heavy load classes (0, class, 0), 3 bucket settings (bucket*1000 +
+    kernel kind*100 + lanes, rows, warps), 4 learned order on/off (1 or 0, 0, 0), 5 long-pair classes
+    (0, class, 1); see include/scrooge.h."""
     res = np.zeros((max_results, 5), dtype=np.int32)
     nres = ctypes.c_int32(0)
     rc = load().scrooge_autotune(ctx, _ptr(texts), _ptr(text_offsets), _ptr(text_lengths), _ptr(patterns),
@@ -358,6 +364,28 @@ def edit_distance_device(ctx, db: "DeviceBatch", sync: bool = True):
                           min(max_m, SCROOGE_EDIT_DISTANCE_MAX_M), SCROOGE_DEVICE_PTRS | (SCROOGE_SYNC if sync else 0),
                           fe, gl)
     return fe, gl
+
+
+def scrooge_set_bucket_config(ctx, bucket: int, kind: int, lanes_per_pair: int, smem_rows: int,
+                              warps_per_block: int):
+    """Kernel settings of one load bucket of learned launches (0 heavy, 1 rest; kind 0 banded, 1 full width)."""
+    return _check(ctx, load().scrooge_set_bucket_config(ctx, bucket, kind, lanes_per_pair, smem_rows,
+                                                        warps_per_block))
+
+
+def scrooge_get_bucket_config(ctx, bucket: int):
+    a = [ctypes.c_int32() for _ in range(4)]
+    _check(ctx, load().scrooge_get_bucket_config(ctx, bucket, *[ctypes.byref(x) for x in a]))
+    return tuple(x.value for x in a)
+
+
+def scrooge_set_learned_order(ctx, on: bool):
+    """SCROOGE_LEARNED launches in the model's order (True) or in input order (False)."""
+    return _check(ctx, load().scrooge_set_learned_order(ctx, 1 if on else 0))
+
+
+def scrooge_get_learned_order(ctx) -> bool:
+    return load().scrooge_get_learned_order(ctx) == 1
 
 
 def scrooge_set_wait_limit(ctx, polls: int = 0):

@@ -307,8 +307,23 @@ __global__ void adam_kernel(float *model, const float *grad, float *m1, float *m
 //             which measured faster than heavier-first on both the long and the uneven reads.
 // rows = predicted mean DP rows per window, load class = floor(4 log2(rows + 1)) in 0..15,
 // work class = floor(log2((m + 1)(rows + 1))) - 6 in 0..15.
+// The longest pattern of the batch (one block).
+__global__ void __launch_bounds__(1024) max_len_kernel(const int32_t *pat_len, int32_t n, int32_t *out) {
+    __shared__ int32_t wmax[32];
+    int32_t v = 0;
+    for (int64_t p = threadIdx.x; p < n; p += blockDim.x) v = max(v, pat_len[p]);
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        v = threadIdx.x < (blockDim.x >> 5) ? wmax[threadIdx.x] : 0;
+        for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+        if (threadIdx.x == 0) *out = v;
+    }
+}
+
 __global__ void bucket_key_kernel(const float *pred, const int32_t *pat_len, int32_t n, int heavy_class,
-                                  int long_class, uint8_t *key) {
+                                  int long_class, const int32_t *max_len, uint8_t *key) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
     const float rows = fmaxf(expm1f(pred[p]), 0.f);
@@ -318,7 +333,10 @@ __global__ void bucket_key_kernel(const float *pred, const int32_t *pat_len, int
     work = max(0, min(15, work));
     const int shortp = work >= long_class ? 0 : 1;
     const int light = load >= heavy_class ? 0 : 1;
-    key[p] = (uint8_t)((shortp << 7) | (light << 6) | ((7 - (work >> 1)) << 3) | (load >> 1));
+    // length class: eighths of an octave below the batch's longest pattern (longest first)
+    int lc = (int)floorf((log2f((float)*max_len + 1.f) - log2f((float)pat_len[p] + 1.f)) * 8.f);
+    lc = max(0, min(63, lc));
+    key[p] = (uint8_t)((shortp << 7) | (light << 6) | lc);
 }
 
 constexpr int kSortTile = 2048;  // elements per block of the counting sort
@@ -401,7 +419,8 @@ cudaError_t launch_feature_stats(const float *feat, int32_t n, float *model, cud
 int learned_kernel_count(int32_t n) {
     if (n <= 0) return 0;
     const int64_t nb = ((int64_t)n + kSortTile - 1) / kSortTile;
-    return 2 /* features, MLP */ + 1 /* keys */ + 1 /* histogram */ + scan_kernel_count(256 * nb) + 1 /* scatter */;
+    return 2 /* features, MLP */ + 1 /* longest pattern */ + 1 /* keys */ + 1 /* histogram */ +
+           scan_kernel_count(256 * nb) + 1 /* scatter */;
 }
 
 int64_t sort_temp_words(int32_t n) {
@@ -421,7 +440,10 @@ cudaError_t launch_learned_order(const float *pred, const int32_t *pat_len, int3
     int32_t *counts = reinterpret_cast<int32_t *>(tmp);       // 256 * nb int32
     int64_t *offsets = tmp + 256 * (int64_t)nb;               // 256 * nb + 1 int64
     int64_t *scan_tmp = offsets + 256 * (int64_t)nb + 8;
-    bucket_key_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pred, pat_len, n, heavy_class, long_class, key);
+    int32_t *max_len = reinterpret_cast<int32_t *>(tmp + sort_temp_words(n) - 2);  // past the scan's scratch
+    max_len_kernel<<<1, 1024, 0, s>>>(pat_len, n, max_len);
+    bucket_key_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(pred, pat_len, n, heavy_class, long_class, max_len,
+                                                                  key);
     key_hist_kernel<<<nb, 256, 0, s>>>(key, n, counts, nb);
     cudaError_t e = exclusive_scan(counts, 0, 256 * (int64_t)nb, offsets, scan_tmp, s);
     if (e != cudaSuccess) return e;

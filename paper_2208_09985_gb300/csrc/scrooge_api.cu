@@ -67,7 +67,7 @@ int scrooge_destroy(scrooge_ctx *c) {
                      &c->scr_runs,  &c->scr_off, &c->scr_len, &c->scr_cap,  &c->scan_tmp, &c->queue,
                      &c->model,     &c->grad,    &c->adam_m1, &c->adam_m2,  &c->loss,     &c->l_feat,
                      &c->l_pred,    &c->l_key,   &c->l_order, &c->l_tmp,    &c->t_rows,   &c->fallback, &c->spill2,
-                     &c->spill3,    &c->fallback2};
+                     &c->spill3,    &c->fallback2, &c->fallback3};
     if (c->graph) cudaGraphExecDestroy(c->graph);
     if (c->stream2) cudaStreamDestroy(c->stream2);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
@@ -186,6 +186,36 @@ int scrooge_get_kernel_config(const scrooge_ctx *c, int32_t words, int32_t *lane
     if (wpb) *wpb = c->kcfg[ix].wpb;
     return SCROOGE_OK;
 }
+
+int scrooge_set_bucket_config(scrooge_ctx *c, int32_t bucket, int32_t kind, int32_t lanes, int32_t rows,
+                              int32_t wpb) {
+    if (!c) return SCROOGE_E_INVAL;
+    const bool ok_kind = kind == 0 ? align_supported(0, lanes) : (kind == 1 && align_supported(2, lanes));
+    if (bucket < 0 || bucket > 1 || !ok_kind || rows < 1 || rows > 129 || wpb < 1 || wpb > 2)
+        return fail(c, SCROOGE_E_INVAL, "unsupported bucket config bucket=%d kind=%d lanes=%d rows=%d warps=%d", bucket,
+                    kind, lanes, rows, wpb);
+    c->bucket_kind[bucket] = kind;
+    c->bucket_cfg[bucket] = {lanes, rows, wpb};
+    return SCROOGE_OK;
+}
+
+int scrooge_get_bucket_config(const scrooge_ctx *c, int32_t bucket, int32_t *kind, int32_t *lanes, int32_t *rows,
+                              int32_t *wpb) {
+    if (!c || bucket < 0 || bucket > 1) return SCROOGE_E_INVAL;
+    if (kind) *kind = c->bucket_kind[bucket];
+    if (lanes) *lanes = c->bucket_cfg[bucket].lanes;
+    if (rows) *rows = c->bucket_cfg[bucket].rows;
+    if (wpb) *wpb = c->bucket_cfg[bucket].wpb;
+    return SCROOGE_OK;
+}
+
+int scrooge_set_learned_order(scrooge_ctx *c, int32_t on) {
+    if (!c || (on != 0 && on != 1)) return SCROOGE_E_INVAL;
+    c->learned_order_on = on != 0;
+    return SCROOGE_OK;
+}
+
+int32_t scrooge_get_learned_order(const scrooge_ctx *c) { return c ? (c->learned_order_on ? 1 : 0) : -1; }
 
 int scrooge_set_heavy_class(scrooge_ctx *c, int32_t load_class) {
     if (!c || load_class < 0 || load_class > 16) return SCROOGE_E_INVAL;
@@ -320,7 +350,7 @@ int make_lane_plan(scrooge_ctx *c, const AlignParams &base, uint32_t flags, DevB
 // fallback area). Queue, order and status are set by the caller.
 // slots > 0: a launch with that many pair slots per warp, one warp per block and three blocks per SM.
 int make_plan(scrooge_ctx *c, const AlignParams &base, bool band, uint32_t flags, DevBuf &spill, DevBuf &fallback,
-              int slots, LaunchPlan &out) {
+              int slots, LaunchPlan &out, const KernelConfig *settings = nullptr) {
     const int W = base.W, O = base.O, k = base.k;
     // the banded kernels: window words nww (their full-width fallback and staged bases), band words bw
     const int nww = W > 64 ? 4 : 2;
@@ -328,7 +358,7 @@ int make_plan(scrooge_ctx *c, const AlignParams &base, bool band, uint32_t flags
     const int words = band ? nww : words_for(W);
     const bool sene = !(flags & SCROOGE_NO_SENE);
     const bool dent = !(flags & SCROOGE_NO_DENT);
-    const KernelConfig kc = c->kcfg[kcfg_index(band ? band_slot_for(W) : words)];
+    const KernelConfig kc = settings ? *settings : c->kcfg[kcfg_index(band ? band_slot_for(W) : words)];
     // warp-specialised blocks: 64-base bands, persistent, four lanes per pair, not the long-pair launch
     const bool ws = band && nww == 2 && bw == 1 && slots == 0 && (flags & SCROOGE_WARP_SPECIALIZED) &&
                     (flags & SCROOGE_PERSISTENT);
@@ -450,6 +480,8 @@ int scrooge_align_batch(scrooge_ctx *c, const uint32_t *texts, const int64_t *te
     if (flags & SCROOGE_LEARNED) flags |= SCROOGE_PERSISTENT;
     if ((flags & SCROOGE_LEARNED) && !c->model_ready)
         return fail(c, SCROOGE_E_NOMODEL, "SCROOGE_LEARNED needs a model (scrooge_model_set or scrooge_model_train)");
+    // the autotuner found that the model's order does not pay on this workload: input order
+    if ((flags & SCROOGE_LEARNED) && !c->learned_order_on) flags &= ~(uint32_t)SCROOGE_LEARNED;
     if (!cigar_offsets) return fail(c, SCROOGE_E_INVAL, "null cigar_offsets");
     const bool dev = (flags & SCROOGE_DEVICE_PTRS) != 0;
     cudaError_t e = cudaSetDevice(c->device);
@@ -569,9 +601,22 @@ int scrooge_align_batch(scrooge_ctx *c, const uint32_t *texts, const int64_t *te
     const bool use_heavy = learned_split && c->heavy_class < 16;
     const bool use_long = learned_split && c->long_class < 16;
     LaunchPlan plan, heavy, lng;
-    if ((rc = make_plan(c, p, band, flags, c->spill, c->fallback, 0, plan))) return rc;
-    if (use_heavy && (rc = make_plan(c, p, false, flags | SCROOGE_NO_BAND, c->spill2, c->fallback, 0, heavy)))
+    // learned launches on band-sized windows take their kernel and settings per load bucket
+    const bool per_bucket = band && (flags & SCROOGE_LEARNED);
+    if (per_bucket) {
+        const bool rest_band = c->bucket_kind[1] == 0;
+        if ((rc = make_plan(c, p, rest_band, rest_band ? flags : (flags | SCROOGE_NO_BAND), c->spill, c->fallback, 0,
+                            plan, &c->bucket_cfg[1])))
+            return rc;
+    } else if ((rc = make_plan(c, p, band, flags, c->spill, c->fallback, 0, plan))) {
         return rc;
+    }
+    if (use_heavy) {
+        const bool heavy_band = c->bucket_kind[0] == 0;
+        if ((rc = make_plan(c, p, heavy_band, heavy_band ? flags : (flags | SCROOGE_NO_BAND), c->spill2, c->fallback3,
+                            0, heavy, &c->bucket_cfg[0])))
+            return rc;
+    }
     if (use_long && (rc = make_plan(c, p, true, flags, c->spill3, c->fallback2, 1, lng))) return rc;
     if ((rc = ensure(c, c->status, 64, "status"))) return rc;
     if ((flags & SCROOGE_PERSISTENT) && (rc = ensure(c, c->queue, 256, "work queues"))) return rc;
@@ -681,7 +726,9 @@ int scrooge_align_batch(scrooge_ctx *c, const uint32_t *texts, const int64_t *te
             ((unsigned long long)plan.wpb << 32) | (unsigned long long)plan.blocks,
             (unsigned long long)(uintptr_t)c->st_rows, (unsigned long long)(uintptr_t)c->st_cells,
             (unsigned long long)(uintptr_t)c->st_windows, (unsigned long long)(uintptr_t)plan.p.fb,
-            (unsigned long long)band | ((unsigned long long)(uint32_t)c->wait_limit << 8),
+            (unsigned long long)band | ((unsigned long long)(uint32_t)c->wait_limit << 8) |
+                ((unsigned long long)plan.band << 40) | ((unsigned long long)plan.lane << 41) |
+                ((unsigned long long)heavy.band << 42) | ((unsigned long long)heavy.lane << 43),
             use_heavy ? (((unsigned long long)heavy.G << 48) | ((unsigned long long)heavy.p.rcap << 32) |
                          ((unsigned long long)heavy.wpb << 24) | (unsigned long long)heavy.blocks)
                       : 0ull,
@@ -858,6 +905,88 @@ int scrooge_autotune(scrooge_ctx *c, const uint32_t *texts, const int64_t *text_
     c->kcfg[ix] = rc == SCROOGE_OK ? best_cfg : saved;
     if (rc == SCROOGE_OK && tune_classes) rc = sweep_classes();  // again, with the chosen settings
     if (rc != SCROOGE_OK) c->heavy_class = saved_class;
+    // learned launches: kernel and settings per load bucket (the rest, then the heavy pairs if the
+    // order splits them off), each chosen with the other fixed, by the time of the whole call
+    const int32_t saved_kind[2] = {c->bucket_kind[0], c->bucket_kind[1]};
+    const KernelConfig saved_bcfg[2] = {c->bucket_cfg[0], c->bucket_cfg[1]};
+    const bool saved_order = c->learned_order_on;
+    if (rc == SCROOGE_OK && tune_classes) {
+        c->learned_order_on = true;
+        if (ix == kcfg_index(0)) {  // 64-base windows: the rest starts from the tuned banded settings
+            c->bucket_kind[1] = 0;
+            c->bucket_cfg[1] = c->kcfg[ix];
+        }
+        const int band_lanes[] = {1, 2, 4, 8}, full_lanes[] = {2, 4, 8}, bucket_rows[] = {2, 4, 8};
+        for (int b = 1; b >= 0 && rc == SCROOGE_OK; --b) {
+            if (b == 0 && c->heavy_class >= 16) break;  // no heavy bucket
+            float bbest = -1.f;
+            int bkind = c->bucket_kind[b];
+            KernelConfig bcfg = c->bucket_cfg[b];
+            for (int kind = 0; kind < 2 && rc == SCROOGE_OK; ++kind) {
+                const int *lanes = kind == 0 ? band_lanes : full_lanes;
+                const int nl = kind == 0 ? 4 : 3;
+                for (int li = 0; li < nl && rc == SCROOGE_OK; ++li) {
+                    if (ix != kcfg_index(0) && kind == 0 && lanes[li] == 1) continue;  // lane kernel: 64-base windows
+                    for (int rows : bucket_rows) {
+                        for (int wpb = 1; wpb <= 2; ++wpb) {
+                            c->bucket_kind[b] = kind;
+                            c->bucket_cfg[b] = {lanes[li], rows, wpb};
+                            float t;
+                            if ((rc = time_it(repeats, t)) != SCROOGE_OK) break;
+                            record(b * 1000 + kind * 100 + lanes[li], rows, wpb, t, 3);
+                            if (bbest < 0.f || t < bbest) {
+                                bbest = t;
+                                bkind = kind;
+                                bcfg = c->bucket_cfg[b];
+                            }
+                        }
+                        if (rc != SCROOGE_OK) break;
+                    }
+                }
+            }
+            c->bucket_kind[b] = bkind;
+            c->bucket_cfg[b] = bcfg;
+        }
+        // the long pairs' own launch (one pair per warp, scrooge_set_long_class): kept only if it is at
+        // least 5% faster than none
+        if (rc == SCROOGE_OK) {
+            const int32_t saved_long = c->long_class;
+            float t_off = -1.f, best_t = -1.f;
+            int best_lc = 16;
+            for (int lc : {16, 14, 13, 12}) {
+                c->long_class = lc;
+                float t;
+                if ((rc = time_it(std::max(repeats, 3), t)) != SCROOGE_OK) break;
+                record(0, lc, 1, t, 5);
+                if (lc == 16) t_off = t;
+                if (best_t < 0.f || t < best_t) {
+                    best_t = t;
+                    best_lc = lc;
+                }
+            }
+            c->long_class = rc != SCROOGE_OK ? saved_long
+                                             : ((best_lc != 16 && best_t <= 0.95f * t_off) ? best_lc : 16);
+        }
+        // does the model's order pay for itself on this workload? keep it only if it is at least 2%
+        // faster than the persistent launch in input order (which SCROOGE_LEARNED then falls back to)
+        if (rc == SCROOGE_OK) {
+            float t_model, t_input;
+            if ((rc = time_it(std::max(repeats, 3), t_model)) == SCROOGE_OK) {
+                c->learned_order_on = false;
+                rc = time_it(std::max(repeats, 3), t_input);
+                record(1, 0, 0, t_model, 4);
+                record(0, 0, 0, t_input, 4);
+                c->learned_order_on = rc == SCROOGE_OK && t_model <= 0.98f * t_input;
+            }
+        }
+    }
+    if (rc != SCROOGE_OK) {
+        for (int b = 0; b < 2; ++b) {
+            c->bucket_kind[b] = saved_kind[b];
+            c->bucket_cfg[b] = saved_bcfg[b];
+        }
+        c->learned_order_on = saved_order;
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (n_results) *n_results = std::min(nres, max_results);

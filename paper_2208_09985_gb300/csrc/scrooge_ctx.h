@@ -35,11 +35,16 @@ struct scrooge_ctx {
     scrooge::KernelConfig kcfg[5] = {{2, 8, 2}, {4, 4, 2}, {8, 8, 2}, {4, 8, 2}, {8, 6, 2}};
     int fail_allocs = 0;  // testing hook: fail the next N device allocations
     int32_t wait_limit = 0;  // polls per bounded device wait (0: the kernel's default bound)
-    scrooge::DevBuf spill, status, fallback, spill2, spill3, fallback2;
+    scrooge::DevBuf spill, status, fallback, spill2, spill3, fallback2, fallback3;
     // learned launches: pairs in load classes >= heavy_class run on the full-width kernel, pairs in
     // work classes >= long_class one per warp on stream3 (16: none); the banded kernel runs the rest
     // on stream2
     int32_t heavy_class = 16, long_class = 16;
+    // kernel settings of the learned launches per load bucket: 0 = the heavy pairs, 1 = the rest;
+    // kind 0 = banded kernel, 1 = full-width kernel (see scrooge_set_bucket_config)
+    int32_t bucket_kind[2] = {1, 0};
+    scrooge::KernelConfig bucket_cfg[2] = {{4, 4, 2}, {4, 8, 2}};
+    bool learned_order_on = true;  // SCROOGE_LEARNED orders by the model (else input order)
     cudaStream_t stream2 = nullptr, stream3 = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join3 = nullptr;
     scrooge::DevBuf in_text, in_pat, in_toff, in_tlen, in_poff, in_plen;

@@ -257,13 +257,14 @@ def test_learned_order_is_stable_bucket_sort(ctx):
     work = np.clip(np.floor(np.log2((m + 1) * (rows + 1))) - 6, 0, 15).astype(np.int64)
     heavy = load >= sc.scrooge_get_heavy_class(h)
     longp = work >= sc.scrooge_get_long_class(h)
-    key = (np.where(longp, 0, 128) | np.where(heavy, 0, 64) | ((7 - (work >> 1)) << 3) |
-           (load >> 1)).astype(np.int64)
+    lenx = (np.log2(np.float32(m.max()) + 1) - np.log2(m + 1)) * 8
+    lc = np.clip(np.floor(lenx), 0, 63).astype(np.int64)
+    key = (np.where(longp, 0, 128) | np.where(heavy, 0, 64) | lc).astype(np.int64)
     # pairs whose class values sit within rounding of an integer may land in either bucket:
     # check the order on the others (a subsequence of a sorted, stable order is sorted and stable)
     # (an exact integer, e.g. log2(1) for rows = 0, is not ambiguous)
     near = lambda x: (np.abs(x - np.round(x)) < 1e-4) & (x != np.round(x))
-    clear = ~near(np.log2(rows + 1) * 4) & ~near(np.log2((m + 1) * (rows + 1)))
+    clear = ~near(np.log2(rows + 1) * 4) & ~near(np.log2((m + 1) * (rows + 1))) & ~near(lenx)
     assert clear.mean() > 0.95
     got = order.cpu().numpy()
     assert np.array_equal(np.sort(got), np.arange(n))
@@ -314,32 +315,109 @@ def test_autotune_picks_a_heavy_class(ctx):
         learned.train(h, db, epochs=3, batch=256)
         table = sc.autotune_device(h, db, 64, 24, flags=sc.SCROOGE_LEARNED, repeats=1)
     s.synchronize()
-    kinds = [r[4] for r in table]
-    assert 1 in kinds and 2 in kinds
-    classes = {r[1]: r[3] for r in table if r[4] == 2}  # the second pass overwrites the first
-    chosen = sc.scrooge_get_heavy_class(h)
-    assert chosen in classes
-    if chosen != 16:
-        assert classes[chosen] <= 0.9 * classes[16]
-    got = _run(ctx, db, sc.SCROOGE_LEARNED)
-    assert_same(got, oracle.align_batch(b, 64, 24), label="after autotune")
+    try:
+        kinds = [r[4] for r in table]
+        assert 1 in kinds and 2 in kinds and 3 in kinds and 4 in kinds and 5 in kinds
+        classes = {r[1]: r[3] for r in table if r[4] == 2}  # the second pass overwrites the first
+        chosen = sc.scrooge_get_heavy_class(h)
+        assert chosen in classes
+        if chosen != 16:
+            assert classes[chosen] <= 0.9 * classes[16]
+        # the rest bucket's settings are the fastest timed for it
+        rest = [r for r in table if r[4] == 3 and r[0] // 1000 == 1]
+        best = min(rest, key=lambda r: r[3])
+        kind, lanes, rows, wpb = sc.scrooge_get_bucket_config(h, 1)
+        assert (best[0] % 1000, best[1], best[2]) == (kind * 100 + lanes, rows, wpb)
+        # the learned order is kept only if it beat input order by 2%
+        order = {r[0]: r[3] for r in table if r[4] == 4}
+        assert sc.scrooge_get_learned_order(h) == (order[1] <= 0.98 * order[0])
+        got = _run(ctx, db, sc.SCROOGE_LEARNED)
+        assert_same(got, oracle.align_batch(b, 64, 24), label="after autotune")
+    finally:
+        sc.scrooge_set_learned_order(h, True)
+        sc.scrooge_set_heavy_class(h, 16)
+        sc.scrooge_set_long_class(h, 16)
+        sc.scrooge_set_bucket_config(h, 0, 1, 4, 4, 2)
+        sc.scrooge_set_bucket_config(h, 1, 0, 4, 8, 2)
 
 
-def test_warp_specialized_learned_and_graph(ctx):
+def test_bucket_settings_identical(ctx):
+    """Per-bucket kernel settings of learned launches (banded with 1 to 8 lanes per pair, full width) and the
+    model order switched off give the plain launch's results."""
+    import torch
     h, s = ctx
-    b = synth.concat([synth.uneven_reads(150, seed=91), synth.short_reads(400, seed=92)])
+    b = synth.concat([synth.uneven_reads(200, seed=121), synth.fixed_error(40, 0.15, length=3000, seed=122),
+                      synth.short_reads(300, seed=123), synth.random_pairs(100, 300, 300, seed=124)])
     db = sc.DeviceBatch(sc.PackedBatch(b))
     plain = _run(ctx, db, 0)
-    import torch
+    assert_same(plain, oracle.align_batch(b, 64, 24), label="plain")
     with torch.cuda.stream(s):
         learned.train(h, db, epochs=3, batch=256)
-    saved = sc.scrooge_get_heavy_class(h)
+    saved = [sc.scrooge_get_bucket_config(h, q) for q in (0, 1)]
     try:
-        for hc in (16, 12):
+        for hc in (16, 10):
             sc.scrooge_set_heavy_class(h, hc)
-            for flags in (sc.SCROOGE_LEARNED, sc.SCROOGE_LEARNED | sc.SCROOGE_GRAPH, sc.SCROOGE_PERSISTENT):
-                for rep in range(2):
-                    _same_device(_run(ctx, db, flags | sc.SCROOGE_WARP_SPECIALIZED), plain,
-                                 f"warp-specialised heavy {hc} flags {flags} run {rep}")
+            for heavy_cfg, rest_cfg in (((0, 1, 4, 1), (1, 4, 4, 2)), ((1, 8, 2, 2), (0, 1, 2, 1)),
+                                        ((0, 8, 8, 2), (0, 2, 8, 1)), ((0, 1, 3, 2), (0, 1, 16, 2))):
+                sc.scrooge_set_bucket_config(h, 0, *heavy_cfg)
+                sc.scrooge_set_bucket_config(h, 1, *rest_cfg)
+                assert sc.scrooge_get_bucket_config(h, 0) == heavy_cfg
+                for flags in (sc.SCROOGE_LEARNED, sc.SCROOGE_LEARNED | sc.SCROOGE_GRAPH):
+                    _same_device(_run(ctx, db, flags), plain, f"heavy {hc} buckets {heavy_cfg}/{rest_cfg} {flags}")
+        sc.scrooge_set_learned_order(h, False)
+        assert not sc.scrooge_get_learned_order(h)
+        _same_device(_run(ctx, db, sc.SCROOGE_LEARNED | sc.SCROOGE_GRAPH), plain, "model order off")
     finally:
-        sc.scrooge_set_heavy_class(h, saved)
+        sc.scrooge_set_learned_order(h, True)
+        sc.scrooge_set_heavy_class(h, 16)
+        for q in (0, 1):
+            sc.scrooge_set_bucket_config(h, q, *saved[q])
+    with pytest.raises(sc.ScroogeError):
+        sc.scrooge_set_bucket_config(h, 2, 0, 4, 8, 2)
+    with pytest.raises(sc.ScroogeError):
+        sc.scrooge_set_bucket_config(h, 0, 1, 1, 8, 2)  # the full-width kernel has no one-lane form
+
+
+def test_trained_model_gains_over_input_order(ctx):
+    """What the learned ordering gains over the method without it: on uneven reads (log-normal lengths,
+    1-15% edits, 100,000 pairs) the persistent launch in the learned order is faster than in input order.
+    The order is length-first (longest first; see the bucket key), so a network with random weights
+    gives the same order when no bucket is split off; its time is measured beside and must be within
+    noise of the trained one. Results are identical in all runs (checked here; the parity tests check
+    them against the oracle). Median of 7 timed calls each, CUDA events on the context stream."""
+    import torch
+    h, s = ctx
+    b = synth.uneven_reads(100_000, seed=3)
+    db = sc.DeviceBatch(sc.PackedBatch(b))
+    with torch.cuda.stream(s):
+        tdb = sc.DeviceBatch(sc.PackedBatch(synth.uneven_reads(8000, seed=40)))
+        learned.train(h, tdb, epochs=20, batch=512, lr=2e-3)
+        del tdb
+    s.synchronize()
+    trained = sc.scrooge_model_get(h)
+
+    def med(flags):
+        for _ in range(2):
+            _run(ctx, db, flags)
+        times = []
+        for _ in range(7):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            with torch.cuda.stream(s):
+                sc.align_device(h, db, 64, 24, flags=flags)
+            e1.record(s)
+            s.synchronize()
+            times.append(e0.elapsed_time(e1))
+        return float(np.median(times))
+
+    plain = _run(ctx, db, 0)
+    t_input = med(sc.SCROOGE_PERSISTENT)
+    t_trained = med(sc.SCROOGE_LEARNED)
+    _same_device(sc.device_results(db), plain, "trained order")
+    sc.scrooge_model_set(h, _random_model(np.random.default_rng(17)).astype(np.float32))
+    t_random = med(sc.SCROOGE_LEARNED)
+    _same_device(sc.device_results(db), plain, "random-weights order")
+    sc.scrooge_model_set(h, trained)
+    print(f"uneven 100k: input order {t_input:.2f} ms, trained {t_trained:.2f} ms, random weights {t_random:.2f} ms")
+    assert t_trained < 0.9 * t_input, (t_trained, t_input)
+    assert abs(t_trained - t_random) < 0.1 * t_input, (t_trained, t_random)
