@@ -69,6 +69,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="long_reads")
     ap.add_argument("--pairs", type=int, default=0, help="override the workload's pair count")
+    ap.add_argument("--W", type=int, default=0, help="override the workload's window size (k = W)")
+    ap.add_argument("--O", type=int, default=-1, help="override the workload's window overlap")
     ap.add_argument("--flags", type=int, default=0, help="extra SCROOGE_* flags (ablations)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -301,7 +303,9 @@ def main():
     torch.cuda.set_device(local)
     wl = WORKLOADS[args.workload]
     n_pairs = args.pairs or wl["n"]
-    W, O, k = wl["W"], wl["O"], wl["W"]
+    W = args.W or wl["W"]
+    O = args.O if args.O >= 0 else wl["O"]
+    k = W
     strong = args.scaling == "strong" and world > 1
     full_batch = None
     if strong:

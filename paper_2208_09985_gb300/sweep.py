@@ -2,7 +2,8 @@
 
 The grid:
 - edit rates 5%, 10% and 15% (50/25/25 substitutions/insertions/deletions);
-- W in {32, 64, 128}, with O in {W/4, 3W/8, W/2};
+- W in {32, 64, 128}, with O in {W/4, 3W/8, W/2, W/2+1} (W/2+1 is the paper's
+  operating point: the DENT entry of W-O+1 bits fits one word at W = 64, O = 33);
 - each of SENE, DENT and ET on or off (the paper's ablations, Sections 2.4.1-2.4.3);
 - the plain launch and the learned-ordering persistent launch side by side.
 
@@ -10,7 +11,13 @@ Each point reports:
 - throughput;
 - the DP-table footprint per pair;
 - the mean edit count against the exact free-end distance of the same pairs
-  (scrooge_edit_distance).
+  (scrooge_edit_distance), and the paper's quantile scores (Section 5): the
+  0.5, 0.1, 0.01 and 0.001 quantiles counted from the worst pair (for 20,000
+  pairs, 0.01 is the 200th worst) of the windowed edit count, of the exact
+  distance, and of the excess of one over the other, pair by pair;
+- the full-width kernel with every improvement on beside the plain
+  launch, so that SENE on and off (GenASM's edge vectors) compare on the same
+  kernel.
 
 SENE, DENT, ET and the launch form never change results, and each run checks
 that its edit counts and CIGAR offsets match the first run of the same
@@ -41,6 +48,15 @@ import paper_2208_09985_gb300 as sc
 from paper_2208_09985_gb300 import learned, synth
 
 TOGGLES = [(sene, dent, et) for sene in (1, 0) for dent in (1, 0) for et in (1, 0)]
+QUANTILES = (0.5, 0.1, 0.01, 0.001)
+
+
+def worst_quantile(values, q: float) -> float:
+    """The q quantile counted from the worst (largest) value: the ceil(q * n)-th largest of n values."""
+    v = np.sort(np.asarray(values, dtype=np.float64))[::-1]
+    if v.size == 0:
+        return float("nan")
+    return float(v[max(1, int(np.ceil(q * v.size))) - 1])
 
 
 def toggle_flags(sene: int, dent: int, et: int) -> int:
@@ -125,7 +141,7 @@ def main(argv=None):
         bases = int(np.diff(batch.pattern_off).sum())
         for W in (int(x) for x in args.W.split(",")):
             k = W
-            for O in (W // 4, 3 * W // 8, W // 2):
+            for O in (W // 4, 3 * W // 8, W // 2, W // 2 + 1):
                 ref = None
                 # statistics of the method (rows per window) from one run with ET
                 win = torch.zeros(db.n_pairs, dtype=torch.int32, device="cuda")
@@ -135,8 +151,10 @@ def main(argv=None):
                 sc.scrooge_set_stats(ctx)
                 mean_rows = float(rws.sum().item()) / max(1, int(win.sum().item()))
                 for sene, dent, et in TOGGLES:
-                    for form in ("plain", "learned"):
-                        fl = toggle_flags(sene, dent, et) | (sc.SCROOGE_LEARNED if form == "learned" else 0)
+                    forms = ("plain", "learned", "full") if (sene, dent, et) == (1, 1, 1) else ("plain", "learned")
+                    for form in forms:
+                        fl = toggle_flags(sene, dent, et) | {"plain": 0, "learned": sc.SCROOGE_LEARNED,
+                                                             "full": sc.SCROOGE_NO_BAND}[form]
                         ms = timed(ctx, db, W, O, k, fl, args.steps, stream)
                         shape = sc.scrooge_last_launch_shape(ctx)
                         res = sc.device_results(db)
@@ -147,7 +165,11 @@ def main(argv=None):
                             ok = ec >= 0
                             acc = {"mean_edits": float(ec[ok].mean()), "failed_pairs": int((~ok).sum()),
                                    "mean_excess_over_free_end": float((ec[ok] - fe_np[ok]).mean()),
-                                   "pairs_at_optimum": float((ec[ok] == fe_np[ok]).mean())}
+                                   "pairs_at_optimum": float((ec[ok] == fe_np[ok]).mean()),
+                                   "quantiles": {str(q): {"windowed": worst_quantile(ec[ok], q),
+                                                          "exact": worst_quantile(fe_np[ok], q),
+                                                          "excess": worst_quantile(ec[ok] - fe_np[ok], q)}
+                                                 for q in QUANTILES}}
                         elif not (np.array_equal(res["edit_counts"], ref["edit_counts"])
                                   and np.array_equal(res["cigar_off"], ref["cigar_off"])):
                             raise SystemExit(f"sweep: rate {rate} W {W} O {O} flags {fl} changed the results")
@@ -221,6 +243,8 @@ def summary(rows) -> str:
     """Markdown tables of a sweep's JSON records."""
     lines = ["| rate | W | O | mean edits | exact free-end | excess | at optimum | rows/window |",
              "|---|---|---|---|---|---|---|---|"]
+    qlines = ["| rate | W | O | " + " | ".join(f"q={q}: windowed / exact / excess" for q in QUANTILES) + " |",
+              "|---|---|---|" + "---|" * len(QUANTILES)]
     seen = set()
     for r in rows:
         key = (r["rate"], r["W"], r["O"])
@@ -230,6 +254,11 @@ def summary(rows) -> str:
         lines.append(f"| {r['rate']:.2f} | {r['W']} | {r['O']} | {r['mean_edits']:.1f} | {r['free_end_mean']:.1f} | "
                      f"{r['mean_excess_over_free_end']:.2f} | {100 * r['pairs_at_optimum']:.1f}% | "
                      f"{r['mean_rows_per_window']:.2f} |")
+        qs = r["quantiles"]
+        qlines.append(f"| {r['rate']:.2f} | {r['W']} | {r['O']} | " + " | ".join(
+            f"{qs[str(q)]['windowed']:.0f} / {qs[str(q)]['exact']:.0f} / {qs[str(q)]['excess']:.0f}"
+            for q in QUANTILES) + " |")
+    lines += ["", "Quantile scores, counted from the worst pair (edit counts; lower is better):", ""] + qlines
     lines += ["", "| rate | W | O | SENE | DENT | ET | plain aln/s | learned aln/s | table B/window (method) | "
               "smem B/pair (kernel) | kernel |", "|---|---|---|---|---|---|---|---|---|---|---|"]
     by = {}
@@ -242,6 +271,17 @@ def summary(rows) -> str:
                      f"{p['alignments_per_s'] / 1e6:.3f}M | {q['alignments_per_s'] / 1e6:.3f}M | "
                      f"{base['method_table_bytes_per_window']:.0f} | {base['smem_bytes_per_pair']:.0f} | "
                      f"{base['kernel']} |" if p and q else "")
+    # SENE on and off on the same kernel (the full-width kernel serves both)
+    lines += ["", "SENE on and off on the full-width kernel (Scrooge's entries against GenASM's edges):", "",
+              "| rate | W | O | SENE on, full width | SENE off (full width) | ratio |", "|---|---|---|---|---|---|"]
+    for key, d in by.items():
+        if key[3:] != (1, 1, 1):
+            continue
+        on = d.get("full")
+        off = by.get(key[:3] + (0, 1, 1), {}).get("plain")
+        if on and off:
+            lines.append(f"| {key[0]:.2f} | {key[1]} | {key[2]} | {on['alignments_per_s'] / 1e6:.3f}M | "
+                         f"{off['alignments_per_s'] / 1e6:.3f}M | {on['alignments_per_s'] / off['alignments_per_s']:.2f} |")
     return "\n".join(x for x in lines if x is not None)
 
 
