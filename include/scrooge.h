@@ -259,7 +259,8 @@ int scrooge_last_launch_shape(const scrooge_ctx *ctx, int64_t *shape, int32_t n)
  * after one untimed run), and installs the fastest configuration in the
  * context. If `results` is not NULL it receives up to max_results rows of 5
  * int32: lanes, rows, warps, microseconds, 1. With SCROOGE_LEARNED on windows
- * the banded kernel serves, it then:
+ * the banded kernel serves, that sweep times persistent launches in input
+ * order (learned launches take the per-bucket settings below), and it then:
  *   - times the heavy load classes (scrooge_set_heavy_class) 16, 15, ..., 10,
  *     0 before and again after the settings sweep (at least 3 timed runs
  *     each), as rows 0, class, 0, microseconds, 2, and installs the fastest

@@ -829,9 +829,12 @@ int scrooge_autotune(scrooge_ctx *c, const uint32_t *texts, const int64_t *text_
         return fail(c, SCROOGE_E_CUDA, "cudaEventCreate failed");
     int nres = 0, rc = SCROOGE_OK;
     const uint32_t fl = (flags | SCROOGE_DEVICE_PTRS) & ~(uint32_t)SCROOGE_SYNC;
+    // the kernel settings sweep times launches that use those settings: with SCROOGE_LEARNED on
+    // band-sized windows (whose launches take the per-bucket settings) a persistent launch in input order
+    uint32_t fl_run = fl;
     auto call = [&]() {
         return scrooge_align_batch(c, texts, text_offsets, text_lengths, patterns, pattern_offsets, pattern_lengths,
-                                   n_pairs, W, O, k, fl, edit_counts, text_consumed, cigar, cigar_capacity,
+                                   n_pairs, W, O, k, fl_run, edit_counts, text_consumed, cigar, cigar_capacity,
                                    cigar_offsets);
     };
     // one untimed run, then the fastest of `reps` timed runs (CUDA events on the context stream)
@@ -885,6 +888,7 @@ int scrooge_autotune(scrooge_ctx *c, const uint32_t *texts, const int64_t *text_
     if (tune_classes) rc = sweep_classes();
     float best = -1.f;
     KernelConfig best_cfg = saved;
+    if (tune_classes) fl_run = (fl & ~(uint32_t)SCROOGE_LEARNED) | SCROOGE_PERSISTENT;
     for (int li = 0; li < 4 && rc == SCROOGE_OK; ++li) {
         const int lanes = lanes_opts[ix][li];
         if (!lanes) continue;
@@ -903,6 +907,7 @@ int scrooge_autotune(scrooge_ctx *c, const uint32_t *texts, const int64_t *text_
         }
     }
     c->kcfg[ix] = rc == SCROOGE_OK ? best_cfg : saved;
+    fl_run = fl;
     if (rc == SCROOGE_OK && tune_classes) rc = sweep_classes();  // again, with the chosen settings
     if (rc != SCROOGE_OK) c->heavy_class = saved_class;
     // learned launches: kernel and settings per load bucket (the rest, then the heavy pairs if the
