@@ -55,6 +55,9 @@ struct LaneTable {
     int32_t pair[32], n[32], m[32], ti[32], pj[32], ccap[32], cn[32], edits[32], st_windows[32], state[32];
     uint32_t ccur[32];
     int32_t pad[32];
+    // the current window's 64 text and pattern bases (both bit planes), staged by the set-up for
+    // the traceback
+    uint64_t qT0[32], qT1[32], qP0[32], qP1[32];
 };
 static_assert(sizeof(LaneTable) == kLaneTableBytes, "lane table size");
 
@@ -162,7 +165,7 @@ __device__ __forceinline__ void lane_window_tb(const AlignParams &p, LaneTable &
     const int L = p.W - p.O;
     const int fb_row = p.fb_ncol * kLFbWin * 2;
     const int ti = part ? lt.ti[lane] : 0, pj = part ? lt.pj[lane] : 0;
-    const int n = part ? lt.n[lane] : 0, m = part ? lt.m[lane] : 0;
+    const int m = part ? lt.m[lane] : 0;
     // the window's 64 text and pattern bases in 64-bit registers (a match run never
     // reaches past the window, so the zeros beyond the sequence ends are never compared)
     uint64_t qT0 = 0, qT1 = 0, qP0 = 0, qP1 = 0;
@@ -173,18 +176,10 @@ __device__ __forceinline__ void lane_window_tb(const AlignParams &p, LaneTable &
     out.cur = 0u;
     out.edits = 0;
     if (part) {
-        const uint2 *tseq = reinterpret_cast<const uint2 *>(p.texts + (lt.toff[lane] >> 4));
-        const uint2 *pseq = reinterpret_cast<const uint2 *>(p.patterns + (lt.poff[lane] >> 4));
-        const int64_t tblk = (n + 31) >> 5, pblk = (m + 31) >> 5;
-        uint32_t a0, a1, b0, b1;
-        load32(tseq, tblk, ti, a0, a1);
-        load32(tseq, tblk, (int64_t)ti + 32, b0, b1);
-        qT0 = ((uint64_t)a0 << 32) | b0;
-        qT1 = ((uint64_t)a1 << 32) | b1;
-        load32(pseq, pblk, pj, a0, a1);
-        load32(pseq, pblk, (int64_t)pj + 32, b0, b1);
-        qP0 = ((uint64_t)a0 << 32) | b0;
-        qP1 = ((uint64_t)a1 << 32) | b1;
+        qT0 = lt.qT0[lane];
+        qT1 = lt.qT1[lane];
+        qP0 = lt.qP0[lane];
+        qP1 = lt.qP1[lane];
         out.dst = p.cigar + lt.cbase[lane];
         out.cap = lt.ccap[lane];
         out.n = lt.cn[lane];
@@ -350,6 +345,11 @@ __global__ void __launch_bounds__(64, 5) align_lane_kernel(const AlignParams p) 
                 PMC[c] = ~((w0 ^ m0) | (w1 ^ m1));  // bit j set: pattern base j equals text base c
                 XA[c] = ~(c < 32 ? __funnelshift_l(S1, S0, c) : __funnelshift_l(S2, S1, c - 32));
             }
+            // the window's bases for the traceback: text from ti, pattern from pj (64 each)
+            lt.qT0[lane] = ((uint64_t)Ta0 << 32) | Tb0;
+            lt.qT1[lane] = ((uint64_t)Ta1 << 32) | Tb1;
+            lt.qP0[lane] = ((uint64_t)__funnelshift_l(Pb0, Pa0, 16) << 32) | __funnelshift_l(Pc0, Pb0, 16);
+            lt.qP1[lane] = ((uint64_t)__funnelshift_l(Pb1, Pa1, 16) << 32) | __funnelshift_l(Pc1, Pb1, 16);
             if (__any_sync(kFull, nw < 64)) {
                 // columns at or past the end of the text window match nothing
                 const uint32_t v0 = ~prefix_mask(nw), v1 = ~prefix_mask(nw - 32);

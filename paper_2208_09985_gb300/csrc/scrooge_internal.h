@@ -145,7 +145,7 @@ inline int ext_dent_ring(int W, int O, int k, int lanes, bool on) {
 // multiple of 8, at most 64) stored columns per row, rcap rows per lane in shared memory after a
 // per-warp table of kLaneTableBytes; windows beyond the band are recomputed at full width by
 // groups of 4 lanes (fb: k+1 rows of fb_ncol columns x 8 windows x 2 words per warp).
-constexpr int kLaneTableBytes = 3072;
+constexpr int kLaneTableBytes = 4096;
 cudaError_t launch_align_lane(const AlignParams &, int wpb, int blocks, size_t smem, cudaStream_t);
 cudaError_t occupancy_lane(int ncol, int wpb, size_t smem, int *blocks_per_sm);
 // Warp-specialised banded kernel (align_band.cu): blocks of 4 DC warps (4 lanes per pair, two
