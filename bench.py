@@ -76,6 +76,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the built-in kernel settings (default: autotune on a separate sample first)")
+    ap.add_argument("--lanes", type=int, default=0,
+                    help="with --no-autotune: lanes per pair of the 64-base banded kernel (persistent launches and "
+                         "the learned launches' rest bucket), with --rows and --wpb")
+    ap.add_argument("--rows", type=int, default=8)
+    ap.add_argument("--wpb", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="time budget of the CPU baseline")
     ap.add_argument("--model", default="", help="saved ordering model (JSON); default: train one first")
     ap.add_argument("--train-pairs", type=int, default=50_000)
@@ -258,12 +263,22 @@ def path_flags(sc, name: str) -> int:
 
 # sources of each alignment kernel, hashed to tell whether committed ncu counters still apply
 KERNEL_SOURCES = {"align_band_kernel": ("align_band.cu", "align_kernel.cuh"),
+                  "align_lane_kernel": ("align_lane.cu", "align_kernel.cuh"),
                   "align_kernel": ("align_kernel.cuh",)}
 
 
-def kernel_name(sc, W: int, flags: int) -> str:
-    """The alignment kernel a call with these flags runs."""
-    return "align_band_kernel" if sc.settings_slot(W, flags) == 0 else "align_kernel"
+def kernel_name(sc, ctx, W: int, flags: int) -> str:
+    """The alignment kernel that serves most pairs of a learned call with these flags (on 33..64-base
+    windows: the rest bucket's kernel, or the persistent launch's when the model order is off)."""
+    slot = sc.settings_slot(W, flags)
+    if slot == 0 and sc.scrooge_get_learned_order(ctx):
+        kind, lanes, _, _ = sc.scrooge_get_bucket_config(ctx, 1)
+        if kind == 1:
+            return "align_kernel"
+        return "align_lane_kernel" if lanes == 1 else "align_band_kernel"
+    if slot == 0:
+        return "align_lane_kernel" if sc.scrooge_get_kernel_config(ctx, 0)[0] == 1 else "align_band_kernel"
+    return "align_band_kernel" if slot == 3 else "align_kernel"
 
 
 def prepare_model(sc, ctx, args):
@@ -364,6 +379,9 @@ def main():
                                   "input": [r[3] / 1e3 for r in table if r[4] == 4 and r[0] == 0]},
                      "long_class_ms": [[r[1], r[3] / 1e3] for r in table if r[4] == 5],
                      "seconds": time.perf_counter() - t0}
+    if args.no_autotune and args.lanes:
+        sc.scrooge_set_kernel_config(ctx, 0, args.lanes, args.rows, args.wpb)
+        sc.scrooge_set_bucket_config(ctx, 1, 0, args.lanes, args.rows, args.wpb)
     db = sc.DeviceBatch(pb)
 
     # untimed run with per-pair statistics: algorithmic DP cells of the method
@@ -516,7 +534,7 @@ def main():
     # window's edit distance; the kernel basis is the full-width kernel's own 3*words-1 LOP3/SHF
     ops_per_cell = PAPER_OPS_PER_CELL
     kernel_ops_per_cell = 3 * words - 1
-    kernel = kernel_name(sc, W, flags)
+    kernel = kernel_name(sc, ctx, W, flags)
     achieved = total_cells * ops_per_cell / (kernel_ms / 1e3)
     probe = sc.scrooge_logic_peak(ctx, 4096)
     traffic = kernel_traffic(kernel, args.workload, n_pairs)
