@@ -65,6 +65,18 @@ static_assert(sizeof(LaneTable) == kLaneTableBytes, "lane table size");
 __device__ __forceinline__ uint32_t lane_shr1(uint32_t v) { return __funnelshift_r(v, kFull, 1); }
 __device__ __forceinline__ uint32_t lane_shl1(uint32_t v) { return __funnelshift_l(kFull, v, 1); }
 
+// Bulk copies from shared to global memory (TMA, asynchronous): a row slot goes to the device area
+// in one instruction of one lane. The callers order them against the row stores with __syncwarp.
+__device__ __forceinline__ void bulk_copy_s2g(uint32_t *gdst, const uint32_t *ssrc, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst),
+                 "r"((uint32_t)__cvta_generic_to_shared(ssrc)), "r"(bytes));
+    asm volatile("cp.async.bulk.commit_group;");
+}
+// The copies issued so far have read their source (it may be overwritten).
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;"); }
+// The copies issued so far are complete (their destination may be read).
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;"); }
+
 __device__ __forceinline__ int64_t shfl64(int64_t v, int src) {
     const int lo = __shfl_sync(kFull, (int)(uint32_t)v, src);
     const int hi = __shfl_sync(kFull, (int)(uint32_t)((uint64_t)v >> 32), src);
@@ -290,7 +302,7 @@ __device__ __forceinline__ void lane_window_tb(const AlignParams &p, LaneTable &
 }
 
 template <int NC8>
-__global__ void __launch_bounds__(64, 5) align_lane_kernel(const AlignParams p) {
+__global__ void __launch_bounds__(64, 4) align_lane_kernel(const AlignParams p) {
     constexpr int ROWW = 8 * NC8 * 32;  // words of one stored row of a warp
     extern __shared__ __align__(16) uint32_t smem[];
     const int lane = threadIdx.x & 31;
@@ -362,23 +374,29 @@ __global__ void __launch_bounds__(64, 5) align_lane_kernel(const AlignParams p) 
         int d_opt = -1;
         bool busy = active;
         int slot = 0;  // row slot of row d
+        // Before a row slot is reused its row goes to the device area ([row][column][lane], the slot's own
+        // layout) by a bulk copy that lane 0 issues one row ahead, so the copy runs behind a row of
+        // work; a lane whose pair is done copies a stale row, which its traceback never reads.
+        uint32_t *ring_w = ring - lane, *spill_w = spill - lane;
         for (int d = 0; d <= dmax; ++d) {
             if (!__any_sync(kFull, busy)) break;
+            if (d >= rcap) {
+                if (rcap == 1 && lane == 0) bulk_copy_s2g(spill_w + (int64_t)(d - 1) * ROWW, ring_w, ROWW * 4);
+                if (lane == 0) bulk_wait_read();  // the slot of row d - rcap has been read
+                __syncwarp();
+            }
+            if (rcap > 1 && d + 1 >= rcap && d + 1 <= dmax) {
+                // the slot that row d + 1 takes holds row d + 1 - rcap, complete since an earlier row
+                const int s1 = slot + 1 == rcap ? 0 : slot + 1;
+                __syncwarp();
+                if (lane == 0) {
+                    asm volatile("fence.proxy.async.shared::cta;");
+                    bulk_copy_s2g(spill_w + (int64_t)(d + 1 - rcap) * ROWW, ring_w + s1 * ROWW, ROWW * 4);
+                }
+            }
             // the column right of the window: bits j < m_w - d of R[n][d] are 1 (0 in complement)
             uint32_t pC = ~prefix_mask(mw - d - 64 + kLB0);
             uint32_t *rowp = ring + slot * ROWW;
-            if (d >= rcap) {  // the slot's row (d - rcap) goes to the device area first
-                uint32_t *evp = spill + (int64_t)(d - rcap) * ROWW;
-#pragma unroll 1
-                for (int c0 = 0; c0 < 8 * NC8; c0 += 8) {
-                    uint32_t v[8];
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) v[q] = busy ? rowp[(c0 + q) * 32] : 0u;
-#pragma unroll
-                    for (int q = 0; q < 8; ++q)
-                        if (busy) evp[(c0 + q) * 32] = v[q];
-                }
-            }
             lane_dc_row<NC8>(XA, PMC, pC, busy, rowp);
             if (busy && ((pC >> (31 - kLB0)) & 1u) != 0u) {
                 d_opt = d;
@@ -386,6 +404,8 @@ __global__ void __launch_bounds__(64, 5) align_lane_kernel(const AlignParams p) 
             }
             slot = slot + 1 == rcap ? 0 : slot + 1;
         }
+        if (lane == 0) bulk_wait_all();  // the evicted rows are in place before the traceback reads them
+        __syncwarp();
 
         // ---- windows beyond the band: full-width DC by groups of kLFbLanes lanes, up to kLFbWin of
         // them per round; a window beyond that waits (keeps its cursors) and is recomputed next round
