@@ -306,7 +306,7 @@ int scrooge_set_order(scrooge_ctx *ctx, const int32_t *order, int32_t n_pairs);
  *     sequential, so the longest pairs must start first, and pairs of
  *     similar length share warps and finish together. On uneven batches this
  *     measured faster than orders that mix in the predicted load, even the
- *     true load (see the design notes).
+ *     true load.
  * Here rows is the predicted mean DP rows per window, the load class is
  * floor(4 log2(rows + 1)) and the work class is
  * floor(log2((m + 1)(rows + 1))) - 6, both clipped to 0..15; they choose the

@@ -19,7 +19,7 @@
  *     keep the traceback only through the first W-O characters, continue with
  *     the rest of both strings.
  *
- * Readings where the paper is silent (each also written in the design notes):
+ * Readings where the paper is silent:
  *   - bit order: bit j = 0 is the most significant bit; "<< 1" moves bit j+1
  *     into bit j and shifts a 0 into bit m-1;
  *   - "distance" is the edit distance with a free end in the text: by

@@ -685,14 +685,7 @@ cudaError_t launch_ws_kernel(const AlignParams &p, int blocks, size_t smem, cuda
 }
 
 cudaError_t occupancy_ws_kernel(size_t smem, int *per_sm) {
-    cudaFuncAttributes a;
-    cudaError_t e = cudaFuncGetAttributes(&a, align_ws_kernel);
-    if (e != cudaSuccess) return e;
-    if ((size_t)a.maxDynamicSharedSizeBytes < smem &&
-        (e = cudaFuncSetAttribute(align_ws_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
-            cudaSuccess)
-        return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, align_ws_kernel, 32 * (kWsDcWarps + 1), smem);
+    return occupancy_raising_smem(align_ws_kernel, 32 * (kWsDcWarps + 1), smem, per_sm);
 }
 
 template <int G, int NWW, int BW>
@@ -701,19 +694,9 @@ cudaError_t launch_g(const AlignParams &p, int wpb, int blocks, size_t smem, cud
     return cudaGetLastError();
 }
 
-// The dynamic shared-memory limit of a kernel is only ever raised: one call may launch the same
-// instantiation with two shapes (the long-pair launch and the main one).
 template <int G, int NWW, int BW>
 cudaError_t occupancy_g(int wpb, size_t smem, int *per_sm) {
-    cudaFuncAttributes a;
-    cudaError_t e = cudaFuncGetAttributes(&a, align_band_kernel<G, NWW, BW>);
-    if (e != cudaSuccess) return e;
-    if ((size_t)a.maxDynamicSharedSizeBytes < smem &&
-        (e = cudaFuncSetAttribute(align_band_kernel<G, NWW, BW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem)) !=
-            cudaSuccess)
-        return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, align_band_kernel<G, NWW, BW>, 32 * wpb, smem);
+    return occupancy_raising_smem(align_band_kernel<G, NWW, BW>, 32 * wpb, smem, per_sm);
 }
 
 }  // namespace kern

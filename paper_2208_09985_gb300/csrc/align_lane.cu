@@ -233,10 +233,19 @@ __device__ __forceinline__ void lane_window_tb(const AlignParams &p, LaneTable &
                 // t1 = bits j, j+1 of entry (i+1, d-1); r0b = bit j+1 of entry (i, d-1)
                 uint32_t t1, r0b;
                 if (fbg < 0) {
-                    const uint32_t *rp = (r > ring_lo ? ring + rs * ROWW : spill + (int64_t)r * ROWW) + i * 32;
                     const int kk = j - i + kLB0;  // band bit of (i, j); 0..30 on the path
-                    const uint32_t v1 = ld1 ? ~rp[32] : 0u;  // stored in complement form
-                    const uint32_t v0 = tx ? ~rp[0] : 0u;
+                    // stored in complement form; evicted rows were written by bulk copies, which do not
+                    // pass through this SM's L1, so they are read from L2 (ld.global.cg)
+                    uint32_t v1 = 0u, v0 = 0u;
+                    if (r > ring_lo) {
+                        const uint32_t *rp = ring + rs * ROWW + i * 32;
+                        if (ld1) v1 = ~rp[32];
+                        if (tx) v0 = ~rp[0];
+                    } else {
+                        const uint32_t *gp = spill + (int64_t)r * ROWW + i * 32;
+                        if (ld1) v1 = ~__ldcg(gp + 32);
+                        if (tx) v0 = ~__ldcg(gp);
+                    }
                     const uint64_t q1 = (1ull << 63) | ((uint64_t)v1 << 31);  // band bit kk-1 at position kk
                     t1 = (uint32_t)((q1 << kk) >> 62);
                     r0b = (uint32_t)((((uint64_t)v0 << 32) << (kk + 1)) >> 63);
@@ -404,7 +413,10 @@ __global__ void __launch_bounds__(64, 4) align_lane_kernel(const AlignParams p) 
             }
             slot = slot + 1 == rcap ? 0 : slot + 1;
         }
-        if (lane == 0) bulk_wait_all();  // the evicted rows are in place before the traceback reads them
+        if (lane == 0) {
+            bulk_wait_all();  // the evicted rows are in place before the traceback reads them
+            asm volatile("fence.proxy.async.global;" ::: "memory");  // and visible to generic loads
+        }
         __syncwarp();
 
         // ---- windows beyond the band: full-width DC by groups of kLFbLanes lanes, up to kLFbWin of
@@ -460,14 +472,7 @@ cudaError_t launch_nc(const AlignParams &p, int wpb, int blocks, size_t smem, cu
 
 template <int NC8>
 cudaError_t occupancy_nc(int wpb, size_t smem, int *per_sm) {
-    cudaFuncAttributes a;
-    cudaError_t e = cudaFuncGetAttributes(&a, align_lane_kernel<NC8>);
-    if (e != cudaSuccess) return e;
-    if ((size_t)a.maxDynamicSharedSizeBytes < smem &&
-        (e = cudaFuncSetAttribute(align_lane_kernel<NC8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
-            cudaSuccess)
-        return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, align_lane_kernel<NC8>, 32 * wpb, smem);
+    return occupancy_raising_smem(align_lane_kernel<NC8>, 32 * wpb, smem, per_sm);
 }
 
 }  // namespace kern

@@ -47,32 +47,23 @@ cudaError_t occupancy_w128(int lanes, bool sene, int swp, int warps_per_block, s
     const int threads = 32 * warps_per_block;
     switch (key(lanes, sene, swp)) {
         case key(8, true, 1):
-            cudaFuncSetAttribute(kern::align_kernel<4, 8, true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
-            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kern::align_kernel<4, 8, true, 1>, threads, smem_bytes);
+            return occupancy_raising_smem(kern::align_kernel<4, 8, true, 1>, threads, smem_bytes, blocks);
         case key(8, true, 2):
-            cudaFuncSetAttribute(kern::align_kernel<4, 8, true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
-            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kern::align_kernel<4, 8, true, 2>, threads, smem_bytes);
+            return occupancy_raising_smem(kern::align_kernel<4, 8, true, 2>, threads, smem_bytes, blocks);
         case key(8, true, 4):
-            cudaFuncSetAttribute(kern::align_kernel<4, 8, true, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
-            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kern::align_kernel<4, 8, true, 4>, threads, smem_bytes);
+            return occupancy_raising_smem(kern::align_kernel<4, 8, true, 4>, threads, smem_bytes, blocks);
         case key(16, true, 1):
-            cudaFuncSetAttribute(kern::align_kernel<4, 16, true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
-            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kern::align_kernel<4, 16, true, 1>, threads, smem_bytes);
+            return occupancy_raising_smem(kern::align_kernel<4, 16, true, 1>, threads, smem_bytes, blocks);
         case key(16, true, 2):
-            cudaFuncSetAttribute(kern::align_kernel<4, 16, true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
-            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kern::align_kernel<4, 16, true, 2>, threads, smem_bytes);
+            return occupancy_raising_smem(kern::align_kernel<4, 16, true, 2>, threads, smem_bytes, blocks);
         case key(16, true, 4):
-            cudaFuncSetAttribute(kern::align_kernel<4, 16, true, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
-            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kern::align_kernel<4, 16, true, 4>, threads, smem_bytes);
+            return occupancy_raising_smem(kern::align_kernel<4, 16, true, 4>, threads, smem_bytes, blocks);
         case key(8, false, 1):
-            cudaFuncSetAttribute(kern::align_kernel<4, 8, false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
-            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kern::align_kernel<4, 8, false, 1>, threads, smem_bytes);
+            return occupancy_raising_smem(kern::align_kernel<4, 8, false, 1>, threads, smem_bytes, blocks);
         case key(8, false, 2):
-            cudaFuncSetAttribute(kern::align_kernel<4, 8, false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
-            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kern::align_kernel<4, 8, false, 2>, threads, smem_bytes);
+            return occupancy_raising_smem(kern::align_kernel<4, 8, false, 2>, threads, smem_bytes, blocks);
         case key(8, false, 4):
-            cudaFuncSetAttribute(kern::align_kernel<4, 8, false, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
-            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kern::align_kernel<4, 8, false, 4>, threads, smem_bytes);
+            return occupancy_raising_smem(kern::align_kernel<4, 8, false, 4>, threads, smem_bytes, blocks);
         default:
             return cudaErrorInvalidValue;
     }

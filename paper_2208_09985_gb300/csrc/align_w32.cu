@@ -32,17 +32,13 @@ cudaError_t occupancy_w32(int lanes, bool sene, int swp, int warps_per_block, si
     const int threads = 32 * warps_per_block;
     switch (key(lanes, sene, swp)) {
         case key(1, true, 1):
-            cudaFuncSetAttribute(kern::align_kernel<1, 1, true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
-            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kern::align_kernel<1, 1, true, 1>, threads, smem_bytes);
+            return occupancy_raising_smem(kern::align_kernel<1, 1, true, 1>, threads, smem_bytes, blocks);
         case key(2, true, 1):
-            cudaFuncSetAttribute(kern::align_kernel<1, 2, true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
-            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kern::align_kernel<1, 2, true, 1>, threads, smem_bytes);
+            return occupancy_raising_smem(kern::align_kernel<1, 2, true, 1>, threads, smem_bytes, blocks);
         case key(4, true, 1):
-            cudaFuncSetAttribute(kern::align_kernel<1, 4, true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
-            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kern::align_kernel<1, 4, true, 1>, threads, smem_bytes);
+            return occupancy_raising_smem(kern::align_kernel<1, 4, true, 1>, threads, smem_bytes, blocks);
         case key(2, false, 1):
-            cudaFuncSetAttribute(kern::align_kernel<1, 2, false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
-            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kern::align_kernel<1, 2, false, 1>, threads, smem_bytes);
+            return occupancy_raising_smem(kern::align_kernel<1, 2, false, 1>, threads, smem_bytes, blocks);
         default:
             return cudaErrorInvalidValue;
     }

@@ -44,29 +44,21 @@ cudaError_t occupancy_w64(int lanes, bool sene, int swp, int warps_per_block, si
     const int threads = 32 * warps_per_block;
     switch (key(lanes, sene, swp)) {
         case key(2, true, 1):
-            cudaFuncSetAttribute(kern::align_kernel<2, 2, true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
-            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kern::align_kernel<2, 2, true, 1>, threads, smem_bytes);
+            return occupancy_raising_smem(kern::align_kernel<2, 2, true, 1>, threads, smem_bytes, blocks);
         case key(2, true, 2):
-            cudaFuncSetAttribute(kern::align_kernel<2, 2, true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
-            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kern::align_kernel<2, 2, true, 2>, threads, smem_bytes);
+            return occupancy_raising_smem(kern::align_kernel<2, 2, true, 2>, threads, smem_bytes, blocks);
         case key(4, true, 1):
-            cudaFuncSetAttribute(kern::align_kernel<2, 4, true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
-            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kern::align_kernel<2, 4, true, 1>, threads, smem_bytes);
+            return occupancy_raising_smem(kern::align_kernel<2, 4, true, 1>, threads, smem_bytes, blocks);
         case key(4, true, 2):
-            cudaFuncSetAttribute(kern::align_kernel<2, 4, true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
-            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kern::align_kernel<2, 4, true, 2>, threads, smem_bytes);
+            return occupancy_raising_smem(kern::align_kernel<2, 4, true, 2>, threads, smem_bytes, blocks);
         case key(8, true, 1):
-            cudaFuncSetAttribute(kern::align_kernel<2, 8, true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
-            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kern::align_kernel<2, 8, true, 1>, threads, smem_bytes);
+            return occupancy_raising_smem(kern::align_kernel<2, 8, true, 1>, threads, smem_bytes, blocks);
         case key(8, true, 2):
-            cudaFuncSetAttribute(kern::align_kernel<2, 8, true, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
-            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kern::align_kernel<2, 8, true, 2>, threads, smem_bytes);
+            return occupancy_raising_smem(kern::align_kernel<2, 8, true, 2>, threads, smem_bytes, blocks);
         case key(4, false, 1):
-            cudaFuncSetAttribute(kern::align_kernel<2, 4, false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
-            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kern::align_kernel<2, 4, false, 1>, threads, smem_bytes);
+            return occupancy_raising_smem(kern::align_kernel<2, 4, false, 1>, threads, smem_bytes, blocks);
         case key(4, false, 2):
-            cudaFuncSetAttribute(kern::align_kernel<2, 4, false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
-            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kern::align_kernel<2, 4, false, 2>, threads, smem_bytes);
+            return occupancy_raising_smem(kern::align_kernel<2, 4, false, 2>, threads, smem_bytes, blocks);
         default:
             return cudaErrorInvalidValue;
     }

@@ -297,14 +297,14 @@ __global__ void adam_kernel(float *model, const float *grad, float *m1, float *m
 }
 
 // Bucket key of each pair from the predicted per-window load (log1p of the
-// mean DP rows per window) and the pattern length: ascending keys put heavy
-// windows first and, inside a load class, long pairs first.
-// 8-bit bucket key, sorted ascending:
+// mean DP rows per window) and the pattern length. 8-bit key, sorted ascending
+// (a stable sort keeps input order inside a bucket):
 //   bit 7     0 for the long pairs (work class >= long_class): they go first;
-//   bit 6     0 for the heavy pairs (load class >= heavy_class);
-//   bits 3-5  7 - work class / 2: predicted total work, pattern length x rows per window, largest first;
-//   bits 0-2  load class / 2: lighter per-window load (hence more windows) first within a work class,
-//             which measured faster than heavier-first on both the long and the uneven reads.
+//   bit 6     0 for the heavy pairs (load class >= heavy_class): they go next;
+//   bits 0-5  length class, eighths of an octave below the batch's longest pattern: the longest
+//             pairs first (the windows of a pair are sequential, so the longest chains must start
+//             first; on the measured batches ordering by predicted load inside this key gained
+//             nothing over length alone).
 // rows = predicted mean DP rows per window, load class = floor(4 log2(rows + 1)) in 0..15,
 // work class = floor(log2((m + 1)(rows + 1))) - 6 in 0..15.
 // The longest pattern of the batch (one block).

@@ -161,6 +161,21 @@ bool supported_w128(int lanes, bool sene, int swp);
 
 bool align_supported(int words, int lanes);
 
+// Occupancy of `kernel` at `threads` threads and `smem` bytes of dynamic shared memory, first
+// raising the kernel's dynamic shared-memory limit to `smem` if it is lower. The limit is never
+// lowered: launches of one kernel with different settings (the buckets of a learned call, the
+// allocation-free entry point) may be planned in any order and run concurrently.
+template <typename K>
+inline cudaError_t occupancy_raising_smem(K *kernel, int threads, size_t smem, int *blocks_per_sm) {
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, kernel);
+    if (e != cudaSuccess) return e;
+    if ((size_t)a.maxDynamicSharedSizeBytes < smem &&
+        (e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+        return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, kernel, threads, smem);
+}
+
 // Dense CIGAR output (cigar_compact.cu).
 int64_t scan_temp_words(int64_t n);
 int scan_kernel_count(int64_t n);

@@ -357,8 +357,11 @@ def test_bucket_settings_identical(ctx):
     try:
         for hc in (16, 10):
             sc.scrooge_set_heavy_class(h, hc)
+            # the last pair: both buckets on one full-width kernel, the rest with more shared memory
+            # than the heavy bucket (planned second), which must not lower the kernel's limit
             for heavy_cfg, rest_cfg in (((0, 1, 4, 1), (1, 4, 4, 2)), ((1, 8, 2, 2), (0, 1, 2, 1)),
-                                        ((0, 8, 8, 2), (0, 2, 8, 1)), ((0, 1, 3, 2), (0, 1, 16, 2))):
+                                        ((0, 8, 8, 2), (0, 2, 8, 1)), ((0, 1, 3, 2), (0, 1, 16, 2)),
+                                        ((1, 4, 4, 2), (1, 4, 8, 2))):
                 sc.scrooge_set_bucket_config(h, 0, *heavy_cfg)
                 sc.scrooge_set_bucket_config(h, 1, *rest_cfg)
                 assert sc.scrooge_get_bucket_config(h, 0) == heavy_cfg
