@@ -188,7 +188,8 @@ int scrooge_align_batch(scrooge_ctx *ctx, const uint32_t *texts, const int64_t *
  *   smem_rows        DP rows of each pair kept in shared memory (>= 1); rows
  *                    beyond go to a device scratch area
  *   warps_per_block  1 or 2 (the kernel is compiled for blocks of at most 64 threads)
- * scrooge_get_kernel_config reports the current values. */
+ * Defaults: words 1 = (2, 8, 2), 2 = (4, 4, 2), 4 = (8, 8, 2), 0 = (1, 4, 1),
+ * 3 = (8, 6, 2). scrooge_get_kernel_config reports the current values. */
 int scrooge_set_kernel_config(scrooge_ctx *ctx, int32_t words, int32_t lanes_per_pair, int32_t smem_rows,
                               int32_t warps_per_block);
 int scrooge_get_kernel_config(const scrooge_ctx *ctx, int32_t words, int32_t *lanes_per_pair,
@@ -212,7 +213,7 @@ int32_t scrooge_get_heavy_class(const scrooge_ctx *ctx);
  * kind 0 = the banded kernel (lanes_per_pair 1, 2, 4 or 8; 1 = one lane per
  * pair) or kind 1 = the full-width kernel (lanes_per_pair 2, 4 or 8), with its
  * own smem_rows and warps_per_block (1 or 2). Defaults: heavy = full width,
- * 4 lanes, 4 rows, 2 warps; rest = banded, 4 lanes, 8 rows, 2 warps.
+ * 4 lanes, 4 rows, 2 warps; rest = banded, 1 lane, 4 rows, 1 warp.
  * scrooge_autotune with SCROOGE_LEARNED sets them. */
 int scrooge_set_bucket_config(scrooge_ctx *ctx, int32_t bucket, int32_t kind, int32_t lanes_per_pair,
                               int32_t smem_rows, int32_t warps_per_block);

@@ -32,7 +32,7 @@ struct scrooge_ctx {
     std::string err;
     // full-width kernels of 1, 2, 4 words, then the banded kernels of 64- and 128-base windows
     // (autotuned on GB300)
-    scrooge::KernelConfig kcfg[5] = {{2, 8, 2}, {4, 4, 2}, {8, 8, 2}, {4, 8, 2}, {8, 6, 2}};
+    scrooge::KernelConfig kcfg[5] = {{2, 8, 2}, {4, 4, 2}, {8, 8, 2}, {1, 4, 1}, {8, 6, 2}};
     int fail_allocs = 0;  // testing hook: fail the next N device allocations
     int32_t wait_limit = 0;  // polls per bounded device wait (0: the kernel's default bound)
     scrooge::DevBuf spill, status, fallback, spill2, spill3, fallback2, fallback3;
@@ -43,7 +43,7 @@ struct scrooge_ctx {
     // kernel settings of the learned launches per load bucket: 0 = the heavy pairs, 1 = the rest;
     // kind 0 = banded kernel, 1 = full-width kernel (see scrooge_set_bucket_config)
     int32_t bucket_kind[2] = {1, 0};
-    scrooge::KernelConfig bucket_cfg[2] = {{4, 4, 2}, {4, 8, 2}};
+    scrooge::KernelConfig bucket_cfg[2] = {{4, 4, 2}, {1, 4, 1}};
     bool learned_order_on = true;  // SCROOGE_LEARNED orders by the model (else input order)
     cudaStream_t stream2 = nullptr, stream3 = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join3 = nullptr;

@@ -311,6 +311,7 @@ def test_autotune_picks_a_heavy_class(ctx):
     b = synth.concat([synth.uneven_reads(150, seed=31), synth.fixed_error(30, 0.15, length=2000, seed=32)])
     db = sc.DeviceBatch(sc.PackedBatch(b))
     import torch
+    saved = [sc.scrooge_get_bucket_config(h, q) for q in (0, 1)]
     with torch.cuda.stream(s):
         learned.train(h, db, epochs=3, batch=256)
         table = sc.autotune_device(h, db, 64, 24, flags=sc.SCROOGE_LEARNED, repeats=1)
@@ -337,8 +338,8 @@ def test_autotune_picks_a_heavy_class(ctx):
         sc.scrooge_set_learned_order(h, True)
         sc.scrooge_set_heavy_class(h, 16)
         sc.scrooge_set_long_class(h, 16)
-        sc.scrooge_set_bucket_config(h, 0, 1, 4, 4, 2)
-        sc.scrooge_set_bucket_config(h, 1, 0, 4, 8, 2)
+        for q in (0, 1):
+            sc.scrooge_set_bucket_config(h, q, *saved[q])
 
 
 def test_bucket_settings_identical(ctx):
