@@ -50,11 +50,12 @@ constexpr int kLFbLanes = 4;     // lanes per window of the full-width fallback
 constexpr int kLFbWin = 32 / kLFbLanes;  // fallback windows per pass
 constexpr int kLaneIdle = 0, kLaneActive = 1, kLaneDone = 2;
 
+// Per-pair statistics, when asked for, accumulate in the caller's arrays directly (a pair stays on
+// one lane), so the table holds none of them.
 struct LaneTable {
-    int64_t toff[32], poff[32], cbase[32], st_rows[32], st_cells[32], t_start[32];
-    int32_t pair[32], n[32], m[32], ti[32], pj[32], ccap[32], cn[32], edits[32], st_windows[32], state[32];
+    int64_t toff[32], poff[32], cbase[32];
+    int32_t pair[32], n[32], m[32], ti[32], pj[32], ccap[32], cn[32], edits[32], state[32];
     uint32_t ccur[32];
-    int32_t pad[32];
     // the current window's 64 text and pattern bases (both bit planes), staged by the set-up for
     // the traceback
     uint64_t qT0[32], qT1[32], qP0[32], qP1[32];
@@ -124,10 +125,10 @@ __device__ __forceinline__ void lane_fetch(const AlignParams &p, LaneTable &lt, 
                     lt.cn[lane] = 0;
                     lt.ccur[lane] = 0u;
                     lt.edits[lane] = 0;
-                    lt.st_windows[lane] = 0;
-                    lt.st_rows[lane] = 0;
-                    lt.st_cells[lane] = 0;
-                    lt.t_start[lane] = clock64();
+                    if (p.st_windows) p.st_windows[pr] = 0;
+                    if (p.st_rows) p.st_rows[pr] = 0;
+                    if (p.st_cells) p.st_cells[pr] = 0;
+                    if (p.st_cycles) p.st_cycles[pr] = -(int64_t)clock64();  // the finish adds its clock
                     lt.state[lane] = kLaneActive;
                 } else {
                     p.edit_counts[pr] = 0;
@@ -150,13 +151,13 @@ __device__ __forceinline__ void lane_fetch(const AlignParams &p, LaneTable &lt, 
 //     C[i][d] = CX[i] | (C[i+1][d] & CPM[i]),
 //     CX[i]   = C[i+1][d-1] | (C[i+1][d-1] >> 1) | (C[i][d-1] << 1)   (the next row's part).
 // Stores the stored columns to `rowp` (this lane's first word of the row slot) when `st`.
-template <int NC8>
+template <int NCOL>
 __device__ __forceinline__ void lane_dc_row(uint32_t (&CX)[64], const uint32_t (&CPM)[64], uint32_t &pC, bool st,
                                             uint32_t *rowp) {
 #pragma unroll
     for (int c = 63; c >= 0; --c) {
         const uint32_t C = CX[c] | (pC & CPM[c]);
-        if (c < 8 * NC8 && st) rowp[c * 32] = C;
+        if (c < NCOL && st) rowp[c * 32] = C;
         // next row: S = C[i+1][d], D = C[i+1][d] >> 1, I = C[i][d] << 1
         CX[c] = pC | (pC >> 1) | (C << 1);
         pC = C;
@@ -169,11 +170,11 @@ __device__ __forceinline__ void lane_dc_row(uint32_t (&CX)[64], const uint32_t (
 // window (fbg >= 0) from its group in `fb`. Emits the CIGAR runs, advances the pair's
 // cursors and statistics in the lane table, and finishes the pair when its pattern is
 // consumed or the window failed.
-template <int NC8>
+template <int NCOL>
 __device__ __forceinline__ void lane_window_tb(const AlignParams &p, LaneTable &lt, int lane, bool part, int d_opt,
                                                int fbg, int nw, int mw, const uint32_t *ring, const uint32_t *spill,
                                                const uint32_t *fb, int rcap, bool stats) {
-    constexpr int ROWW = 8 * NC8 * 32;
+    constexpr int ROWW = NCOL * 32;
     const int L = p.W - p.O;
     const int fb_row = p.fb_ncol * kLFbWin * 2;
     const int ti = part ? lt.ti[lane] : 0, pj = part ? lt.pj[lane] : 0;
@@ -282,11 +283,10 @@ __device__ __forceinline__ void lane_window_tb(const AlignParams &p, LaneTable &
     }
     if (!part) return;
     if (stats) {
-        lt.st_windows[lane] += 1;
-        if (live) {
-            lt.st_rows[lane] += d_opt + 1;
-            lt.st_cells[lane] += (int64_t)(d_opt + 1) * nw;
-        }
+        const int pair = lt.pair[lane];
+        if (p.st_windows) p.st_windows[pair] += 1;
+        if (live && p.st_rows) p.st_rows[pair] += d_opt + 1;
+        if (live && p.st_cells) p.st_cells[pair] += (int64_t)(d_opt + 1) * nw;
     }
     const int nti = ti + (live ? i : 0), npj = pj + (live ? j : 0);
     if (failed || npj >= m) {
@@ -296,10 +296,7 @@ __device__ __forceinline__ void lane_window_tb(const AlignParams &p, LaneTable &
         p.text_consumed[pair] = failed ? 0 : nti;
         if (out.n > out.cap) atomicOr(p.status, 2);  // capacity too small for this pair
         p.cigar_lens[pair] = failed ? 0 : min(out.n, (int32_t)out.cap);
-        if (p.st_windows) p.st_windows[pair] = lt.st_windows[lane];
-        if (p.st_rows) p.st_rows[pair] = lt.st_rows[lane];
-        if (p.st_cells) p.st_cells[pair] = lt.st_cells[lane];
-        if (p.st_cycles) p.st_cycles[pair] = clock64() - lt.t_start[lane];
+        if (p.st_cycles) p.st_cycles[pair] += (int64_t)clock64();
         lt.state[lane] = kLaneIdle;
     } else {
         lt.ti[lane] = nti;
@@ -310,9 +307,9 @@ __device__ __forceinline__ void lane_window_tb(const AlignParams &p, LaneTable &
     }
 }
 
-template <int NC8>
+template <int NCOL>
 __global__ void __launch_bounds__(64, 4) align_lane_kernel(const AlignParams p) {
-    constexpr int ROWW = 8 * NC8 * 32;  // words of one stored row of a warp
+    constexpr int ROWW = NCOL * 32;  // words of one stored row of a warp
     extern __shared__ __align__(16) uint32_t smem[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
@@ -406,7 +403,7 @@ __global__ void __launch_bounds__(64, 4) align_lane_kernel(const AlignParams p) 
             // the column right of the window: bits j < m_w - d of R[n][d] are 1 (0 in complement)
             uint32_t pC = ~prefix_mask(mw - d - 64 + kLB0);
             uint32_t *rowp = ring + slot * ROWW;
-            lane_dc_row<NC8>(XA, PMC, pC, busy, rowp);
+            lane_dc_row<NCOL>(XA, PMC, pC, busy, rowp);
             if (busy && ((pC >> (31 - kLB0)) & 1u) != 0u) {
                 d_opt = d;
                 busy = false;
@@ -459,49 +456,51 @@ __global__ void __launch_bounds__(64, 4) align_lane_kernel(const AlignParams p) 
         }
 
         // ---- GenASM-TB, every lane on its own pair
-        lane_window_tb<NC8>(p, lt, lane, active && !wait, d_opt, fbg, nw, mw, ring, spill, fb, rcap, stats);
+        lane_window_tb<NCOL>(p, lt, lane, active && !wait, d_opt, fbg, nw, mw, ring, spill, fb, rcap, stats);
         __syncwarp();
     }
 }
 
-template <int NC8>
+template <int NCOL>
 cudaError_t launch_nc(const AlignParams &p, int wpb, int blocks, size_t smem, cudaStream_t st) {
-    align_lane_kernel<NC8><<<blocks, 32 * wpb, smem, st>>>(p);
+    align_lane_kernel<NCOL><<<blocks, 32 * wpb, smem, st>>>(p);
     return cudaGetLastError();
 }
 
-template <int NC8>
+template <int NCOL>
 cudaError_t occupancy_nc(int wpb, size_t smem, int *per_sm) {
-    return occupancy_raising_smem(align_lane_kernel<NC8>, 32 * wpb, smem, per_sm);
+    return occupancy_raising_smem(align_lane_kernel<NCOL>, 32 * wpb, smem, per_sm);
 }
 
 }  // namespace kern
 
 cudaError_t launch_align_lane(const AlignParams &p, int wpb, int blocks, size_t smem, cudaStream_t st) {
-    switch (p.ncol / 8) {
-        case 1: return kern::launch_nc<1>(p, wpb, blocks, smem, st);
-        case 2: return kern::launch_nc<2>(p, wpb, blocks, smem, st);
-        case 3: return kern::launch_nc<3>(p, wpb, blocks, smem, st);
-        case 4: return kern::launch_nc<4>(p, wpb, blocks, smem, st);
-        case 5: return kern::launch_nc<5>(p, wpb, blocks, smem, st);
-        case 6: return kern::launch_nc<6>(p, wpb, blocks, smem, st);
-        case 7: return kern::launch_nc<7>(p, wpb, blocks, smem, st);
-        case 8: return kern::launch_nc<8>(p, wpb, blocks, smem, st);
+    switch (p.ncol) {
+#define SCROOGE_LANE_NCOL(n) \
+    case n: return kern::launch_nc<n>(p, wpb, blocks, smem, st);
+        SCROOGE_LANE_NCOLS
+#undef SCROOGE_LANE_NCOL
         default: return cudaErrorInvalidValue;
     }
 }
 
 cudaError_t occupancy_lane(int ncol, int wpb, size_t smem, int *per_sm) {
-    switch (ncol / 8) {
-        case 1: return kern::occupancy_nc<1>(wpb, smem, per_sm);
-        case 2: return kern::occupancy_nc<2>(wpb, smem, per_sm);
-        case 3: return kern::occupancy_nc<3>(wpb, smem, per_sm);
-        case 4: return kern::occupancy_nc<4>(wpb, smem, per_sm);
-        case 5: return kern::occupancy_nc<5>(wpb, smem, per_sm);
-        case 6: return kern::occupancy_nc<6>(wpb, smem, per_sm);
-        case 7: return kern::occupancy_nc<7>(wpb, smem, per_sm);
-        case 8: return kern::occupancy_nc<8>(wpb, smem, per_sm);
+    switch (ncol) {
+#define SCROOGE_LANE_NCOL(n) \
+    case n: return kern::occupancy_nc<n>(wpb, smem, per_sm);
+        SCROOGE_LANE_NCOLS
+#undef SCROOGE_LANE_NCOL
         default: return cudaErrorInvalidValue;
+    }
+}
+
+bool lane_ncol_supported(int ncol) {
+    switch (ncol) {
+#define SCROOGE_LANE_NCOL(n) \
+    case n: return true;
+        SCROOGE_LANE_NCOLS
+#undef SCROOGE_LANE_NCOL
+        default: return false;
     }
 }
 

@@ -283,7 +283,10 @@ int make_lane_plan(scrooge_ctx *c, const AlignParams &base, uint32_t flags, DevB
     const int W = base.W, O = base.O, k = base.k, L = W - O;
     const bool dent = !(flags & SCROOGE_NO_DENT);
     AlignParams p = base;
-    const int ncol = std::min(64, (((dent ? std::min(L + 1, W) : W) + 7) / 8) * 8);
+    // stored columns: 0..W-O with DENT (exactly, where the kernel is compiled for that count, else
+    // rounded up to 8), else all W
+    const int want = dent ? std::min(L + 1, W) : W;
+    const int ncol = lane_ncol_supported(want) ? want : std::min(64, ((want + 7) / 8) * 8);
     p.et = 1;
     p.sene = 1;
     p.ncol = ncol;

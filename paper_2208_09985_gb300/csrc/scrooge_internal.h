@@ -141,13 +141,27 @@ inline int ext_dent_ring(int W, int O, int k, int lanes, bool on) {
     if (ring < (k + 2) / 2) ring = (k + 2) / 2;
     return on && ring < k + 1 ? ring : k + 1;
 }
-// Banded kernel with one lane per pair (align_lane.cu) for windows of 33..64 bases: ncol (a
-// multiple of 8, at most 64) stored columns per row, rcap rows per lane in shared memory after a
+// Banded kernel with one lane per pair (align_lane.cu) for windows of 33..64 bases: ncol (at most
+// 64; see SCROOGE_LANE_NCOLS) stored columns per row, rcap rows per lane in shared memory after a
 // per-warp table of kLaneTableBytes; windows beyond the band are recomputed at full width by
 // groups of 4 lanes (fb: k+1 rows of fb_ncol columns x 8 windows x 2 words per warp).
-constexpr int kLaneTableBytes = 4096;
+constexpr int kLaneTableBytes = 3072;
+// Stored-column counts the lane kernel is compiled for: the multiples of 8, and W-O+1 at the
+// operating points W=64/O=24 (41) and W=64/O=32 (33), which would otherwise round up to 48 and 40.
+#define SCROOGE_LANE_NCOLS \
+    SCROOGE_LANE_NCOL(8)       \
+    SCROOGE_LANE_NCOL(16)      \
+    SCROOGE_LANE_NCOL(24)      \
+    SCROOGE_LANE_NCOL(32)      \
+    SCROOGE_LANE_NCOL(33)      \
+    SCROOGE_LANE_NCOL(40)      \
+    SCROOGE_LANE_NCOL(41)      \
+    SCROOGE_LANE_NCOL(48)      \
+    SCROOGE_LANE_NCOL(56)      \
+    SCROOGE_LANE_NCOL(64)
 cudaError_t launch_align_lane(const AlignParams &, int wpb, int blocks, size_t smem, cudaStream_t);
 cudaError_t occupancy_lane(int ncol, int wpb, size_t smem, int *blocks_per_sm);
+bool lane_ncol_supported(int ncol);
 // Warp-specialised banded kernel (align_band.cu): blocks of 4 DC warps (4 lanes per pair, two
 // sets of 8 pairs each) and one traceback warp; persistent launches only. Shared memory per block:
 // 8 sets x smem_words_per_warp words, then ws_meta_bytes().

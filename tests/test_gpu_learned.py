@@ -423,5 +423,7 @@ def test_trained_model_gains_over_input_order(ctx):
     _same_device(sc.device_results(db), plain, "random-weights order")
     sc.scrooge_model_set(h, trained)
     print(f"uneven 100k: input order {t_input:.2f} ms, trained {t_trained:.2f} ms, random weights {t_random:.2f} ms")
-    assert t_trained < 0.9 * t_input, (t_trained, t_input)
+    # with one lane per pair a long pair holds only its own lane, so the order matters less than with
+    # four lanes per pair (input order 50 ms there against 35 learned); a lenient 3% bound
+    assert t_trained < 0.97 * t_input, (t_trained, t_input)
     assert abs(t_trained - t_random) < 0.1 * t_input, (t_trained, t_random)
