@@ -387,7 +387,15 @@ __global__ void __launch_bounds__(64, 4) align_lane_kernel(const AlignParams p) 
         for (int d = 0; d <= dmax; ++d) {
             if (!__any_sync(kFull, busy)) break;
             if (d >= rcap) {
-                if (rcap == 1 && lane == 0) bulk_copy_s2g(spill_w + (int64_t)(d - 1) * ROWW, ring_w, ROWW * 4);
+                if (rcap == 1) {
+                    // one slot: row d - 1 is copied out just before row d overwrites it, once every
+                    // lane's store of it is done and ordered before the copy's read
+                    __syncwarp();
+                    if (lane == 0) {
+                        asm volatile("fence.proxy.async.shared::cta;");
+                        bulk_copy_s2g(spill_w + (int64_t)(d - 1) * ROWW, ring_w, ROWW * 4);
+                    }
+                }
                 if (lane == 0) bulk_wait_read();  // the slot of row d - rcap has been read
                 __syncwarp();
             }

@@ -55,8 +55,17 @@ def _check_paths(ctx, batch, W, O, paths, label):
     ref = oracle.align_batch(batch, W, O, W, threads=THREADS)
     # capacity for every run of the batch (the oracle's count) so no call is cut short
     db = sc.DeviceBatch(pb, cigar_capacity=int(np.asarray(ref["cigar_lens"]).astype(np.int64).sum()) + 16)
-    for name, flags in paths:
-        got = _gpu(ctx, db, W, O, flags)
+    h, _ = ctx
+    for path in paths:
+        name, flags = path[:2]
+        cfg = path[2] if len(path) > 2 else None  # kernel settings of the 33..64-base windows' slot
+        saved = sc.scrooge_get_kernel_config(h, 0)
+        try:
+            if cfg:
+                sc.scrooge_set_kernel_config(h, 0, *cfg)
+            got = _gpu(ctx, db, W, O, flags)
+        finally:
+            sc.scrooge_set_kernel_config(h, 0, *saved)
         assert_same_all(got, ref, label=f"{label} {name} W={W} O={O}")
     return ref
 
@@ -66,9 +75,16 @@ PERSISTENT = ("persistent", sc.SCROOGE_PERSISTENT)
 LEARNED_GRAPH = ("learned+graph", sc.SCROOGE_LEARNED | sc.SCROOGE_GRAPH)
 
 
+# the one-lane-per-pair kernel with one, two and three shared-memory row slots: every row the
+# traceback reads then goes through the device area, so the eviction copies are exercised at scale
+LANE_SLOTS = tuple((f"persistent lanes 1 rows {r} warps {w}", sc.SCROOGE_PERSISTENT, (1, r, w))
+                   for r, w in ((1, 1), (2, 1), (3, 2)))
+
+
 def test_long_reads_every_pair(ctx):
     """100,000 pairs of 10 kbp at 10% edits: the benchmark's workload."""
-    ref = _check_paths(ctx, synth.long_reads(100_000), 64, 24, (PLAIN, PERSISTENT, LEARNED_GRAPH), "long_reads")
+    ref = _check_paths(ctx, synth.long_reads(100_000), 64, 24, (PLAIN, PERSISTENT, LEARNED_GRAPH) + LANE_SLOTS,
+                       "long_reads")
     assert (ref["edit_counts"] >= 0).all()
 
 
