@@ -182,7 +182,8 @@ def main(argv=None):
                                                                                  rows_per_window),
                                "smem_bytes_per_pair": shape["table_bytes_per_warp"] / pps,
                                "scratch_bytes_per_pair": shape["scratch_bytes_per_warp"] / pps,
-                               "kernel": "band" if shape["kernel"] == 0 else f"full{shape['kernel']}",
+                               "kernel": (("lane" if shape["lanes"] == 1 else "band") if shape["kernel"] == 0
+                                          else f"full{shape['kernel']}"),
                                "lanes": shape["lanes"], "smem_rows": shape["smem_rows"],
                                "row_slots": shape["row_slots"],
                                "mean_rows_per_window": mean_rows,
