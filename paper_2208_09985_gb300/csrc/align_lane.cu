@@ -173,10 +173,10 @@ __device__ __forceinline__ void lane_dc_row(uint32_t (&CX)[64], const uint32_t (
 template <int NCOL>
 __device__ __forceinline__ void lane_window_tb(const AlignParams &p, LaneTable &lt, int lane, bool part, int d_opt,
                                                int fbg, int nw, int mw, const uint32_t *ring, const uint32_t *spill,
-                                               const uint32_t *fb, int rcap, bool stats) {
+                                               const uint32_t *fb, int fbw, int rcap, bool stats) {
     constexpr int ROWW = NCOL * 32;
     const int L = p.W - p.O;
-    const int fb_row = p.fb_ncol * kLFbWin * 2;
+    const int fb_row = p.fb_ncol * fbw * 2;
     const int ti = part ? lt.ti[lane] : 0, pj = part ? lt.pj[lane] : 0;
     const int m = part ? lt.m[lane] : 0;
     // the window's 64 text and pattern bases in 64-bit registers (a match run never
@@ -251,8 +251,8 @@ __device__ __forceinline__ void lane_window_tb(const AlignParams &p, LaneTable &
                     t1 = (uint32_t)((q1 << kk) >> 62);
                     r0b = (uint32_t)((((uint64_t)v0 << 32) << (kk + 1)) >> 63);
                 } else {
-                    const uint32_t *fp = fb + (int64_t)r * fb_row + (i * kLFbWin + fbg) * 2;
-                    t1 = ld1 ? entry_bits2<2>(fp + kLFbWin * 2, j) : 0u;
+                    const uint32_t *fp = fb + (int64_t)r * fb_row + (i * fbw + fbg) * 2;
+                    t1 = ld1 ? entry_bits2<2>(fp + fbw * 2, j) : 0u;
                     r0b = tx ? (entry_bits2<2>(fp, j) & 1u) : 0u;
                 }
                 const uint32_t r1j = ld1 ? (t1 >> 1) : (j < lim_r ? 1u : 0u);
@@ -305,6 +305,38 @@ __device__ __forceinline__ void lane_window_tb(const AlignParams &p, LaneTable &
         lt.ccur[lane] = out.cur;
         lt.edits[lane] = out.edits;
     }
+}
+
+// Full-width DC (Algorithm 1 on two words) of the windows of the lanes in `take` (at most 32 / FG,
+// lowest lanes first), each by a group of FG lanes; group g's rows go to window slot g of the
+// fallback rows ([row][column][32 / FG slots][2 words]). Returns, on each lane of `take`, its
+// window's edit distance (-1: none up to k).
+template <int FG>
+__device__ __forceinline__ int lane_fallback(const AlignParams &p, uint32_t take, int lane, int ti, int pj, int nw,
+                                             int mw, int64_t tblk, int64_t pblk, const uint2 *tseq,
+                                             const uint2 *pseq, uint32_t *fb) {
+    constexpr int slots = 32 / FG;
+    constexpr uint32_t tb_lanes = FG == 8 ? 0x80808080u : 0x88888888u;  // lane FG-1 of every group
+    static_assert(FG == 4 || FG == 8, "fallback groups of 4 or 8 lanes");
+    const int g = lane / FG, l = lane % FG;
+    uint32_t x = take;
+    for (int t = 0; t < g && x; ++t) x &= x - 1u;
+    const int src = x ? __ffs(x) - 1 : -1;  // lane whose window group g computes
+    const int sl = src >= 0 ? src : lane;
+    const int f_ti = __shfl_sync(kFull, ti, sl), f_pj = __shfl_sync(kFull, pj, sl);
+    const int f_nw = __shfl_sync(kFull, nw, sl), f_mw = __shfl_sync(kFull, mw, sl);
+    const int64_t f_tblk = shfl64(tblk, sl), f_pblk = shfl64(pblk, sl);
+    const uint2 *f_tseq = reinterpret_cast<const uint2 *>(shfl64((int64_t)(uintptr_t)tseq, sl));
+    const uint2 *f_pseq = reinterpret_cast<const uint2 *>(shfl64((int64_t)(uintptr_t)pseq, sl));
+    const uint32_t full_mask = __ballot_sync(kFull, l == FG - 1 && src >= 0);
+    const int colbase = (FG - 1 - l) * (64 / FG);
+    int dfb = -1;
+    full_width_dc<FG, 2>(f_pseq, src >= 0 ? f_pblk : 0, f_pj, f_tseq, src >= 0 ? f_tblk : 0, f_ti, f_nw, f_mw, p.k, l,
+                         g * FG + FG - 1, tb_lanes, full_mask, colbase < p.fb_ncol,
+                         fb + ((int64_t)colbase * slots + g) * 2, p.fb_ncol * slots * 2, dfb);
+    const bool mine = (take >> lane) & 1u;
+    const int myg = __popc(take & ((1u << lane) - 1u));
+    return __shfl_sync(kFull, dfb, (mine ? myg : 0) * FG + FG - 1);
 }
 
 template <int NCOL>
@@ -424,47 +456,32 @@ __global__ void __launch_bounds__(64, 4) align_lane_kernel(const AlignParams p) 
         }
         __syncwarp();
 
-        // ---- windows beyond the band: full-width DC by groups of kLFbLanes lanes, up to kLFbWin of
-        // them per round; a window beyond that waits (keeps its cursors) and is recomputed next round
+        // ---- windows beyond the band: full-width DC by groups of lanes, 8 lanes per window when at
+        // most 4 are pending (the usual case: one), else 4 lanes per window for up to 8 of them; a
+        // window beyond that waits (keeps its cursors) and is recomputed next round
         const uint32_t pend = __ballot_sync(kFull, active && d_opt < 0 && k >= kLBandRows);
-        int fbg = -1;
+        int fbg = -1, fbw = kLFbWin;
         bool wait = false;
         if (pend) {
+            const bool wide = __popc(pend) <= 32 / 8;
+            fbw = wide ? 32 / 8 : kLFbWin;
             uint32_t take = 0, rest = pend;
-            for (int t = 0; t < kLFbWin && rest; ++t) {
+            for (int t = 0; t < fbw && rest; ++t) {
                 const uint32_t b = rest & (0u - rest);
                 take |= b;
                 rest ^= b;
             }
-            const int g = lane / kLFbLanes, l = lane % kLFbLanes;
-            uint32_t x = take;
-            for (int t = 0; t < g && x; ++t) x &= x - 1u;
-            const int src = x ? __ffs(x) - 1 : -1;  // lane whose window group g computes
-            const int sl = src >= 0 ? src : lane;
-            const int f_ti = __shfl_sync(kFull, ti, sl), f_pj = __shfl_sync(kFull, pj, sl);
-            const int f_nw = __shfl_sync(kFull, nw, sl), f_mw = __shfl_sync(kFull, mw, sl);
-            const int64_t f_tblk = shfl64(tblk, sl), f_pblk = shfl64(pblk, sl);
-            const uint2 *f_tseq = reinterpret_cast<const uint2 *>(shfl64((int64_t)(uintptr_t)tseq, sl));
-            const uint2 *f_pseq = reinterpret_cast<const uint2 *>(shfl64((int64_t)(uintptr_t)pseq, sl));
-            const uint32_t full_mask = __ballot_sync(kFull, l == kLFbLanes - 1 && src >= 0);
-            const int colbase = (kLFbLanes - 1 - l) * (64 / kLFbLanes);
-            int dfb = -1;
-            full_width_dc<kLFbLanes, 2>(f_pseq, src >= 0 ? f_pblk : 0, f_pj, f_tseq, src >= 0 ? f_tblk : 0, f_ti,
-                                        f_nw, f_mw, k, l, g * kLFbLanes + kLFbLanes - 1, 0x88888888u, full_mask,
-                                        colbase < p.fb_ncol, fb + ((int64_t)colbase * kLFbWin + g) * 2,
-                                        p.fb_ncol * kLFbWin * 2, dfb);
-            const bool mine = (take >> lane) & 1u;
-            const int myg = __popc(take & ((1u << lane) - 1u));
-            const int got = __shfl_sync(kFull, dfb, (mine ? myg : 0) * kLFbLanes + kLFbLanes - 1);
-            if (mine) {
+            const int got = wide ? lane_fallback<8>(p, take, lane, ti, pj, nw, mw, tblk, pblk, tseq, pseq, fb)
+                                 : lane_fallback<kLFbLanes>(p, take, lane, ti, pj, nw, mw, tblk, pblk, tseq, pseq, fb);
+            if ((take >> lane) & 1u) {
                 d_opt = got;
-                fbg = myg;
+                fbg = __popc(take & ((1u << lane) - 1u));
             }
             wait = ((rest >> lane) & 1u) != 0u;
         }
 
         // ---- GenASM-TB, every lane on its own pair
-        lane_window_tb<NCOL>(p, lt, lane, active && !wait, d_opt, fbg, nw, mw, ring, spill, fb, rcap, stats);
+        lane_window_tb<NCOL>(p, lt, lane, active && !wait, d_opt, fbg, nw, mw, ring, spill, fb, fbw, rcap, stats);
         __syncwarp();
     }
 }
