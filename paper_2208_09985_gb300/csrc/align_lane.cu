@@ -316,8 +316,9 @@ __device__ __forceinline__ int lane_fallback(const AlignParams &p, uint32_t take
                                              int mw, int64_t tblk, int64_t pblk, const uint2 *tseq,
                                              const uint2 *pseq, uint32_t *fb) {
     constexpr int slots = 32 / FG;
-    constexpr uint32_t tb_lanes = FG == 8 ? 0x80808080u : 0x88888888u;  // lane FG-1 of every group
-    static_assert(FG == 4 || FG == 8, "fallback groups of 4 or 8 lanes");
+    // lane FG-1 of every group
+    constexpr uint32_t tb_lanes = FG == 16 ? 0x80008000u : (FG == 8 ? 0x80808080u : 0x88888888u);
+    static_assert(FG == 4 || FG == 8 || FG == 16, "fallback groups of 4, 8 or 16 lanes");
     const int g = lane / FG, l = lane % FG;
     uint32_t x = take;
     for (int t = 0; t < g && x; ++t) x &= x - 1u;
@@ -456,23 +457,25 @@ __global__ void __launch_bounds__(64, 4) align_lane_kernel(const AlignParams p) 
         }
         __syncwarp();
 
-        // ---- windows beyond the band: full-width DC by groups of lanes, 8 lanes per window when at
-        // most 4 are pending (the usual case: one), else 4 lanes per window for up to 8 of them; a
-        // window beyond that waits (keeps its cursors) and is recomputed next round
+        // ---- windows beyond the band: full-width DC by groups of lanes, 16 lanes per window when at
+        // most 2 are pending (the usual case: one), 8 when at most 4, else 4 lanes per window for up
+        // to 8 of them; a window beyond that waits (keeps its cursors) and is recomputed next round
         const uint32_t pend = __ballot_sync(kFull, active && d_opt < 0 && k >= kLBandRows);
         int fbg = -1, fbw = kLFbWin;
         bool wait = false;
         if (pend) {
-            const bool wide = __popc(pend) <= 32 / 8;
-            fbw = wide ? 32 / 8 : kLFbWin;
+            const int npend = __popc(pend);
+            fbw = npend <= 32 / 16 ? 32 / 16 : (npend <= 32 / 8 ? 32 / 8 : kLFbWin);
             uint32_t take = 0, rest = pend;
             for (int t = 0; t < fbw && rest; ++t) {
                 const uint32_t b = rest & (0u - rest);
                 take |= b;
                 rest ^= b;
             }
-            const int got = wide ? lane_fallback<8>(p, take, lane, ti, pj, nw, mw, tblk, pblk, tseq, pseq, fb)
-                                 : lane_fallback<kLFbLanes>(p, take, lane, ti, pj, nw, mw, tblk, pblk, tseq, pseq, fb);
+            const int got =
+                fbw == 32 / 16 ? lane_fallback<16>(p, take, lane, ti, pj, nw, mw, tblk, pblk, tseq, pseq, fb)
+                : fbw == 32 / 8 ? lane_fallback<8>(p, take, lane, ti, pj, nw, mw, tblk, pblk, tseq, pseq, fb)
+                                : lane_fallback<kLFbLanes>(p, take, lane, ti, pj, nw, mw, tblk, pblk, tseq, pseq, fb);
             if ((take >> lane) & 1u) {
                 d_opt = got;
                 fbg = __popc(take & ((1u << lane) - 1u));
