@@ -106,6 +106,8 @@ def load():
                 "scrooge_get_bucket_config": ([P, i32, P, P, P, P], ctypes.c_int),
                 "scrooge_set_learned_order": ([P, i32], ctypes.c_int),
                 "scrooge_get_learned_order": ([P], i32),
+                "scrooge_set_host_overlap": ([P, i32], ctypes.c_int),
+                "scrooge_get_host_overlap": ([P], i32),
             }
             for name, (args, res) in sig.items():
                 f = getattr(lib, name)
@@ -386,6 +388,16 @@ def scrooge_set_learned_order(ctx, on: bool):
 
 def scrooge_get_learned_order(ctx) -> bool:
     return load().scrooge_get_learned_order(ctx) == 1
+
+
+def scrooge_set_host_overlap(ctx, on: bool):
+    """Host-pointer persistent calls of 8,192 pairs or more in two halves, copies under the kernels (True, the
+    default), or as one launch (False)."""
+    return _check(ctx, load().scrooge_set_host_overlap(ctx, 1 if on else 0))
+
+
+def scrooge_get_host_overlap(ctx) -> bool:
+    return load().scrooge_get_host_overlap(ctx) == 1
 
 
 def scrooge_set_wait_limit(ctx, polls: int = 0):

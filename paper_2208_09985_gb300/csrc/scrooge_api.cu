@@ -67,13 +67,17 @@ int scrooge_destroy(scrooge_ctx *c) {
                      &c->scr_runs,  &c->scr_off, &c->scr_len, &c->scr_cap,  &c->scan_tmp, &c->queue,
                      &c->model,     &c->grad,    &c->adam_m1, &c->adam_m2,  &c->loss,     &c->l_feat,
                      &c->l_pred,    &c->l_key,   &c->l_order, &c->l_tmp,    &c->t_rows,   &c->fallback, &c->spill2,
-                     &c->spill3,    &c->fallback2, &c->fallback3};
+                     &c->spill3,    &c->fallback2, &c->fallback3, &c->split_bounds, &c->out_cig2};
     if (c->graph) cudaGraphExecDestroy(c->graph);
     if (c->stream2) cudaStreamDestroy(c->stream2);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->ev_join3) cudaEventDestroy(c->ev_join3);
     if (c->stream3) cudaStreamDestroy(c->stream3);
+    if (c->split_copy) cudaStreamDestroy(c->split_copy);
+    if (c->split_b) cudaStreamDestroy(c->split_b);
+    for (cudaEvent_t ev : c->split_ev)
+        if (ev) cudaEventDestroy(ev);
     for (DevBuf *b : all) release(*b);
     delete c;
     return SCROOGE_OK;
@@ -92,6 +96,14 @@ int scrooge_set_wait_limit(scrooge_ctx *c, int32_t polls) {
     c->wait_limit = polls;
     return SCROOGE_OK;
 }
+
+int scrooge_set_host_overlap(scrooge_ctx *c, int32_t on) {
+    if (!c) return SCROOGE_E_INVAL;
+    c->host_split = on != 0;
+    return SCROOGE_OK;
+}
+
+int32_t scrooge_get_host_overlap(const scrooge_ctx *c) { return c ? (c->host_split ? 1 : 0) : -1; }
 
 int scrooge_debug_fail_next_allocs(scrooge_ctx *c, int32_t count) {
     if (!c || count < 0) return SCROOGE_E_INVAL;
@@ -464,6 +476,205 @@ cudaError_t launch_plan(const LaunchPlan &lp, cudaStream_t st) {
     }
 }
 
+constexpr int32_t kHostSplitMinPairs = 8192;
+
+// Host-pointer persistent calls on large batches, in two halves of the pair range [0, h) and
+// [h, n): the second half's inputs are copied while the first half's kernel runs, and the first
+// half's outputs while the second half's kernel runs. One kernel launch per half over its range of
+// the persistent queue, each with its own row scratch, so that the second launch's blocks take the
+// SMs the first one's blocks free; the dense CIGAR of each half is gathered and copied on its own.
+// Same results as the one-launch path (the kernels align each pair independently).
+int align_host_split(scrooge_ctx *c, const uint32_t *texts, const int64_t *text_offsets, const int32_t *text_lengths,
+                     const uint32_t *patterns, const int64_t *pattern_offsets, const int32_t *pattern_lengths,
+                     int32_t n_pairs, int32_t W, int32_t O, int32_t k, uint32_t flags, int32_t *edit_counts,
+                     int32_t *text_consumed, uint32_t *cigar, int64_t cigar_capacity, int64_t *cigar_offsets) {
+    const int32_t h = n_pairs / 2;
+    const size_t np = (size_t)n_pairs;
+    cudaError_t e;
+    int rc;
+    // layout check; the words of both sequence arrays that the first half needs (a prefix)
+    int64_t text_words = 0, pat_words = 0, text_words_a = 0, pat_words_a = 0, scratch_runs = 0;
+    for (int32_t q = 0; q < n_pairs; ++q) {
+        const int64_t to = text_offsets[q], po = pattern_offsets[q];
+        const int32_t tl = text_lengths[q], pl = pattern_lengths[q];
+        if (to < 0 || po < 0 || (to & 63) || (po & 63) || tl < 0 || pl < 0)
+            return fail(c, SCROOGE_E_INVAL, "pair %d: offsets must be >= 0 multiples of 64, lengths >= 0", q);
+        text_words = std::max(text_words, to / 16 + scrooge_packed_words(tl));
+        pat_words = std::max(pat_words, po / 16 + scrooge_packed_words(pl));
+        if (q == h - 1) {
+            text_words_a = text_words;
+            pat_words_a = pat_words;
+        }
+        scratch_runs += (int64_t)tl + pl + 1;
+    }
+    if ((rc = ensure(c, c->scr_off, (np + 1) * 8, "CIGAR scratch offsets")) ||
+        (rc = ensure(c, c->scr_len, np * 4, "CIGAR run counts")) ||
+        (rc = ensure(c, c->scan_tmp, (size_t)scan_temp_words((int64_t)np + 1) * 8, "scan scratch")) ||
+        (rc = ensure(c, c->in_text, text_words * 4, "texts")) || (rc = ensure(c, c->in_pat, pat_words * 4, "patterns")) ||
+        (rc = ensure(c, c->in_toff, np * 8, "text offsets")) || (rc = ensure(c, c->in_tlen, np * 4, "text lengths")) ||
+        (rc = ensure(c, c->in_poff, np * 8, "pattern offsets")) ||
+        (rc = ensure(c, c->in_plen, np * 4, "pattern lengths")) || (rc = ensure(c, c->out_ec, np * 4, "edit counts")) ||
+        (rc = ensure(c, c->out_tc, np * 4, "text consumed")) || (rc = ensure(c, c->out_off, (np + 1) * 8, "cigar offsets")) ||
+        (rc = ensure(c, c->scr_cap, (np + 1) * 8, "CIGAR capacities")) ||
+        (rc = ensure(c, c->scr_runs, (size_t)std::max<int64_t>(scratch_runs, 1) * 4, "CIGAR run scratch")) ||
+        (rc = ensure(c, c->status, 64, "status")) || (rc = ensure(c, c->queue, 256, "work queues")) ||
+        (rc = ensure(c, c->split_bounds, 4 * 8, "range bounds")))
+        return rc;
+    if (!c->split_copy) {
+        if ((e = cudaStreamCreateWithFlags(&c->split_copy, cudaStreamNonBlocking)) != cudaSuccess ||
+            (e = cudaStreamCreateWithFlags(&c->split_b, cudaStreamNonBlocking)) != cudaSuccess)
+            return cuda_fail(c, e, "split streams");
+        for (cudaEvent_t &ev : c->split_ev)
+            if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
+                return cuda_fail(c, e, "split events");
+    }
+    cudaStream_t st = c->stream, cs = c->split_copy, sb = c->split_b;
+    cudaEvent_t ev_in_a = c->split_ev[0], ev_in_b = c->split_ev[1], ev_ready = c->split_ev[2],
+                ev_b = c->split_ev[3], ev_gather_a = c->split_ev[4], ev_start = c->split_ev[5];
+    AlignParams p;
+    memset(&p, 0, sizeof p);
+    p.n_pairs = n_pairs;
+    p.W = W;
+    p.O = O;
+    p.k = k;
+    p.texts = (const uint32_t *)c->in_text.p;
+    p.patterns = (const uint32_t *)c->in_pat.p;
+    p.text_off = (const int64_t *)c->in_toff.p;
+    p.text_len = (const int32_t *)c->in_tlen.p;
+    p.pat_off = (const int64_t *)c->in_poff.p;
+    p.pat_len = (const int32_t *)c->in_plen.p;
+    p.edit_counts = (int32_t *)c->out_ec.p;
+    p.text_consumed = (int32_t *)c->out_tc.p;
+    p.cigar = (uint32_t *)c->scr_runs.p;
+    p.cigar_off = (const int64_t *)c->scr_off.p;
+    p.cigar_lens = (int32_t *)c->scr_len.p;
+    p.st_windows = c->st_windows;
+    p.st_rows = c->st_rows;
+    p.st_cells = c->st_cells;
+    p.st_cycles = c->st_cycles;
+    const bool band = use_band(W, flags);
+    LaunchPlan pa, pb;
+    if ((rc = make_plan(c, p, band, flags, c->spill, c->fallback, 0, pa)) ||
+        (rc = make_plan(c, p, band, flags, c->spill2, c->fallback3, 0, pb)))
+        return rc;
+    const int64_t *bounds = (const int64_t *)c->split_bounds.p;  // {0, h, h, n}
+    pa.p.range_lo = bounds;
+    pa.p.range_hi = bounds + 1;
+    pb.p.range_lo = bounds + 2;
+    pb.p.range_hi = bounds + 3;
+    for (LaunchPlan *lp : {&pa, &pb}) {
+        lp->p.status = (int32_t *)c->status.p;
+        lp->p.wait_limit = c->wait_limit;
+        lp->p.order = nullptr;
+        lp->p.queue = (int32_t *)c->queue.p + (lp == &pb ? 16 : 0);
+    }
+    {
+        const TableShape &ts = pa.ts;
+        const int64_t shape[13] = {pa.band ? 0 : pa.words, pa.G, pa.p.rcap, pa.wpb, (int64_t)pa.smem, pa.blocks,
+                                   pa.p.ncol, ts.swp, pa.p.table_words_per_warp * 4LL, pa.p.spill_words_per_pair * 4,
+                                   pa.p.fb_words_per_warp * 4, 32 / pa.G, pa.p.ring};
+        memcpy(c->last_shape, shape, sizeof shape);
+    }
+    // kernels: two alignment launches, and per half a scan and a gather
+    c->last_kernels = 2 + scan_kernel_count(h) + scan_kernel_count(n_pairs - h) + 2;  // alignment, offsets, gathers
+    const int64_t bounds_h[4] = {0, h, h, n_pairs};
+    // inputs: the small per-pair arrays and the first half's sequence words, then the rest
+    if ((e = cudaEventRecord(ev_start, st)) != cudaSuccess || (e = cudaStreamWaitEvent(cs, ev_start, 0)) != cudaSuccess)
+        return cuda_fail(c, e, "stream fork");
+    struct Copy {
+        void *d;
+        const void *h;
+        size_t b;
+    };
+    const Copy in_a[] = {{c->in_toff.p, text_offsets, np * 8},
+                         {c->in_tlen.p, text_lengths, np * 4},
+                         {c->in_poff.p, pattern_offsets, np * 8},
+                         {c->in_plen.p, pattern_lengths, np * 4},
+                         {c->in_text.p, texts, (size_t)text_words_a * 4},
+                         {c->in_pat.p, patterns, (size_t)pat_words_a * 4}};
+    const Copy in_b[] = {{(uint32_t *)c->in_text.p + text_words_a, texts + text_words_a,
+                          (size_t)(text_words - text_words_a) * 4},
+                         {(uint32_t *)c->in_pat.p + pat_words_a, patterns + pat_words_a,
+                          (size_t)(pat_words - pat_words_a) * 4}};
+    for (const Copy &x : in_a)
+        if (x.b && (e = cudaMemcpyAsync(x.d, x.h, x.b, cudaMemcpyHostToDevice, cs)) != cudaSuccess)
+            return cuda_fail(c, e, "host-to-device copy");
+    if ((e = cudaEventRecord(ev_in_a, cs)) != cudaSuccess) return cuda_fail(c, e, "event");
+    for (const Copy &x : in_b)
+        if (x.b && (e = cudaMemcpyAsync(x.d, x.h, x.b, cudaMemcpyHostToDevice, cs)) != cudaSuccess)
+            return cuda_fail(c, e, "host-to-device copy");
+    if ((e = cudaEventRecord(ev_in_b, cs)) != cudaSuccess) return cuda_fail(c, e, "event");
+    // first half: run scratch layout, resets, kernel, run offsets
+    int64_t *off_a = (int64_t *)c->out_off.p;  // dense offsets of pairs [0, h)
+    int64_t *off_b = (int64_t *)c->scr_cap.p;  // of pairs [h, n), from 0 (the capacities are used first)
+    if ((e = cudaMemcpyAsync(c->split_bounds.p, bounds_h, sizeof bounds_h, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(st, ev_in_a, 0)) != cudaSuccess ||
+        (e = launch_capacity(p.text_len, p.pat_len, n_pairs, (int64_t *)c->scr_cap.p, st)) != cudaSuccess ||
+        (e = exclusive_scan(c->scr_cap.p, 1, n_pairs, (int64_t *)c->scr_off.p, (int64_t *)c->scan_tmp.p, st)) !=
+            cudaSuccess ||
+        (e = cudaMemsetAsync(c->status.p, 0, 4, st)) != cudaSuccess ||
+        (e = cudaMemsetAsync(c->queue.p, 0, 256, st)) != cudaSuccess || (e = cudaEventRecord(ev_ready, st)) != cudaSuccess)
+        return cuda_fail(c, e, "CIGAR scratch layout");
+    if ((e = launch_plan(pa, st)) != cudaSuccess) return cuda_fail(c, e, "alignment kernel launch");
+    if ((e = exclusive_scan(p.cigar_lens, 0, h, off_a, (int64_t *)c->scan_tmp.p, st)) != cudaSuccess)
+        return cuda_fail(c, e, "CIGAR offsets");
+    // second half: waits for its inputs and for the layout and resets
+    if ((e = cudaStreamWaitEvent(sb, ev_in_b, 0)) != cudaSuccess || (e = cudaStreamWaitEvent(sb, ev_ready, 0)) != cudaSuccess)
+        return cuda_fail(c, e, "stream wait");
+    if ((e = launch_plan(pb, sb)) != cudaSuccess) return cuda_fail(c, e, "alignment kernel launch");
+    if ((e = cudaEventRecord(ev_b, sb)) != cudaSuccess) return cuda_fail(c, e, "event");
+    // first half's outputs while the second half runs
+    int64_t total_a = 0;
+    if ((e = cudaMemcpyAsync(&total_a, off_a + h, 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+        return cuda_fail(c, e, "CIGAR offsets copy");
+    const int64_t keep_a = std::min(total_a, cigar_capacity);
+    if ((rc = ensure(c, c->out_cig, (size_t)std::max<int64_t>(keep_a, 1) * 4, "cigar"))) return rc;
+    if ((e = launch_compact(p.cigar, p.cigar_off, p.cigar_lens, off_a, h, (uint32_t *)c->out_cig.p, keep_a, c->sm_count,
+                            st)) != cudaSuccess ||
+        (e = cudaEventRecord(ev_gather_a, st)) != cudaSuccess || (e = cudaStreamWaitEvent(cs, ev_gather_a, 0)) != cudaSuccess)
+        return cuda_fail(c, e, "CIGAR gather");
+    const Copy out_a[] = {{edit_counts, p.edit_counts, (size_t)h * 4},
+                          {text_consumed, p.text_consumed, (size_t)h * 4},
+                          {cigar_offsets, off_a, (size_t)h * 8},  // entry h comes with the second half
+                          {cigar, c->out_cig.p, (size_t)keep_a * 4}};
+    for (const Copy &x : out_a)  // host destination in d, device source in h
+        if (x.b && (e = cudaMemcpyAsync(x.d, x.h, x.b, cudaMemcpyDeviceToHost, cs)) != cudaSuccess)
+            return cuda_fail(c, e, "device-to-host copy");
+    // second half: run offsets from 0, gather below the capacity left, copy
+    int64_t total_b = 0;
+    if ((e = cudaStreamWaitEvent(st, ev_b, 0)) != cudaSuccess ||
+        (e = exclusive_scan(p.cigar_lens + h, 0, n_pairs - h, off_b, (int64_t *)c->scan_tmp.p, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(&total_b, off_b + (n_pairs - h), 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess)
+        return cuda_fail(c, e, "CIGAR offsets");
+    const int64_t keep_b = std::max<int64_t>(0, std::min(total_b, cigar_capacity - total_a));
+    if (keep_b > 0) {
+        if ((rc = ensure(c, c->out_cig2, (size_t)keep_b * 4, "cigar"))) return rc;
+        if ((e = launch_compact(p.cigar, p.cigar_off + h, p.cigar_lens + h, off_b, n_pairs - h,
+                                (uint32_t *)c->out_cig2.p, keep_b, c->sm_count, st)) != cudaSuccess)
+            return cuda_fail(c, e, "CIGAR gather");
+    }
+    int32_t status_h = 0;
+    const Copy out_b[] = {{edit_counts + h, p.edit_counts + h, (size_t)(n_pairs - h) * 4},
+                          {text_consumed + h, p.text_consumed + h, (size_t)(n_pairs - h) * 4},
+                          {cigar_offsets + h, off_b, ((size_t)(n_pairs - h) + 1) * 8},
+                          {cigar + total_a, c->out_cig2.p, (size_t)keep_b * 4},
+                          {&status_h, c->status.p, 4}};
+    for (const Copy &x : out_b)  // host destination in d, device source in h
+        if (x.b && (e = cudaMemcpyAsync(x.d, x.h, x.b, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+            return cuda_fail(c, e, "device-to-host copy");
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess || (e = cudaStreamSynchronize(cs)) != cudaSuccess)
+        return cuda_fail(c, e, "stream synchronise");
+    for (int32_t q = h; q <= n_pairs; ++q) cigar_offsets[q] += total_a;
+    if (status_h & 8) return fail(c, SCROOGE_E_TIMEOUT, "a bounded device wait gave up (status %d)", status_h);
+    if (status_h != 0) return fail(c, SCROOGE_E_INTERNAL, "kernel status %d", status_h);
+    if (total_a + total_b > cigar_capacity)
+        return fail(c, SCROOGE_E_CAPACITY, "CIGAR needs %lld runs, capacity %lld", (long long)(total_a + total_b),
+                    (long long)cigar_capacity);
+    return SCROOGE_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -503,6 +714,13 @@ int scrooge_align_batch(scrooge_ctx *c, const uint32_t *texts, const int64_t *te
     if (!texts || !text_offsets || !text_lengths || !patterns || !pattern_offsets || !pattern_lengths ||
         !edit_counts || !text_consumed || (cigar_capacity > 0 && !cigar))
         return fail(c, SCROOGE_E_INVAL, "null pointer argument");
+    // host pointers, persistent launch in input order: two halves, copies under the kernels
+    if (!dev && c->host_split && (flags & SCROOGE_PERSISTENT) &&
+        !(flags & (SCROOGE_LEARNED | SCROOGE_WARP_SPECIALIZED)) && n_pairs >= kHostSplitMinPairs &&
+        !(c->order && c->order_n == n_pairs))
+        return align_host_split(c, texts, text_offsets, text_lengths, patterns, pattern_offsets, pattern_lengths,
+                                n_pairs, W, O, k, flags, edit_counts, text_consumed, cigar, cigar_capacity,
+                                cigar_offsets);
     int rc;
     const size_t np = (size_t)n_pairs;
 
