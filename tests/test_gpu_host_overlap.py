@@ -59,6 +59,19 @@ def test_two_halves_equal_one_launch_and_oracle(ctx):
     _same(again, split, "second call")
 
 
+@pytest.mark.parametrize("W,O,extra", [(32, 17, 0), (64, 24, sc.SCROOGE_NO_BAND), (64, 33, sc.SCROOGE_NO_SENE),
+                                        (128, 64, 0)])
+def test_two_halves_other_kernels(ctx, W, O, extra):
+    """The two halves on the full-width kernels, the SENE-off ablation and the 128-base band."""
+    b = synth.concat([synth.long_reads(2500, seed=81), synth.short_reads(7000, seed=82)])
+    pb = sc.PackedBatch(b)
+    got = {}
+    for overlap in (True, False):
+        sc.scrooge_set_host_overlap(ctx, overlap)
+        got[overlap] = sc.align_host(ctx, pb, W, O, W, sc.SCROOGE_PERSISTENT | extra)
+    _same(got[True], got[False], f"W={W} O={O} flags={extra}")
+
+
 def test_two_halves_sequences_out_of_order(ctx):
     """Pairs whose sequences lie out of pair order: the first half's prefix of the arrays is all of them."""
     b = synth.concat([synth.long_reads(3000, seed=74), synth.short_reads(7000, seed=75)])
