@@ -13,8 +13,9 @@
 //     X[i]    = V[i+1][d-1] & (V[i+1][d-1] >> 1) & (V[i][d-1] << 1),
 // with 1s shifted in at the band edges. It is exact for windows whose edit
 // distance is at most 15 (see align_band.cu); the others are recomputed at
-// full width (Algorithm 1 on two words, Section 2.2.1) by groups of four
-// lanes, up to eight such windows per round.
+// full width (Algorithm 1 on two words, Section 2.2.1) by groups of 16, 8 or
+// 4 lanes (one window per group), whichever takes all of the warp's pending
+// windows: usually there is one, and the whole warp waits for it.
 //
 // Registers hold the whole window: X (the part of the next row that comes
 // from the current one) and PMrel for all 64 columns, both in complement
@@ -25,18 +26,21 @@
 // never executed) measured 45% slower.
 //
 // Storage (SENE, Section 2.4.1; DENT, Section 2.4.2). Only entries of the
-// columns 0..W-O (rounded up to 8) are stored, one word per cell. The last
+// columns 0..W-O are stored (W-O+1 of them where the kernel is compiled for
+// that count, else rounded up to 8), one word per cell. The last
 // `rcap` rows of each lane are kept in a cycle of row slots in shared memory
 // laid out [slot][column][lane], so every access of a lane falls on its own
 // bank whatever its column. A row that is about to be overwritten is copied
-// to a per-warp device area first ([row][column][lane]). Stored entries are in
+// to a per-warp device area first ([row][column][lane]) by one TMA bulk copy
+// issued a row ahead; the traceback reads those rows from L2. Stored entries are in
 // complement form; the traceback inverts what it reads. ET (Section 2.4.3)
 // stops a lane at the first row that reaches the window start, so the slots
 // then hold rows d_opt-rcap+1 .. d_opt: the rows the traceback (Section
 // 2.2.2) reads first, and usually the only ones it reads.
 //
-// Pair state (cursors, CIGAR output, statistics) lives in a per-warp table in
-// shared memory, [field][lane], so it does not hold registers during the DP.
+// Pair state (cursors, CIGAR output, the window's bases) lives in a per-warp
+// table in shared memory, [field][lane], so it does not hold registers during
+// the DP.
 // Idle lanes take their next pairs together: one atomic on the work queue per
 // warp and refill.
 #include "align_kernel.cuh"
