@@ -520,14 +520,12 @@ int align_host_split(scrooge_ctx *c, const uint32_t *texts, const int64_t *text_
         (rc = ensure(c, c->status, 64, "status")) || (rc = ensure(c, c->queue, 256, "work queues")) ||
         (rc = ensure(c, c->split_bounds, 4 * 8, "range bounds")))
         return rc;
-    if (!c->split_copy) {
-        if ((e = cudaStreamCreateWithFlags(&c->split_copy, cudaStreamNonBlocking)) != cudaSuccess ||
-            (e = cudaStreamCreateWithFlags(&c->split_b, cudaStreamNonBlocking)) != cudaSuccess)
-            return cuda_fail(c, e, "split streams");
-        for (cudaEvent_t &ev : c->split_ev)
-            if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
-                return cuda_fail(c, e, "split events");
-    }
+    if ((!c->split_copy && (e = cudaStreamCreateWithFlags(&c->split_copy, cudaStreamNonBlocking)) != cudaSuccess) ||
+        (!c->split_b && (e = cudaStreamCreateWithFlags(&c->split_b, cudaStreamNonBlocking)) != cudaSuccess))
+        return cuda_fail(c, e, "split streams");
+    for (cudaEvent_t &ev : c->split_ev)
+        if (!ev && (e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
+            return cuda_fail(c, e, "split events");
     cudaStream_t st = c->stream, cs = c->split_copy, sb = c->split_b;
     cudaEvent_t ev_in_a = c->split_ev[0], ev_in_b = c->split_ev[1], ev_ready = c->split_ev[2],
                 ev_b = c->split_ev[3], ev_gather_a = c->split_ev[4], ev_start = c->split_ev[5];
