@@ -476,6 +476,67 @@ cudaError_t launch_plan(const LaunchPlan &lp, cudaStream_t st) {
     }
 }
 
+// Layout of a host-pointer batch: every pair's offsets must be >= 0 multiples of 64 bases and its
+// lengths >= 0. Gives the packed words of the text and pattern arrays that the pairs reach (all
+// pairs, and the pairs [0, h)) and the CIGAR scratch runs (n + m + 1 per pair). Large batches are
+// checked by several host threads. Returns the first pair that breaks the layout, or -1.
+struct HostLayout {
+    int64_t text_words = 0, pat_words = 0, text_words_a = 0, pat_words_a = 0, runs = 0;
+};
+
+int32_t host_layout(const int64_t *to, const int32_t *tl, const int64_t *po, const int32_t *pl, int32_t n, int32_t h,
+                    HostLayout &out) {
+    auto part = [&](int32_t lo, int32_t hi, HostLayout &r, int32_t &bad) {
+        bad = -1;
+        for (int32_t q = lo; q < hi; ++q) {
+            const int64_t x = to[q], y = po[q];
+            const int32_t u = tl[q], v = pl[q];
+            if (x < 0 || y < 0 || (x & 63) || (y & 63) || u < 0 || v < 0) {
+                bad = q;
+                return;
+            }
+            const int64_t et = x / 16 + scrooge_packed_words(u), ep = y / 16 + scrooge_packed_words(v);
+            r.text_words = std::max(r.text_words, et);
+            r.pat_words = std::max(r.pat_words, ep);
+            if (q < h) {
+                r.text_words_a = std::max(r.text_words_a, et);
+                r.pat_words_a = std::max(r.pat_words_a, ep);
+            }
+            r.runs += (int64_t)u + v + 1;
+        }
+    };
+    const unsigned hw = std::thread::hardware_concurrency();
+    int nt = n >= 65536 ? (int)std::min(8u, std::max(1u, hw)) : 1;
+    std::vector<HostLayout> rs(nt);
+    std::vector<int32_t> bads(nt, -1);
+    if (nt > 1) {
+        std::vector<std::thread> th;
+        try {
+            for (int t = 0; t < nt; ++t)
+                th.emplace_back(part, (int32_t)((int64_t)n * t / nt), (int32_t)((int64_t)n * (t + 1) / nt),
+                                std::ref(rs[t]), std::ref(bads[t]));
+        } catch (...) {  // no threads: check on this one
+            for (auto &x : th) x.join();
+            th.clear();
+            nt = 1;
+            rs.assign(1, HostLayout());
+            bads.assign(1, -1);
+        }
+        for (auto &x : th) x.join();
+    }
+    if (nt == 1) part(0, n, rs[0], bads[0]);
+    out = HostLayout();
+    for (int t = 0; t < nt; ++t) {
+        if (bads[t] >= 0) return bads[t];  // chunks are in pair order: the first bad chunk holds the first bad pair
+        out.text_words = std::max(out.text_words, rs[t].text_words);
+        out.pat_words = std::max(out.pat_words, rs[t].pat_words);
+        out.text_words_a = std::max(out.text_words_a, rs[t].text_words_a);
+        out.pat_words_a = std::max(out.pat_words_a, rs[t].pat_words_a);
+        out.runs += rs[t].runs;
+    }
+    return -1;
+}
+
 constexpr int32_t kHostSplitMinPairs = 8192;
 
 // Host-pointer persistent calls on large batches, in two halves of the pair range [0, h) and
@@ -493,20 +554,12 @@ int align_host_split(scrooge_ctx *c, const uint32_t *texts, const int64_t *text_
     cudaError_t e;
     int rc;
     // layout check; the words of both sequence arrays that the first half needs (a prefix)
-    int64_t text_words = 0, pat_words = 0, text_words_a = 0, pat_words_a = 0, scratch_runs = 0;
-    for (int32_t q = 0; q < n_pairs; ++q) {
-        const int64_t to = text_offsets[q], po = pattern_offsets[q];
-        const int32_t tl = text_lengths[q], pl = pattern_lengths[q];
-        if (to < 0 || po < 0 || (to & 63) || (po & 63) || tl < 0 || pl < 0)
-            return fail(c, SCROOGE_E_INVAL, "pair %d: offsets must be >= 0 multiples of 64, lengths >= 0", q);
-        text_words = std::max(text_words, to / 16 + scrooge_packed_words(tl));
-        pat_words = std::max(pat_words, po / 16 + scrooge_packed_words(pl));
-        if (q == h - 1) {
-            text_words_a = text_words;
-            pat_words_a = pat_words;
-        }
-        scratch_runs += (int64_t)tl + pl + 1;
-    }
+    HostLayout lay;
+    const int32_t bad = host_layout(text_offsets, text_lengths, pattern_offsets, pattern_lengths, n_pairs, h, lay);
+    if (bad >= 0)
+        return fail(c, SCROOGE_E_INVAL, "pair %d: offsets must be >= 0 multiples of 64, lengths >= 0", bad);
+    const int64_t text_words = lay.text_words, pat_words = lay.pat_words, text_words_a = lay.text_words_a,
+                  pat_words_a = lay.pat_words_a, scratch_runs = lay.runs;
     if ((rc = ensure(c, c->scr_off, (np + 1) * 8, "CIGAR scratch offsets")) ||
         (rc = ensure(c, c->scr_len, np * 4, "CIGAR run counts")) ||
         (rc = ensure(c, c->scan_tmp, (size_t)scan_temp_words((int64_t)np + 1) * 8, "scan scratch")) ||
@@ -756,16 +809,12 @@ int scrooge_align_batch(scrooge_ctx *c, const uint32_t *texts, const int64_t *te
     } else {
         // host pointers: check the layout, then stage everything on the device (the run scratch
         // offsets are laid out on the device from the copied lengths, as for device pointers)
-        int64_t text_words = 0, pat_words = 0;
-        for (int32_t q = 0; q < n_pairs; ++q) {
-            const int64_t to = text_offsets[q], po = pattern_offsets[q];
-            const int32_t tl = text_lengths[q], pl = pattern_lengths[q];
-            if (to < 0 || po < 0 || (to & 63) || (po & 63) || tl < 0 || pl < 0)
-                return fail(c, SCROOGE_E_INVAL, "pair %d: offsets must be >= 0 multiples of 64, lengths >= 0", q);
-            text_words = std::max(text_words, to / 16 + scrooge_packed_words(tl));
-            pat_words = std::max(pat_words, po / 16 + scrooge_packed_words(pl));
-            scratch_runs += (int64_t)tl + pl + 1;
-        }
+        HostLayout lay;
+        const int32_t bad = host_layout(text_offsets, text_lengths, pattern_offsets, pattern_lengths, n_pairs, 0, lay);
+        if (bad >= 0)
+            return fail(c, SCROOGE_E_INVAL, "pair %d: offsets must be >= 0 multiples of 64, lengths >= 0", bad);
+        const int64_t text_words = lay.text_words, pat_words = lay.pat_words;
+        scratch_runs = lay.runs;
         if ((rc = ensure(c, c->in_text, text_words * 4, "texts")) ||
             (rc = ensure(c, c->in_pat, pat_words * 4, "patterns")) ||
             (rc = ensure(c, c->in_toff, np * 8, "text offsets")) ||

@@ -121,3 +121,26 @@ def test_two_halves_capacity_too_small(ctx, where):
         s, e = off[p], off[p + 1]
         assert np.array_equal(out[True][s:e], full["cigar"][s:e]), f"pair {p}"
         assert np.array_equal(out[False][s:e], full["cigar"][s:e]), f"pair {p}"
+
+
+def test_large_batch_layout_checked_by_threads(ctx):
+    """Batches of 65,536 pairs or more have their layout checked by several host threads: the results are
+    those of the one-launch path, and a broken pair is reported by its index (the first broken one)."""
+    b = synth.short_reads(120_000, seed=83)
+    pb = sc.PackedBatch(b)
+    got = {}
+    for overlap in (True, False):
+        sc.scrooge_set_host_overlap(ctx, overlap)
+        got[overlap] = sc.align_host(ctx, pb, 64, 24, 64, sc.SCROOGE_PERSISTENT)
+    _same(got[True], got[False], "120,000 short reads")
+    for q in (119_990, 61_000):
+        bad = copy.copy(pb)
+        bad.pat_off = pb.pat_off.copy()
+        bad.pat_off[q] += 16
+        bad.pat_off[119_995] += 32  # a later broken pair: the first one is named
+        for overlap in (True, False):
+            sc.scrooge_set_host_overlap(ctx, overlap)
+            with pytest.raises(sc.ScroogeError) as err:
+                sc.align_host(ctx, bad, 64, 24, 64, sc.SCROOGE_PERSISTENT)
+            assert err.value.code == sc.SCROOGE_E_INVAL
+            assert f"pair {q}:" in str(err.value), str(err.value)
