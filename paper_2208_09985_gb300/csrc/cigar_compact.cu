@@ -18,6 +18,12 @@ __global__ void capacity_kernel(const int32_t *text_len, const int32_t *pat_len,
     if (p < n) cap[p] = (int64_t)text_len[p] + (int64_t)pat_len[p] + 1;
 }
 
+// v[i] += *base for i < n (the base is a device value, e.g. an earlier scan's total)
+__global__ void add_base_kernel(int64_t *v, int64_t n, const int64_t *base) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) v[i] += *base;
+}
+
 __device__ __forceinline__ int64_t warp_incl_scan(int64_t v) {
     const int lane = threadIdx.x & 31;
 #pragma unroll
@@ -125,6 +131,12 @@ cudaError_t exclusive_scan(const void *in, int wide, int64_t n, int64_t *out, in
         add_tile_offsets<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(out, n, sum_off);
     }
     total_kernel<<<1, 32, 0, s>>>(in, wide, n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_add_base(int64_t *v, int64_t n, const int64_t *base, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    add_base_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(v, n, base);
     return cudaGetLastError();
 }
 

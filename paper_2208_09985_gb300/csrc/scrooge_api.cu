@@ -627,7 +627,8 @@ int align_host_split(scrooge_ctx *c, const uint32_t *texts, const int64_t *text_
         memcpy(c->last_shape, shape, sizeof shape);
     }
     // kernels: two alignment launches, and per half a scan and a gather
-    c->last_kernels = 2 + scan_kernel_count(h) + scan_kernel_count(n_pairs - h) + 2;  // alignment, offsets, gathers
+    // alignment, offsets (two scans and a rebase), gathers
+    c->last_kernels = 2 + scan_kernel_count(h) + scan_kernel_count(n_pairs - h) + 1 + 2;
     const int64_t bounds_h[4] = {0, h, h, n_pairs};
     // inputs: the small per-pair arrays and the first half's sequence words, then the rest
     if ((e = cudaEventRecord(ev_start, st)) != cudaSuccess || (e = cudaStreamWaitEvent(cs, ev_start, 0)) != cudaSuccess)
@@ -706,6 +707,9 @@ int align_host_split(scrooge_ctx *c, const uint32_t *texts, const int64_t *text_
                                 (uint32_t *)c->out_cig2.p, keep_b, c->sm_count, st)) != cudaSuccess)
             return cuda_fail(c, e, "CIGAR gather");
     }
+    // the second half's offsets from the first half's total on, before they are copied out
+    if ((e = launch_add_base(off_b, (int64_t)(n_pairs - h) + 1, off_a + h, st)) != cudaSuccess)
+        return cuda_fail(c, e, "CIGAR offsets");
     int32_t status_h = 0;
     const Copy out_b[] = {{edit_counts + h, p.edit_counts + h, (size_t)(n_pairs - h) * 4},
                           {text_consumed + h, p.text_consumed + h, (size_t)(n_pairs - h) * 4},
@@ -717,7 +721,6 @@ int align_host_split(scrooge_ctx *c, const uint32_t *texts, const int64_t *text_
             return cuda_fail(c, e, "device-to-host copy");
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess || (e = cudaStreamSynchronize(cs)) != cudaSuccess)
         return cuda_fail(c, e, "stream synchronise");
-    for (int32_t q = h; q <= n_pairs; ++q) cigar_offsets[q] += total_a;
     if (status_h & 8) return fail(c, SCROOGE_E_TIMEOUT, "a bounded device wait gave up (status %d)", status_h);
     if (status_h != 0) return fail(c, SCROOGE_E_INTERNAL, "kernel status %d", status_h);
     if (total_a + total_b > cigar_capacity)

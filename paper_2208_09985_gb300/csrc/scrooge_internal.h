@@ -197,6 +197,8 @@ int scan_kernel_count(int64_t n);
 cudaError_t exclusive_scan(const void *in, int wide, int64_t n, int64_t *out, int64_t *tmp, cudaStream_t s);
 // cap[p] = text_len[p] + pat_len[p] + 1
 cudaError_t launch_capacity(const int32_t *text_len, const int32_t *pat_len, int32_t n, int64_t *cap, cudaStream_t s);
+// v[i] += *base for i < n (base: a device pointer)
+cudaError_t launch_add_base(int64_t *v, int64_t n, const int64_t *base, cudaStream_t s);
 // copies each pair's runs to dense[dense_off[p] ..] when they fit below capacity
 cudaError_t launch_compact(const uint32_t *scratch, const int64_t *scratch_off, const int32_t *lens,
                            const int64_t *dense_off, int32_t n, uint32_t *dense, int64_t capacity, int sm_count,
