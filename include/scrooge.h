@@ -228,19 +228,21 @@ int scrooge_get_bucket_config(const scrooge_ctx *ctx, int32_t bucket, int32_t *k
 int scrooge_set_learned_order(scrooge_ctx *ctx, int32_t on);
 int32_t scrooge_get_learned_order(const scrooge_ctx *ctx);
 
-/* Host-pointer calls in two halves (no counterpart in the paper; never
- * changes results). A scrooge_align_batch call with host pointers, a
- * persistent launch in input order (SCROOGE_PERSISTENT, or SCROOGE_LEARNED
- * with the model's order switched off, no order set by scrooge_set_order for
- * this batch, not SCROOGE_WARP_SPECIALIZED) and at least 8,192 pairs is run
- * as two halves of its pair range when this is on (1, the default): the
- * second half's sequences are copied to the device while the first half's
- * kernel runs, and the first half's outputs are gathered and copied back
- * while the second half's kernel runs. Each half has its own launch and row
- * scratch, and the second launch's blocks take the SMs that the first one's
- * blocks free. The first half's sequence words are the prefix of the texts
- * and patterns arrays that its pairs reach, so the overlap needs pairs laid
- * out in pair order. Such calls are not captured in a CUDA graph
+/* Host-pointer calls in parts (no counterpart in the paper; never changes
+ * results). A scrooge_align_batch call with host pointers, a persistent
+ * launch in input order (SCROOGE_PERSISTENT, or SCROOGE_LEARNED with the
+ * model's order switched off, no order set by scrooge_set_order for this
+ * batch, not SCROOGE_WARP_SPECIALIZED) and at least 8,192 pairs is run as 2
+ * to 4 parts of its pair range when this is on (1, the default); a part
+ * holds at least as many pairs as the kernel has pair slots on the GPU where
+ * the batch allows. Each part's sequences are copied to the device while the
+ * parts before it run, and its outputs are gathered and copied back while
+ * the parts after it run. Each part has its own launch; consecutive parts
+ * alternate between two kernel streams with their own row scratch, and a
+ * part's blocks take the SMs that the previous part's blocks free. The
+ * sequence words a part needs are the prefix of the texts and patterns
+ * arrays that its pairs and the earlier ones reach, so the overlap needs
+ * pairs laid out in pair order. Such calls are not captured in a CUDA graph
  * (SCROOGE_GRAPH is ignored for them). 0 runs them as one launch. */
 int scrooge_set_host_overlap(scrooge_ctx *ctx, int32_t on);
 int32_t scrooge_get_host_overlap(const scrooge_ctx *ctx);

@@ -67,7 +67,8 @@ int scrooge_destroy(scrooge_ctx *c) {
                      &c->scr_runs,  &c->scr_off, &c->scr_len, &c->scr_cap,  &c->scan_tmp, &c->queue,
                      &c->model,     &c->grad,    &c->adam_m1, &c->adam_m2,  &c->loss,     &c->l_feat,
                      &c->l_pred,    &c->l_key,   &c->l_order, &c->l_tmp,    &c->t_rows,   &c->fallback, &c->spill2,
-                     &c->spill3,    &c->fallback2, &c->fallback3, &c->split_bounds, &c->out_cig2};
+                     &c->spill3,    &c->fallback2, &c->fallback3, &c->split_bounds, &c->out_cig_parts[0],
+                     &c->out_cig_parts[1], &c->out_cig_parts[2]};
     if (c->graph) cudaGraphExecDestroy(c->graph);
     if (c->stream2) cudaStreamDestroy(c->stream2);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
@@ -75,6 +76,7 @@ int scrooge_destroy(scrooge_ctx *c) {
     if (c->ev_join3) cudaEventDestroy(c->ev_join3);
     if (c->stream3) cudaStreamDestroy(c->stream3);
     if (c->split_copy) cudaStreamDestroy(c->split_copy);
+    if (c->split_a) cudaStreamDestroy(c->split_a);
     if (c->split_b) cudaStreamDestroy(c->split_b);
     for (cudaEvent_t ev : c->split_ev)
         if (ev) cudaEventDestroy(ev);
@@ -476,90 +478,112 @@ cudaError_t launch_plan(const LaunchPlan &lp, cudaStream_t st) {
     }
 }
 
+constexpr int kMaxParts = 4;
+
 // Layout of a host-pointer batch: every pair's offsets must be >= 0 multiples of 64 bases and its
-// lengths >= 0. Gives the packed words of the text and pattern arrays that the pairs reach (all
-// pairs, and the pairs [0, h)) and the CIGAR scratch runs (n + m + 1 per pair). Large batches are
-// checked by several host threads. Returns the first pair that breaks the layout, or -1.
+// lengths >= 0. Gives the packed words of the text and pattern arrays that the pairs [0, ends[i])
+// reach, for each of the `nparts` ascending part ends (the last is n), and the CIGAR scratch runs
+// (n + m + 1 per pair). Large batches are checked by several host threads. Returns the first pair
+// that breaks the layout, or -1.
 struct HostLayout {
-    int64_t text_words = 0, pat_words = 0, text_words_a = 0, pat_words_a = 0, runs = 0;
+    int64_t text_upto[kMaxParts] = {}, pat_upto[kMaxParts] = {}, runs = 0;
 };
 
-int32_t host_layout(const int64_t *to, const int32_t *tl, const int64_t *po, const int32_t *pl, int32_t n, int32_t h,
-                    HostLayout &out) {
-    auto part = [&](int32_t lo, int32_t hi, HostLayout &r, int32_t &bad) {
-        bad = -1;
+int32_t host_layout(const int64_t *to, const int32_t *tl, const int64_t *po, const int32_t *pl, int32_t n,
+                    const int32_t *ends, int nparts, HostLayout &out) {
+    // per chunk of pairs: the words each part's pairs in the chunk reach, the runs, the first bad pair
+    struct Part {
+        int64_t text[kMaxParts] = {}, pat[kMaxParts] = {}, runs = 0;
+        int32_t bad = -1;
+    };
+    auto run = [&](int32_t lo, int32_t hi, Part &r) {
+        int pi = 0;
         for (int32_t q = lo; q < hi; ++q) {
+            while (q >= ends[pi]) ++pi;
             const int64_t x = to[q], y = po[q];
             const int32_t u = tl[q], v = pl[q];
             if (x < 0 || y < 0 || (x & 63) || (y & 63) || u < 0 || v < 0) {
-                bad = q;
+                r.bad = q;
                 return;
             }
-            const int64_t et = x / 16 + scrooge_packed_words(u), ep = y / 16 + scrooge_packed_words(v);
-            r.text_words = std::max(r.text_words, et);
-            r.pat_words = std::max(r.pat_words, ep);
-            if (q < h) {
-                r.text_words_a = std::max(r.text_words_a, et);
-                r.pat_words_a = std::max(r.pat_words_a, ep);
-            }
+            r.text[pi] = std::max(r.text[pi], x / 16 + scrooge_packed_words(u));
+            r.pat[pi] = std::max(r.pat[pi], y / 16 + scrooge_packed_words(v));
             r.runs += (int64_t)u + v + 1;
         }
     };
     const unsigned hw = std::thread::hardware_concurrency();
     int nt = n >= 65536 ? (int)std::min(8u, std::max(1u, hw)) : 1;
-    std::vector<HostLayout> rs(nt);
-    std::vector<int32_t> bads(nt, -1);
+    std::vector<Part> rs(nt);
     if (nt > 1) {
         std::vector<std::thread> th;
         try {
             for (int t = 0; t < nt; ++t)
-                th.emplace_back(part, (int32_t)((int64_t)n * t / nt), (int32_t)((int64_t)n * (t + 1) / nt),
-                                std::ref(rs[t]), std::ref(bads[t]));
+                th.emplace_back(run, (int32_t)((int64_t)n * t / nt), (int32_t)((int64_t)n * (t + 1) / nt),
+                                std::ref(rs[t]));
         } catch (...) {  // no threads: check on this one
             for (auto &x : th) x.join();
             th.clear();
             nt = 1;
-            rs.assign(1, HostLayout());
-            bads.assign(1, -1);
+            rs.assign(1, Part());
         }
         for (auto &x : th) x.join();
     }
-    if (nt == 1) part(0, n, rs[0], bads[0]);
+    if (nt == 1) run(0, n, rs[0]);
     out = HostLayout();
     for (int t = 0; t < nt; ++t) {
-        if (bads[t] >= 0) return bads[t];  // chunks are in pair order: the first bad chunk holds the first bad pair
-        out.text_words = std::max(out.text_words, rs[t].text_words);
-        out.pat_words = std::max(out.pat_words, rs[t].pat_words);
-        out.text_words_a = std::max(out.text_words_a, rs[t].text_words_a);
-        out.pat_words_a = std::max(out.pat_words_a, rs[t].pat_words_a);
+        if (rs[t].bad >= 0) return rs[t].bad;  // chunks are in pair order: the first bad chunk holds the first bad pair
+        for (int i = 0; i < nparts; ++i) {
+            out.text_upto[i] = std::max(out.text_upto[i], rs[t].text[i]);
+            out.pat_upto[i] = std::max(out.pat_upto[i], rs[t].pat[i]);
+        }
         out.runs += rs[t].runs;
+    }
+    for (int i = 1; i < nparts; ++i) {  // words reached by every pair before the end of part i
+        out.text_upto[i] = std::max(out.text_upto[i], out.text_upto[i - 1]);
+        out.pat_upto[i] = std::max(out.pat_upto[i], out.pat_upto[i - 1]);
     }
     return -1;
 }
 
 constexpr int32_t kHostSplitMinPairs = 8192;
 
-// Host-pointer persistent calls on large batches, in two halves of the pair range [0, h) and
-// [h, n): the second half's inputs are copied while the first half's kernel runs, and the first
-// half's outputs while the second half's kernel runs. One kernel launch per half over its range of
-// the persistent queue, each with its own row scratch, so that the second launch's blocks take the
-// SMs the first one's blocks free; the dense CIGAR of each half is gathered and copied on its own.
-// Same results as the one-launch path (the kernels align each pair independently).
+// Host-pointer persistent calls on large batches, in K = 2..4 parts of the pair range, each of at
+// least a wave of the kernel's pair slots where the batch allows. Part i's sequences are copied
+// while the parts before it run, and its outputs
+// are gathered and copied back while the parts after it run, so only the first part's input copy
+// and the last part's output copy are exposed. One kernel launch per part over its range of the
+// persistent queue; parts alternate between two kernel streams, each with its own row scratch, so
+// that part i + 1's blocks take the SMs that part i's blocks free. Each part's run offsets are
+// scanned, gathered and rebased by the previous parts' total on the device. Same results as the
+// one-launch path (the kernels align each pair independently).
 int align_host_split(scrooge_ctx *c, const uint32_t *texts, const int64_t *text_offsets, const int32_t *text_lengths,
                      const uint32_t *patterns, const int64_t *pattern_offsets, const int32_t *pattern_lengths,
                      int32_t n_pairs, int32_t W, int32_t O, int32_t k, uint32_t flags, int32_t *edit_counts,
                      int32_t *text_consumed, uint32_t *cigar, int64_t cigar_capacity, int64_t *cigar_offsets) {
-    const int32_t h = n_pairs / 2;
     const size_t np = (size_t)n_pairs;
     cudaError_t e;
     int rc;
-    // layout check; the words of both sequence arrays that the first half needs (a prefix)
+    AlignParams p;
+    memset(&p, 0, sizeof p);
+    p.n_pairs = n_pairs;
+    p.W = W;
+    p.O = O;
+    p.k = k;
+    const bool band = use_band(W, flags);
+    // parts of at least a wave of pair slots each, so that a part's launch fills the GPU
+    LaunchPlan shape_plan;
+    if ((rc = make_plan(c, p, band, flags, c->spill, c->fallback, 0, shape_plan))) return rc;
+    const int64_t slots = (int64_t)shape_plan.blocks * shape_plan.wpb * (32 / shape_plan.G);
+    const int K = (int)std::max<int64_t>(2, std::min<int64_t>(kMaxParts, n_pairs / std::max<int64_t>(slots, 1)));
+    int32_t start[kMaxParts + 1];
+    for (int i = 0; i <= K; ++i) start[i] = (int32_t)((int64_t)n_pairs * i / K);
+    // layout check; the words of both sequence arrays that the parts up to each one need (prefixes)
     HostLayout lay;
-    const int32_t bad = host_layout(text_offsets, text_lengths, pattern_offsets, pattern_lengths, n_pairs, h, lay);
+    const int32_t bad =
+        host_layout(text_offsets, text_lengths, pattern_offsets, pattern_lengths, n_pairs, start + 1, K, lay);
     if (bad >= 0)
         return fail(c, SCROOGE_E_INVAL, "pair %d: offsets must be >= 0 multiples of 64, lengths >= 0", bad);
-    const int64_t text_words = lay.text_words, pat_words = lay.pat_words, text_words_a = lay.text_words_a,
-                  pat_words_a = lay.pat_words_a, scratch_runs = lay.runs;
+    const int64_t text_words = lay.text_upto[K - 1], pat_words = lay.pat_upto[K - 1], scratch_runs = lay.runs;
     if ((rc = ensure(c, c->scr_off, (np + 1) * 8, "CIGAR scratch offsets")) ||
         (rc = ensure(c, c->scr_len, np * 4, "CIGAR run counts")) ||
         (rc = ensure(c, c->scan_tmp, (size_t)scan_temp_words((int64_t)np + 1) * 8, "scan scratch")) ||
@@ -567,27 +591,23 @@ int align_host_split(scrooge_ctx *c, const uint32_t *texts, const int64_t *text_
         (rc = ensure(c, c->in_toff, np * 8, "text offsets")) || (rc = ensure(c, c->in_tlen, np * 4, "text lengths")) ||
         (rc = ensure(c, c->in_poff, np * 8, "pattern offsets")) ||
         (rc = ensure(c, c->in_plen, np * 4, "pattern lengths")) || (rc = ensure(c, c->out_ec, np * 4, "edit counts")) ||
-        (rc = ensure(c, c->out_tc, np * 4, "text consumed")) || (rc = ensure(c, c->out_off, (np + 1) * 8, "cigar offsets")) ||
+        (rc = ensure(c, c->out_tc, np * 4, "text consumed")) ||
+        (rc = ensure(c, c->out_off, (np + kMaxParts) * 8, "cigar offsets")) ||
         (rc = ensure(c, c->scr_cap, (np + 1) * 8, "CIGAR capacities")) ||
         (rc = ensure(c, c->scr_runs, (size_t)std::max<int64_t>(scratch_runs, 1) * 4, "CIGAR run scratch")) ||
         (rc = ensure(c, c->status, 64, "status")) || (rc = ensure(c, c->queue, 256, "work queues")) ||
-        (rc = ensure(c, c->split_bounds, 4 * 8, "range bounds")))
+        (rc = ensure(c, c->split_bounds, 2 * kMaxParts * 8, "range bounds")))
         return rc;
     if ((!c->split_copy && (e = cudaStreamCreateWithFlags(&c->split_copy, cudaStreamNonBlocking)) != cudaSuccess) ||
+        (!c->split_a && (e = cudaStreamCreateWithFlags(&c->split_a, cudaStreamNonBlocking)) != cudaSuccess) ||
         (!c->split_b && (e = cudaStreamCreateWithFlags(&c->split_b, cudaStreamNonBlocking)) != cudaSuccess))
         return cuda_fail(c, e, "split streams");
     for (cudaEvent_t &ev : c->split_ev)
         if (!ev && (e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
             return cuda_fail(c, e, "split events");
-    cudaStream_t st = c->stream, cs = c->split_copy, sb = c->split_b;
-    cudaEvent_t ev_in_a = c->split_ev[0], ev_in_b = c->split_ev[1], ev_ready = c->split_ev[2],
-                ev_b = c->split_ev[3], ev_gather_a = c->split_ev[4], ev_start = c->split_ev[5];
-    AlignParams p;
-    memset(&p, 0, sizeof p);
-    p.n_pairs = n_pairs;
-    p.W = W;
-    p.O = O;
-    p.k = k;
+    cudaStream_t st = c->stream, cs = c->split_copy, ks[2] = {c->split_a, c->split_b};
+    cudaEvent_t ev_start = c->split_ev[0], ev_ready = c->split_ev[1], *ev_in = c->split_ev + 2,
+                *ev_k = c->split_ev + 2 + kMaxParts, *ev_g = c->split_ev + 2 + 2 * kMaxParts;
     p.texts = (const uint32_t *)c->in_text.p;
     p.patterns = (const uint32_t *)c->in_pat.p;
     p.text_off = (const int64_t *)c->in_toff.p;
@@ -603,128 +623,118 @@ int align_host_split(scrooge_ctx *c, const uint32_t *texts, const int64_t *text_
     p.st_rows = c->st_rows;
     p.st_cells = c->st_cells;
     p.st_cycles = c->st_cycles;
-    const bool band = use_band(W, flags);
-    LaunchPlan pa, pb;
-    if ((rc = make_plan(c, p, band, flags, c->spill, c->fallback, 0, pa)) ||
-        (rc = make_plan(c, p, band, flags, c->spill2, c->fallback3, 0, pb)))
+    LaunchPlan plans[2];
+    if ((rc = make_plan(c, p, band, flags, c->spill, c->fallback, 0, plans[0])) ||
+        (rc = make_plan(c, p, band, flags, c->spill2, c->fallback3, 0, plans[1])))
         return rc;
-    const int64_t *bounds = (const int64_t *)c->split_bounds.p;  // {0, h, h, n}
-    pa.p.range_lo = bounds;
-    pa.p.range_hi = bounds + 1;
-    pb.p.range_lo = bounds + 2;
-    pb.p.range_hi = bounds + 3;
-    for (LaunchPlan *lp : {&pa, &pb}) {
-        lp->p.status = (int32_t *)c->status.p;
-        lp->p.wait_limit = c->wait_limit;
-        lp->p.order = nullptr;
-        lp->p.queue = (int32_t *)c->queue.p + (lp == &pb ? 16 : 0);
-    }
     {
+        const LaunchPlan &pa = plans[0];
         const TableShape &ts = pa.ts;
         const int64_t shape[13] = {pa.band ? 0 : pa.words, pa.G, pa.p.rcap, pa.wpb, (int64_t)pa.smem, pa.blocks,
                                    pa.p.ncol, ts.swp, pa.p.table_words_per_warp * 4LL, pa.p.spill_words_per_pair * 4,
                                    pa.p.fb_words_per_warp * 4, 32 / pa.G, pa.p.ring};
         memcpy(c->last_shape, shape, sizeof shape);
     }
-    // kernels: two alignment launches, and per half a scan and a gather
-    // alignment, offsets (two scans and a rebase), gathers
-    c->last_kernels = 2 + scan_kernel_count(h) + scan_kernel_count(n_pairs - h) + 1 + 2;
-    const int64_t bounds_h[4] = {0, h, h, n_pairs};
-    // inputs: the small per-pair arrays and the first half's sequence words, then the rest
-    if ((e = cudaEventRecord(ev_start, st)) != cudaSuccess || (e = cudaStreamWaitEvent(cs, ev_start, 0)) != cudaSuccess)
-        return cuda_fail(c, e, "stream fork");
+    // kernels: an alignment launch, a scan and a gather per part, and a rebase per part after the first
+    c->last_kernels = 3 * K - 1;
+    for (int i = 0; i < K; ++i) c->last_kernels += scan_kernel_count(start[i + 1] - start[i]);
+    int64_t bounds_h[2 * kMaxParts];
+    for (int i = 0; i < K; ++i) {
+        bounds_h[2 * i] = start[i];
+        bounds_h[2 * i + 1] = start[i + 1];
+    }
     struct Copy {
         void *d;
         const void *h;
         size_t b;
     };
-    const Copy in_a[] = {{c->in_toff.p, text_offsets, np * 8},
-                         {c->in_tlen.p, text_lengths, np * 4},
-                         {c->in_poff.p, pattern_offsets, np * 8},
-                         {c->in_plen.p, pattern_lengths, np * 4},
-                         {c->in_text.p, texts, (size_t)text_words_a * 4},
-                         {c->in_pat.p, patterns, (size_t)pat_words_a * 4}};
-    const Copy in_b[] = {{(uint32_t *)c->in_text.p + text_words_a, texts + text_words_a,
-                          (size_t)(text_words - text_words_a) * 4},
-                         {(uint32_t *)c->in_pat.p + pat_words_a, patterns + pat_words_a,
-                          (size_t)(pat_words - pat_words_a) * 4}};
-    for (const Copy &x : in_a)
-        if (x.b && (e = cudaMemcpyAsync(x.d, x.h, x.b, cudaMemcpyHostToDevice, cs)) != cudaSuccess)
+    // inputs: the per-pair arrays, then each part's new sequence words (prefixes of the arrays)
+    if ((e = cudaEventRecord(ev_start, st)) != cudaSuccess || (e = cudaStreamWaitEvent(cs, ev_start, 0)) != cudaSuccess)
+        return cuda_fail(c, e, "stream fork");
+    const Copy per_pair[] = {{c->in_toff.p, text_offsets, np * 8},
+                             {c->in_tlen.p, text_lengths, np * 4},
+                             {c->in_poff.p, pattern_offsets, np * 8},
+                             {c->in_plen.p, pattern_lengths, np * 4}};
+    for (const Copy &x : per_pair)
+        if ((e = cudaMemcpyAsync(x.d, x.h, x.b, cudaMemcpyHostToDevice, cs)) != cudaSuccess)
             return cuda_fail(c, e, "host-to-device copy");
-    if ((e = cudaEventRecord(ev_in_a, cs)) != cudaSuccess) return cuda_fail(c, e, "event");
-    for (const Copy &x : in_b)
-        if (x.b && (e = cudaMemcpyAsync(x.d, x.h, x.b, cudaMemcpyHostToDevice, cs)) != cudaSuccess)
-            return cuda_fail(c, e, "host-to-device copy");
-    if ((e = cudaEventRecord(ev_in_b, cs)) != cudaSuccess) return cuda_fail(c, e, "event");
-    // first half: run scratch layout, resets, kernel, run offsets
-    int64_t *off_a = (int64_t *)c->out_off.p;  // dense offsets of pairs [0, h)
-    int64_t *off_b = (int64_t *)c->scr_cap.p;  // of pairs [h, n), from 0 (the capacities are used first)
-    if ((e = cudaMemcpyAsync(c->split_bounds.p, bounds_h, sizeof bounds_h, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
-        (e = cudaStreamWaitEvent(st, ev_in_a, 0)) != cudaSuccess ||
+    for (int i = 0; i < K; ++i) {
+        const int64_t t0 = i ? lay.text_upto[i - 1] : 0, p0 = i ? lay.pat_upto[i - 1] : 0;
+        const Copy seq[] = {{(uint32_t *)c->in_text.p + t0, texts + t0, (size_t)(lay.text_upto[i] - t0) * 4},
+                            {(uint32_t *)c->in_pat.p + p0, patterns + p0, (size_t)(lay.pat_upto[i] - p0) * 4}};
+        for (const Copy &x : seq)
+            if (x.b && (e = cudaMemcpyAsync(x.d, x.h, x.b, cudaMemcpyHostToDevice, cs)) != cudaSuccess)
+                return cuda_fail(c, e, "host-to-device copy");
+        if ((e = cudaEventRecord(ev_in[i], cs)) != cudaSuccess) return cuda_fail(c, e, "event");
+    }
+    // run scratch layout and resets, once the per-pair arrays are in (they precede part 0's words)
+    if ((e = cudaMemcpyAsync(c->split_bounds.p, bounds_h, sizeof(int64_t) * 2 * K, cudaMemcpyHostToDevice, st)) !=
+            cudaSuccess ||
+        (e = cudaStreamWaitEvent(st, ev_in[0], 0)) != cudaSuccess ||
         (e = launch_capacity(p.text_len, p.pat_len, n_pairs, (int64_t *)c->scr_cap.p, st)) != cudaSuccess ||
         (e = exclusive_scan(c->scr_cap.p, 1, n_pairs, (int64_t *)c->scr_off.p, (int64_t *)c->scan_tmp.p, st)) !=
             cudaSuccess ||
         (e = cudaMemsetAsync(c->status.p, 0, 4, st)) != cudaSuccess ||
         (e = cudaMemsetAsync(c->queue.p, 0, 256, st)) != cudaSuccess || (e = cudaEventRecord(ev_ready, st)) != cudaSuccess)
         return cuda_fail(c, e, "CIGAR scratch layout");
-    if ((e = launch_plan(pa, st)) != cudaSuccess) return cuda_fail(c, e, "alignment kernel launch");
-    if ((e = exclusive_scan(p.cigar_lens, 0, h, off_a, (int64_t *)c->scan_tmp.p, st)) != cudaSuccess)
-        return cuda_fail(c, e, "CIGAR offsets");
-    // second half: waits for its inputs and for the layout and resets
-    if ((e = cudaStreamWaitEvent(sb, ev_in_b, 0)) != cudaSuccess || (e = cudaStreamWaitEvent(sb, ev_ready, 0)) != cudaSuccess)
-        return cuda_fail(c, e, "stream wait");
-    if ((e = launch_plan(pb, sb)) != cudaSuccess) return cuda_fail(c, e, "alignment kernel launch");
-    if ((e = cudaEventRecord(ev_b, sb)) != cudaSuccess) return cuda_fail(c, e, "event");
-    // first half's outputs while the second half runs
-    int64_t total_a = 0;
-    if ((e = cudaMemcpyAsync(&total_a, off_a + h, 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
-        (e = cudaStreamSynchronize(st)) != cudaSuccess)
-        return cuda_fail(c, e, "CIGAR offsets copy");
-    const int64_t keep_a = std::min(total_a, cigar_capacity);
-    if ((rc = ensure(c, c->out_cig, (size_t)std::max<int64_t>(keep_a, 1) * 4, "cigar"))) return rc;
-    if ((e = launch_compact(p.cigar, p.cigar_off, p.cigar_lens, off_a, h, (uint32_t *)c->out_cig.p, keep_a, c->sm_count,
-                            st)) != cudaSuccess ||
-        (e = cudaEventRecord(ev_gather_a, st)) != cudaSuccess || (e = cudaStreamWaitEvent(cs, ev_gather_a, 0)) != cudaSuccess)
-        return cuda_fail(c, e, "CIGAR gather");
-    const Copy out_a[] = {{edit_counts, p.edit_counts, (size_t)h * 4},
-                          {text_consumed, p.text_consumed, (size_t)h * 4},
-                          {cigar_offsets, off_a, (size_t)h * 8},  // entry h comes with the second half
-                          {cigar, c->out_cig.p, (size_t)keep_a * 4}};
-    for (const Copy &x : out_a)  // host destination in d, device source in h
-        if (x.b && (e = cudaMemcpyAsync(x.d, x.h, x.b, cudaMemcpyDeviceToHost, cs)) != cudaSuccess)
-            return cuda_fail(c, e, "device-to-host copy");
-    // second half: run offsets from 0, gather below the capacity left, copy
-    int64_t total_b = 0;
-    if ((e = cudaStreamWaitEvent(st, ev_b, 0)) != cudaSuccess ||
-        (e = exclusive_scan(p.cigar_lens + h, 0, n_pairs - h, off_b, (int64_t *)c->scan_tmp.p, st)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(&total_b, off_b + (n_pairs - h), 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
-        (e = cudaStreamSynchronize(st)) != cudaSuccess)
-        return cuda_fail(c, e, "CIGAR offsets");
-    const int64_t keep_b = std::max<int64_t>(0, std::min(total_b, cigar_capacity - total_a));
-    if (keep_b > 0) {
-        if ((rc = ensure(c, c->out_cig2, (size_t)keep_b * 4, "cigar"))) return rc;
-        if ((e = launch_compact(p.cigar, p.cigar_off + h, p.cigar_lens + h, off_b, n_pairs - h,
-                                (uint32_t *)c->out_cig2.p, keep_b, c->sm_count, st)) != cudaSuccess)
-            return cuda_fail(c, e, "CIGAR gather");
+    // the parts' kernels, alternating between two streams (part i + 2 after part i)
+    const int64_t *bounds = (const int64_t *)c->split_bounds.p;
+    for (int i = 0; i < K; ++i) {
+        LaunchPlan lp = plans[i & 1];
+        lp.p.status = (int32_t *)c->status.p;
+        lp.p.wait_limit = c->wait_limit;
+        lp.p.order = nullptr;
+        lp.p.queue = (int32_t *)c->queue.p + 16 * i;
+        lp.p.range_lo = bounds + 2 * i;
+        lp.p.range_hi = bounds + 2 * i + 1;
+        cudaStream_t s = ks[i & 1];
+        if ((e = cudaStreamWaitEvent(s, ev_in[i], 0)) != cudaSuccess || (e = cudaStreamWaitEvent(s, ev_ready, 0)) != cudaSuccess)
+            return cuda_fail(c, e, "stream wait");
+        if ((e = launch_plan(lp, s)) != cudaSuccess) return cuda_fail(c, e, "alignment kernel launch");
+        if ((e = cudaEventRecord(ev_k[i], s)) != cudaSuccess) return cuda_fail(c, e, "event");
     }
-    // the second half's offsets from the first half's total on, before they are copied out
-    if ((e = launch_add_base(off_b, (int64_t)(n_pairs - h) + 1, off_a + h, st)) != cudaSuccess)
-        return cuda_fail(c, e, "CIGAR offsets");
+    // each part's outputs, in order, while the later parts run: run offsets from 0 (into out_off
+    // at start + i), gather below the capacity left, rebase by the previous part's end, copy back
+    int64_t base = 0;  // runs of the parts before this one
     int32_t status_h = 0;
-    const Copy out_b[] = {{edit_counts + h, p.edit_counts + h, (size_t)(n_pairs - h) * 4},
-                          {text_consumed + h, p.text_consumed + h, (size_t)(n_pairs - h) * 4},
-                          {cigar_offsets + h, off_b, ((size_t)(n_pairs - h) + 1) * 8},
-                          {cigar + total_a, c->out_cig2.p, (size_t)keep_b * 4},
-                          {&status_h, c->status.p, 4}};
-    for (const Copy &x : out_b)  // host destination in d, device source in h
-        if (x.b && (e = cudaMemcpyAsync(x.d, x.h, x.b, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
-            return cuda_fail(c, e, "device-to-host copy");
-    if ((e = cudaStreamSynchronize(st)) != cudaSuccess || (e = cudaStreamSynchronize(cs)) != cudaSuccess)
+    for (int i = 0; i < K; ++i) {
+        const int32_t lo = start[i], ni = start[i + 1] - start[i];
+        int64_t *off_i = (int64_t *)c->out_off.p + lo + i;  // ni + 1 entries
+        int64_t total_i = 0;
+        if ((e = cudaStreamWaitEvent(st, ev_k[i], 0)) != cudaSuccess ||
+            (e = exclusive_scan(p.cigar_lens + lo, 0, ni, off_i, (int64_t *)c->scan_tmp.p, st)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(&total_i, off_i + ni, 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(st)) != cudaSuccess)
+            return cuda_fail(c, e, "CIGAR offsets");
+        const int64_t keep_i = std::max<int64_t>(0, std::min(total_i, cigar_capacity - base));
+        DevBuf &dense = i ? c->out_cig_parts[i - 1] : c->out_cig;
+        if (keep_i > 0) {
+            if ((rc = ensure(c, dense, (size_t)keep_i * 4, "cigar"))) return rc;
+            if ((e = launch_compact(p.cigar, p.cigar_off + lo, p.cigar_lens + lo, off_i, ni, (uint32_t *)dense.p,
+                                    keep_i, c->sm_count, st)) != cudaSuccess)
+                return cuda_fail(c, e, "CIGAR gather");
+        }
+        if (i && (e = launch_add_base(off_i, (int64_t)ni + 1, off_i - 1, st)) != cudaSuccess)  // previous part's end
+            return cuda_fail(c, e, "CIGAR offsets");
+        if ((e = cudaEventRecord(ev_g[i], st)) != cudaSuccess || (e = cudaStreamWaitEvent(cs, ev_g[i], 0)) != cudaSuccess)
+            return cuda_fail(c, e, "event");
+        const bool last = i == K - 1;
+        const Copy out[] = {{edit_counts + lo, p.edit_counts + lo, (size_t)ni * 4},
+                            {text_consumed + lo, p.text_consumed + lo, (size_t)ni * 4},
+                            {cigar_offsets + lo, off_i, ((size_t)ni + (last ? 1 : 0)) * 8},
+                            {cigar + base, dense.p, (size_t)keep_i * 4},
+                            {&status_h, c->status.p, last ? 4u : 0u}};
+        for (const Copy &x : out)  // host destination in d, device source in h
+            if (x.b && (e = cudaMemcpyAsync(x.d, x.h, x.b, cudaMemcpyDeviceToHost, cs)) != cudaSuccess)
+                return cuda_fail(c, e, "device-to-host copy");
+        base += total_i;
+    }
+    if ((e = cudaStreamSynchronize(cs)) != cudaSuccess || (e = cudaStreamSynchronize(st)) != cudaSuccess)
         return cuda_fail(c, e, "stream synchronise");
     if (status_h & 8) return fail(c, SCROOGE_E_TIMEOUT, "a bounded device wait gave up (status %d)", status_h);
     if (status_h != 0) return fail(c, SCROOGE_E_INTERNAL, "kernel status %d", status_h);
-    if (total_a + total_b > cigar_capacity)
-        return fail(c, SCROOGE_E_CAPACITY, "CIGAR needs %lld runs, capacity %lld", (long long)(total_a + total_b),
+    if (base > cigar_capacity)
+        return fail(c, SCROOGE_E_CAPACITY, "CIGAR needs %lld runs, capacity %lld", (long long)base,
                     (long long)cigar_capacity);
     return SCROOGE_OK;
 }
@@ -813,10 +823,11 @@ int scrooge_align_batch(scrooge_ctx *c, const uint32_t *texts, const int64_t *te
         // host pointers: check the layout, then stage everything on the device (the run scratch
         // offsets are laid out on the device from the copied lengths, as for device pointers)
         HostLayout lay;
-        const int32_t bad = host_layout(text_offsets, text_lengths, pattern_offsets, pattern_lengths, n_pairs, 0, lay);
+        const int32_t bad =
+            host_layout(text_offsets, text_lengths, pattern_offsets, pattern_lengths, n_pairs, &n_pairs, 1, lay);
         if (bad >= 0)
             return fail(c, SCROOGE_E_INVAL, "pair %d: offsets must be >= 0 multiples of 64, lengths >= 0", bad);
-        const int64_t text_words = lay.text_words, pat_words = lay.pat_words;
+        const int64_t text_words = lay.text_upto[0], pat_words = lay.pat_upto[0];
         scratch_runs = lay.runs;
         if ((rc = ensure(c, c->in_text, text_words * 4, "texts")) ||
             (rc = ensure(c, c->in_pat, pat_words * 4, "patterns")) ||

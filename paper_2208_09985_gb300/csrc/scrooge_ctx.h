@@ -63,12 +63,12 @@ struct scrooge_ctx {
     cudaEvent_t t_start = nullptr, t_stop = nullptr;
     int32_t last_kernels = 0;  // kernels launched by the last alignment call
     int64_t last_shape[13] = {0};  // launch shape of the last alignment call (scrooge_last_launch_shape)
-    // host-pointer persistent calls in two halves (align_host_split): copy stream, second kernel
-    // stream, events, range bounds, the second half's dense CIGAR
+    // host-pointer persistent calls in parts (align_host_split): copy stream, two kernel streams,
+    // events, range bounds, the dense CIGAR of the parts after the first (which uses out_cig)
     bool host_split = true;
-    cudaStream_t split_copy = nullptr, split_b = nullptr;
-    cudaEvent_t split_ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-    scrooge::DevBuf split_bounds, out_cig2;
+    cudaStream_t split_copy = nullptr, split_a = nullptr, split_b = nullptr;
+    cudaEvent_t split_ev[16] = {};
+    scrooge::DevBuf split_bounds, out_cig_parts[3];
     // CUDA graph of the learned pipeline, keyed by the call it was captured for
     cudaGraphExec_t graph = nullptr;
     unsigned long long graph_key[28] = {0};

@@ -1,11 +1,12 @@
-"""Host-pointer calls in two halves (copies under the kernels) against one launch and the oracle
+"""Host-pointer calls in parts (copies under the kernels) against one launch and the oracle
 (needs a GB300).
 
-A persistent call with host pointers on at least 8,192 pairs runs as two launches over the two
-halves of its pairs, each half's copies overlapping the other half's kernel. The results must be
-those of the one-launch path and of the oracle, bit for bit: with pairs laid out in order, with
-sequences out of pair order (the first half then needs the whole arrays), and with a CIGAR buffer
-too small for the second half or for the first.
+A persistent call with host pointers on at least 8,192 pairs runs as launches over 2 to 4 parts
+of its pairs (a part holds at least a wave of the kernel's pair slots where the batch allows),
+each part's copies overlapping the other parts' kernels.
+The results must be those of the one-launch path and of the oracle, bit for bit: with pairs laid
+out in order, with sequences out of pair order (the first part then needs the whole arrays), and
+with a CIGAR buffer that ends inside any part.
 """
 import copy
 import os
@@ -144,3 +145,35 @@ def test_large_batch_layout_checked_by_threads(ctx):
                 sc.align_host(ctx, bad, 64, 24, 64, sc.SCROOGE_PERSISTENT)
             assert err.value.code == sc.SCROOGE_E_INVAL
             assert f"pair {q}:" in str(err.value), str(err.value)
+
+
+@pytest.mark.parametrize("part", [0, 2, 3])
+def test_four_parts_capacity_too_small(ctx, part):
+    """Four parts (at least four waves of the lane kernel's 38,912 pair slots) with a CIGAR buffer that
+    ends inside part `part`."""
+    b = synth.concat([synth.long_reads(1500, seed=84), synth.short_reads(160_000, seed=85)])
+    pb = sc.PackedBatch(b)
+    n = pb.n_pairs
+    assert n >= 4 * 38_912
+    full = _run(ctx, pb, False)
+    off = full["cigar_off"]
+    lo, hi = n * part // 4, n * (part + 1) // 4
+    cap = int((off[lo] + off[hi]) // 2)
+    got = {}
+    for overlap in (True, False):
+        sc.scrooge_set_host_overlap(ctx, overlap)
+        ec, tc = np.zeros(n, np.int32), np.zeros(n, np.int32)
+        o, cig = np.zeros(n + 1, np.int64), np.zeros(cap, np.uint32)
+        with pytest.raises(sc.ScroogeError) as err:
+            sc.scrooge_align_batch(ctx, pb.texts, pb.text_off, pb.text_len, pb.patterns, pb.pat_off, pb.pat_len, n,
+                                   64, 24, 64, sc.SCROOGE_PERSISTENT, ec, tc, cig, cap, o)
+        assert err.value.code == sc.SCROOGE_E_CAPACITY
+        assert np.array_equal(o, off) and np.array_equal(ec, full["edit_counts"])
+        assert np.array_equal(tc, full["text_consumed"])
+        got[overlap] = cig
+    fits = np.flatnonzero(off[1:] <= cap)
+    end = int(off[fits[-1] + 1]) if fits.size else 0
+    assert np.array_equal(got[True][:end], full["cigar"][:end])
+    assert np.array_equal(got[False][:end], full["cigar"][:end])
+    split = _run(ctx, pb, True)
+    _same(split, full, "four parts, full capacity")
