@@ -391,7 +391,7 @@ def scrooge_get_learned_order(ctx) -> bool:
 
 
 def scrooge_set_host_overlap(ctx, on: bool):
-    """Host-pointer persistent calls of 8,192 pairs or more in two halves, copies under the kernels (True, the
+    """Host-pointer persistent calls of 8,192 pairs or more in 2 to 4 parts, copies under the kernels (True, the
     default), or as one launch (False)."""
     return _check(ctx, load().scrooge_set_host_overlap(ctx, 1 if on else 0))
 

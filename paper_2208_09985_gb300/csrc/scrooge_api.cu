@@ -778,7 +778,7 @@ int scrooge_align_batch(scrooge_ctx *c, const uint32_t *texts, const int64_t *te
     if (!texts || !text_offsets || !text_lengths || !patterns || !pattern_offsets || !pattern_lengths ||
         !edit_counts || !text_consumed || (cigar_capacity > 0 && !cigar))
         return fail(c, SCROOGE_E_INVAL, "null pointer argument");
-    // host pointers, persistent launch in input order: two halves, copies under the kernels
+    // host pointers, persistent launch in input order: parts, copies under the kernels
     if (!dev && c->host_split && (flags & SCROOGE_PERSISTENT) &&
         !(flags & (SCROOGE_LEARNED | SCROOGE_WARP_SPECIALIZED)) && n_pairs >= kHostSplitMinPairs &&
         !(c->order && c->order_n == n_pairs))
