@@ -102,14 +102,14 @@ struct CigarOut {
         edits += (any && op != kOpEq) ? len : 0;
         const bool same = cur != 0u && (int)(cur & 15u) == op;
         const bool spill = any && cur != 0u && !same;
-        if (spill && n < cap) dst[n] = cur;
+        if (spill && n < cap) __stcs(dst + n, cur);  // streaming: not read again by this kernel
         n += spill ? 1 : 0;
         cur = !any ? cur : (same ? cur + ((uint32_t)len << 4) : (((uint32_t)len << 4) | (uint32_t)op));
     }
     __device__ __forceinline__ void emit(int op, int len) { emit_maybe(op, len); }
     __device__ __forceinline__ void flush() {
         if (cur != 0u) {
-            if (n < cap) dst[n] = cur;
+            if (n < cap) __stcs(dst + n, cur);
             ++n;
         }
         cur = 0u;

@@ -73,8 +73,11 @@ __device__ __forceinline__ uint32_t lane_shl1(uint32_t v) { return __funnelshift
 // Bulk copies from shared to global memory (TMA, asynchronous): a row slot goes to the device area
 // in one instruction of one lane. The callers order them against the row stores with __syncwarp.
 __device__ __forceinline__ void bulk_copy_s2g(uint32_t *gdst, const uint32_t *ssrc, uint32_t bytes) {
-    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst),
-                 "r"((uint32_t)__cvta_generic_to_shared(ssrc)), "r"(bytes));
+    // the evicted rows are read back within a window: keep them in L2 ahead of streaming data
+    uint64_t policy;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(policy));
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group.L2::cache_hint [%0], [%1], %2, %3;" ::"l"(gdst),
+                 "r"((uint32_t)__cvta_generic_to_shared(ssrc)), "r"(bytes), "l"(policy));
     asm volatile("cp.async.bulk.commit_group;");
 }
 // The copies issued so far have read their source (it may be overwritten).
